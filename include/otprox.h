@@ -1,0 +1,180 @@
+/*
+ * otprox.h -- C ABI of the GB300 (sm_103a) unbalanced Beckmann-OT proximal
+ * library.
+ *
+ * The library computes the proximal operator of the unbalanced Beckmann
+ * optimal-transport regulariser of Lee, Bertrand & Rozell, "Parallel
+ * Unbalanced Optimal Transport Regularization for Large-scale Imaging
+ * Problems" (arXiv:1909.00149):
+ *
+ *   prox^mu_{rho V}(p0, p1) = argmin_{x0,x1 >= 0, M, r}
+ *        ||M||_{2,1} + mu ||r||_p^p + (1/2 rho) ||[x0;x1] - [p0;p1]||^2
+ *        s.t.  D(M) - x0 + x1 = r                           (eq. Prox_UOT)
+ *
+ * by Algorithm 1 (Sec. III-B), and the RPCA+UOT-DF solver (Algorithm 3,
+ * Sec. IV-B) that uses it, for B independent problems at once.
+ *
+ * Conventions shared by every entry point:
+ *  - Images are dense row-major float32 arrays [B][H][W] (row = the paper's
+ *    index i, "x"; column = index j, "y").  B independent problems share
+ *    H, W and the parameters.
+ *  - Array pointers may be HOST or DEVICE memory: the library copies with
+ *    cudaMemcpyDefault (unified addressing), so pinned host memory is copied
+ *    asynchronously and pageable host memory synchronously.  The caller
+ *    keeps ownership of every array it passes; the library never keeps a
+ *    caller pointer past the call.  State lives in library-owned device
+ *    memory with rows padded to a multiple of 4 floats.
+ *  - Work is ordered on the CUDA stream given at create time (NULL = the
+ *    legacy default stream).  Calls marked "sync" wait for that stream.
+ *  - Every function returns OT_OK (0) or a negative OT_E* code, and sets a
+ *    thread-local message readable with ot_last_error().  Invalid arguments
+ *    never reach a kernel.
+ *  - A handle is not thread-safe: one thread at a time per handle.
+ */
+#ifndef OTPROX_H
+#define OTPROX_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------ status codes */
+#define OT_OK          0
+#define OT_EINVAL     -1  /* bad argument: shape, pointer, parameter, step rule */
+#define OT_ENOMEM     -2  /* device or pinned-host allocation failed            */
+#define OT_ECUDA      -3  /* a CUDA runtime call failed (message has the name)  */
+#define OT_ENOTCONV   -4  /* max_iter reached before the tolerance; outputs valid */
+#define OT_ENONFINITE -5  /* a NaN/Inf appeared in the iterates                 */
+#define OT_ETIMEOUT   -6  /* a bounded device wait gave up                      */
+
+/* ------------------------------------------------------------ enumerations */
+/* Which arguments of V_mu are variables (Sec. III-B):
+ *  PROX        -- x0 and x1 free: eq. (Prox_UOT);
+ *  FIXED_FIRST -- x0 frozen at p0 = s, x1 free with prox centre p1: the
+ *                 special case eq. (Prox_UOT_specialcase), K = D(M) - s + x - r;
+ *  EVAL        -- x0 = p0, x1 = p1 frozen: solves V_mu(p0, p1) itself
+ *                 (eq. Unbal_OT_beckman); the objective is the OT cost. */
+#define OT_MODE_PROX        0
+#define OT_MODE_FIXED_FIRST 1
+#define OT_MODE_EVAL        2
+/* Flux norm: ISO = ||M||_{2,1} (Sec. III-A); ANISO = sum |Mx| + |My|. */
+#define OT_NORM_ISO   0
+#define OT_NORM_ANISO 1
+/* Kernel choice for Algorithm 1: AUTO picks RESIDENT when one problem's
+ * state fits in one CTA's shared memory, TILED otherwise. */
+#define OT_KERNEL_AUTO     0
+#define OT_KERNEL_TILED    1
+#define OT_KERNEL_RESIDENT 2
+
+typedef struct ot_prox* ot_prox_t;
+
+typedef struct {
+  int32_t B, H, W;        /* problems, rows, columns (all >= 1)                  */
+  int32_t mode;           /* OT_MODE_*                                           */
+  int32_t norm;           /* OT_NORM_*                                           */
+  int32_t balanced;       /* 1: r = 0, the balanced problem (eq. OT_beckman)    */
+  int32_t p_exp;          /* 1: mu ||r||_1 (the paper's choice); 2: mu ||r||_2^2 */
+  double  mu;             /* growth/decay penalty mu > 0                         */
+  double  rho;            /* prox weight: (1/2rho)||x - p||^2, rho > 0           */
+  double  tau1, tau2;     /* primal/dual steps; <= 0 selects
+                             0.99 / sqrt(lambda_max(D D*) + n_id), which obeys
+                             Theorem 1; given steps must satisfy
+                             tau1 tau2 (lambda_max + n_id) < 1                   */
+  double  tol;            /* stopping tolerance on res_pri and res_fp            */
+  int32_t max_iter;       /* iteration cap of ot_prox_solve                      */
+  int32_t check_every;    /* iterations between stopping tests (>= 1)            */
+  int32_t kernel;         /* OT_KERNEL_*                                         */
+  int32_t use_graph;      /* 1: replay each check interval as a CUDA graph       */
+} ot_prox_params;
+
+typedef struct {
+  int32_t iters;          /* iterations run by this call                         */
+  int32_t status;         /* OT_OK / OT_ENOTCONV / OT_ENONFINITE                 */
+  double  res_pri;        /* ||K(z)|| / ||p||  at the last check                  */
+  double  res_fp;         /* ||(z,a)^{k+1}-(z,a)^k|| / ||(z,a)^{k+1}||            */
+  double  objective;      /* ||M||_{2,1} + mu ||r||_p^p + (1/2rho)||x - p||^2     */
+  double  primal_feasible;/* objective with r' = D(M) + A x (constraint exact)   */
+  double  dual_obj;       /* dual objective at the scaled/clipped dual a         */
+  double  rel_gap;        /* (primal_feasible - dual_obj) / |primal_feasible|    */
+} ot_prox_result;
+
+/* Fill *p with the defaults: mode PROX, iso, unbalanced, p = 1, mu = 3,
+ * rho = 0.01, default steps, tol = 1e-5, max_iter = 100000,
+ * check_every = 10, kernel AUTO, use_graph = 1.  B, H, W are set to 1. */
+void ot_prox_default_params(ot_prox_params* p);
+
+/* lambda_max(D D*) = 4 sin^2(pi (H-1) / 2H) + 4 sin^2(pi (W-1) / 2W): the
+ * largest eigenvalue of the Neumann grid Laplacian of Theorem 1. */
+double ot_lambda_max(int32_t H, int32_t W);
+
+/* Number of identity blocks n_id of K acting on free variables (x0, x1, r):
+ * ||K||^2 = lambda_max + n_id; the full problem of Theorem 1 has n_id = 3. */
+int32_t ot_n_identity_blocks(int32_t mode, int32_t balanced);
+
+/* Create a solver for B problems of H x W (Sec. III-B).  Validates every
+ * field, applies the default steps, rejects steps that break Theorem 1
+ * (tau1 tau2 (lambda_max + n_id) >= 1) with OT_EINVAL, allocates the state
+ * (zero) on the current device.  `cuda_stream` is a cudaStream_t or NULL. */
+int ot_prox_create(const ot_prox_params* params, void* cuda_stream, ot_prox_t* out);
+
+/* The prox centres [B][H][W]: p0, p1 (PROX), s = p0 and p (FIXED_FIRST),
+ * the two arguments of V_mu (EVAL).  Both pointers required.  Async on the
+ * handle's stream (synchronous for pageable host memory). */
+int ot_prox_set_input(ot_prox_t h, const float* p0, const float* p1);
+
+/* Run n_iter >= 0 iterations of Algorithm 1 from the current (warm) state,
+ * with no stopping test: the inexact warm-started use of Sec. III-B that
+ * Algorithm 3 line 11 makes.  Async. */
+int ot_prox_step(ot_prox_t h, int32_t n_iter);
+
+/* One check interval of ot_prox_solve: n_iter >= 1 iterations, the last one
+ * also computing the stopping quantities (res_pri, res_fp, objective; the
+ * certificate fields are left 0).  Returns OT_OK or OT_ENONFINITE.  Sync. */
+int ot_prox_check_interval(ot_prox_t h, int32_t n_iter, ot_prox_result* res);
+
+/* ot_prox_step bracketed by two CUDA events recorded on the handle's stream;
+ * *elapsed_ms receives the device time between them.  Used to time the
+ * iteration kernel alone.  Sync. */
+int ot_prox_step_timed(ot_prox_t h, int32_t n_iter, double* elapsed_ms);
+
+/* Iterate from the current state until max(res_pri, res_fp) <= tol (tested
+ * every check_every iterations) or max_iter iterations; fills *res (may be
+ * NULL).  Returns OT_OK, OT_ENOTCONV (outputs still valid) or
+ * OT_ENONFINITE.  Sync. */
+int ot_prox_solve(ot_prox_t h, ot_prox_result* res);
+
+/* Residuals, objective and duality-gap certificate of the current state,
+ * without iterating (res_fp is 0, iters is 0).  Sync. */
+int ot_prox_evaluate(ot_prox_t h, ot_prox_result* res);
+
+/* Copy the state out, dense [B][H][W]; any pointer may be NULL to skip it.
+ * For a frozen x the copy is its input.  Async (pageable host: sync). */
+int ot_prox_get_state(ot_prox_t h, float* Mx, float* My, float* x0, float* x1,
+                      float* r, float* a);
+
+/* Copy a warm state in (Algorithm 2 caches the prox state between outer
+ * iterations); NULL pointers leave that variable unchanged.  Flux on the
+ * outer slots Mx[H-1,:], My[:,W-1] (no edge there) is set to 0; frozen x
+ * ignore their pointer.  Async (pageable host: sync). */
+int ot_prox_set_state(ot_prox_t h, const float* Mx, const float* My, const float* x0,
+                      const float* x1, const float* r, const float* a);
+
+/* Zero the state (Algorithm 2 line 2 initialises the prox state to 0). */
+int ot_prox_reset(ot_prox_t h);
+
+/* Resolved parameters (defaults filled in) of a handle. */
+int ot_prox_get_params(ot_prox_t h, ot_prox_params* out);
+
+/* Free everything the handle owns; NULL is accepted. */
+int ot_prox_destroy(ot_prox_t h);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char* ot_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* OTPROX_H */

@@ -1,0 +1,181 @@
+"""GB300 (sm_103a) unbalanced Beckmann-OT proximal solver -- Python binding.
+
+Thin marshalling layer over the C ABI of include/otprox.h (libotprox.so):
+every step of the computation runs in the library's CUDA kernels.  PyTorch
+is used only for device memory and the current CUDA stream.  If the library
+is not built, importing this package raises: there is no CPU fallback.
+
+The raw C functions are re-exported under their C names (``ot_prox_create``
+etc.); :class:`OtProx` wraps a handle with tensor arguments.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _abi
+from ._abi import (KERNELS, MODES, NORMS, OT_ENONFINITE, OT_ENOTCONV, OT_OK, STATUS_NAMES, ot_prox_params,
+                   ot_prox_result)
+
+_lib = _abi.load()
+LIB_PATH = _abi.LIB_PATH
+
+for _name, _res, _args in _abi.PROTOTYPES:
+    globals()[_name] = getattr(_lib, _name)
+
+
+class OtError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        msg = _lib.ot_last_error().decode(errors="replace")
+        super().__init__(f"{where}: {STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+def check(code: int, where: str, ok=(OT_OK,)) -> int:
+    if code not in ok:
+        raise OtError(code, where)
+    return code
+
+
+def _stream_handle(stream) -> int | None:
+    if stream is None:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+class _Arrays:
+    """Keeps numpy temporaries alive for the duration of a call."""
+
+    def __init__(self, n: int):
+        self.n = n
+        self.keep = []
+
+    def ptr(self, x, writable=False):
+        if x is None:
+            return None
+        try:
+            import torch
+            if isinstance(x, torch.Tensor):
+                if x.dtype != torch.float32 or not x.is_contiguous():
+                    raise ValueError("tensors must be contiguous float32")
+                if x.numel() != self.n:
+                    raise ValueError(f"expected {self.n} elements, got {x.numel()}")
+                return x.data_ptr()
+        except ImportError:
+            pass
+        a = np.asarray(x)
+        if writable:
+            if a.dtype != np.float32 or not a.flags.c_contiguous:
+                raise ValueError("output arrays must be C-contiguous float32")
+        else:
+            a = np.ascontiguousarray(a, dtype=np.float32)
+        if a.size != self.n:
+            raise ValueError(f"expected {self.n} elements, got {a.size}")
+        self.keep.append(a)
+        return a.ctypes.data
+
+
+def default_params(**kw) -> ot_prox_params:
+    p = ot_prox_params()
+    _lib.ot_prox_default_params(ctypes.byref(p))
+    for k, v in kw.items():
+        if k == "mode":
+            v = MODES[v] if isinstance(v, str) else v
+        elif k == "norm":
+            v = NORMS[v] if isinstance(v, str) else v
+        elif k == "kernel":
+            v = KERNELS[v] if isinstance(v, str) else v
+        elif k in ("balanced", "use_graph"):
+            v = int(bool(v))
+        if not hasattr(p, k):
+            raise TypeError(f"unknown parameter {k!r}")
+        setattr(p, k, v)
+    return p
+
+
+class OtProx:
+    """B independent prox problems of eq. (Prox_UOT) on an H x W grid."""
+
+    def __init__(self, B: int, H: int, W: int, stream=None, **params):
+        self.B, self.H, self.W = int(B), int(H), int(W)
+        p = default_params(B=self.B, H=self.H, W=self.W, **params)
+        h = ctypes.c_void_p()
+        self._stream = _stream_handle(stream)
+        check(_lib.ot_prox_create(ctypes.byref(p), self._stream, ctypes.byref(h)), "ot_prox_create")
+        self.h = h
+        self.params = ot_prox_params()
+        check(_lib.ot_prox_get_params(self.h, ctypes.byref(self.params)), "ot_prox_get_params")
+
+    @property
+    def n(self) -> int:
+        return self.B * self.H * self.W
+
+    def close(self):
+        if getattr(self, "h", None):
+            _lib.ot_prox_destroy(self.h)
+            self.h = None
+
+    __del__ = close
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def set_input(self, p0, p1):
+        A = _Arrays(self.n)
+        check(_lib.ot_prox_set_input(self.h, A.ptr(p0), A.ptr(p1)), "ot_prox_set_input")
+
+    def step(self, n_iter: int):
+        check(_lib.ot_prox_step(self.h, int(n_iter)), "ot_prox_step")
+
+    def solve(self) -> dict:
+        r = ot_prox_result()
+        check(_lib.ot_prox_solve(self.h, ctypes.byref(r)), "ot_prox_solve", ok=(OT_OK, OT_ENOTCONV))
+        return r.as_dict()
+
+    def check_interval(self, n_iter: int) -> dict:
+        r = ot_prox_result()
+        check(_lib.ot_prox_check_interval(self.h, int(n_iter), ctypes.byref(r)), "ot_prox_check_interval")
+        return r.as_dict()
+
+    def step_timed(self, n_iter: int) -> float:
+        ms = ctypes.c_double()
+        check(_lib.ot_prox_step_timed(self.h, int(n_iter), ctypes.byref(ms)), "ot_prox_step_timed")
+        return ms.value
+
+    def evaluate(self) -> dict:
+        r = ot_prox_result()
+        check(_lib.ot_prox_evaluate(self.h, ctypes.byref(r)), "ot_prox_evaluate", ok=(OT_OK, OT_ENONFINITE))
+        return r.as_dict()
+
+    def reset(self):
+        check(_lib.ot_prox_reset(self.h), "ot_prox_reset")
+
+    def get_state(self, device=None) -> dict:
+        """State as float32 tensors [B, H, W] (on ``device``, default cuda)."""
+        import torch
+        dev = torch.device("cuda") if device is None else torch.device(device)
+        names = ("Mx", "My", "x0", "x1", "r", "a")
+        out = {k: torch.empty((self.B, self.H, self.W), dtype=torch.float32, device=dev,
+                              pin_memory=(dev.type == "cpu" and torch.cuda.is_available()))
+               for k in names}
+        A = _Arrays(self.n)
+        check(_lib.ot_prox_get_state(self.h, *(A.ptr(out[k], True) for k in names)), "ot_prox_get_state")
+        torch.cuda.synchronize()
+        return out
+
+    def set_state(self, Mx=None, My=None, x0=None, x1=None, r=None, a=None):
+        A = _Arrays(self.n)
+        check(_lib.ot_prox_set_state(self.h, A.ptr(Mx), A.ptr(My), A.ptr(x0), A.ptr(x1), A.ptr(r), A.ptr(a)),
+              "ot_prox_set_state")
+
+
+__all__ = ["OtProx", "OtError", "default_params", "check", "LIB_PATH", "ot_prox_params", "ot_prox_result"]

@@ -1,0 +1,81 @@
+"""ctypes declarations of the C ABI in include/otprox.h (argument marshalling only)."""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libotprox.so")
+
+OT_OK = 0
+OT_EINVAL = -1
+OT_ENOMEM = -2
+OT_ECUDA = -3
+OT_ENOTCONV = -4
+OT_ENONFINITE = -5
+OT_ETIMEOUT = -6
+STATUS_NAMES = {0: "OT_OK", -1: "OT_EINVAL", -2: "OT_ENOMEM", -3: "OT_ECUDA", -4: "OT_ENOTCONV",
+                -5: "OT_ENONFINITE", -6: "OT_ETIMEOUT"}
+
+MODES = {"prox": 0, "fixed_first": 1, "eval": 2}
+NORMS = {"iso": 0, "aniso": 1}
+KERNELS = {"auto": 0, "tiled": 1, "resident": 2}
+
+c_float_p = ctypes.POINTER(ctypes.c_float)
+c_double_p = ctypes.POINTER(ctypes.c_double)
+
+
+class ot_prox_params(ctypes.Structure):
+    _fields_ = [("B", ctypes.c_int32), ("H", ctypes.c_int32), ("W", ctypes.c_int32),
+                ("mode", ctypes.c_int32), ("norm", ctypes.c_int32), ("balanced", ctypes.c_int32),
+                ("p_exp", ctypes.c_int32),
+                ("mu", ctypes.c_double), ("rho", ctypes.c_double),
+                ("tau1", ctypes.c_double), ("tau2", ctypes.c_double), ("tol", ctypes.c_double),
+                ("max_iter", ctypes.c_int32), ("check_every", ctypes.c_int32),
+                ("kernel", ctypes.c_int32), ("use_graph", ctypes.c_int32)]
+
+
+class ot_prox_result(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int32), ("status", ctypes.c_int32),
+                ("res_pri", ctypes.c_double), ("res_fp", ctypes.c_double),
+                ("objective", ctypes.c_double), ("primal_feasible", ctypes.c_double),
+                ("dual_obj", ctypes.c_double), ("rel_gap", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+# (name, restype, argtypes)
+PROTOTYPES = [
+    ("ot_last_error", ctypes.c_char_p, []),
+    ("ot_prox_default_params", None, [ctypes.POINTER(ot_prox_params)]),
+    ("ot_lambda_max", ctypes.c_double, [ctypes.c_int32, ctypes.c_int32]),
+    ("ot_n_identity_blocks", ctypes.c_int32, [ctypes.c_int32, ctypes.c_int32]),
+    ("ot_prox_create", ctypes.c_int, [ctypes.POINTER(ot_prox_params), ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]),
+    ("ot_prox_set_input", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    ("ot_prox_step", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
+    ("ot_prox_solve", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ot_prox_result)]),
+    ("ot_prox_check_interval", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ot_prox_result)]),
+    ("ot_prox_step_timed", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_double)]),
+    ("ot_prox_evaluate", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ot_prox_result)]),
+    ("ot_prox_get_state", ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_void_p] * 6),
+    ("ot_prox_set_state", ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_void_p] * 6),
+    ("ot_prox_reset", ctypes.c_int, [ctypes.c_void_p]),
+    ("ot_prox_get_params", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ot_prox_params)]),
+    ("ot_prox_destroy", ctypes.c_int, [ctypes.c_void_p]),
+]
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load libotprox.so and declare its prototypes.  Raises if it is absent:
+    there is no fallback implementation."""
+    if not os.path.exists(path):
+        raise ImportError(f"libotprox.so is not built ({path}); run __graft_entry__.build() "
+                          "or python -m paper_1909_00149_gb300.build")
+    lib = ctypes.CDLL(path)
+    for name, res, args in PROTOTYPES:
+        if hasattr(lib, name):
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+    return lib

@@ -1,0 +1,95 @@
+// Internal declarations shared by the library's translation units.
+// Nothing here is part of the C ABI (include/otprox.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace otp {
+
+// ----------------------------------------------------------------- tiling
+// Tiled Algorithm 1 iteration: a CTA owns kTH rows x kTW columns of one
+// problem; 32 x 8 threads, each thread a float4 column group on kRPT rows.
+constexpr int kTW = 128;
+constexpr int kTH = 16;
+constexpr int kTX = 32;
+constexpr int kTY = 8;
+constexpr int kRPT = kTH / kTY;
+constexpr int kTiledThreads = kTX * kTY;
+// Resident kernel: one CTA iterates a whole problem in shared memory.
+constexpr int kResidentThreads = 512;
+constexpr size_t kResidentSmemCap = 200 * 1024;
+// Reduction quantities of a stopping check (FP64 sums):
+//  0 ||K(z')||^2      1 ||(z',a') - (z,a)||^2   2 ||(z',a')||^2
+//  3 ||M'||_{2,1}     4 sum |r'| (or r'^2)      5 sum_free (x' - p)^2
+//  6 ||p0||^2 + ||p1||^2                        7 non-finite count
+constexpr int kNumSums = 8;
+
+struct Geometry {
+  int B, H, W, Wp;         // Wp: row pitch in floats, multiple of 4
+  long long plane;         // H * Wp
+  int tiles_x, tiles_y;
+};
+
+struct IterCoeffs {
+  float tau1, tau2;
+  float cp, cx, ca;        // x-step: x' = max(cp p + cx x -/+ ca a, 0)
+  float mu_tau1;           // r-step threshold (p = 1)
+  float r2;                // r-step scale 1 / (1 + 2 mu tau1) (p = 2)
+  int iso;                 // 1: ||.||_{2,1}; 0: anisotropic l1
+  int pexp;                // 1 or 2
+};
+
+// One iteration's buffers.  M and a are ping-ponged (their neighbours are
+// read); x and r are updated in place (only their own pixel is read).
+struct StatePtrs {
+  const float* Mx_in;
+  const float* My_in;
+  const float* a_in;
+  float* Mx_out;
+  float* My_out;
+  float* a_out;
+  float* x0;
+  float* x1;
+  float* r;
+  const float* p0;
+  const float* p1;
+};
+
+struct CertCoeffs {
+  double mu, rho;
+  int iso, pexp, mode, balanced;
+};
+
+// ----------------------------------------------------------------- launchers
+int tiled_num_ctas(const Geometry& g);
+cudaError_t launch_prox_tiled(int mode, bool balanced, bool reduce, const Geometry& g,
+                              const IterCoeffs& c, const StatePtrs& s, double* partials,
+                              cudaStream_t st);
+
+size_t resident_smem_bytes(const Geometry& g, int mode, bool balanced);
+bool resident_fits(const Geometry& g, int mode, bool balanced);
+// Raise the kernel's dynamic shared-memory limit (once, outside any capture).
+cudaError_t prepare_prox_resident(int mode, bool balanced, const Geometry& g);
+// n_iter iterations in place on (Mx, My, a, x0, x1, r); the last one writes
+// per-problem partial sums to partials[B][kNumSums] when reduce_last.
+cudaError_t launch_prox_resident(int mode, bool balanced, const Geometry& g, const IterCoeffs& c,
+                                 float* Mx, float* My, float* a, float* x0, float* x1, float* r,
+                                 const float* p0, const float* p1, int n_iter, bool reduce_last,
+                                 double* partials, cudaStream_t st);
+
+// Sum partials[n][kNumSums] in a fixed order into out[kNumSums].
+cudaError_t launch_finalize_sums(const double* partials, int n, double* out, cudaStream_t st);
+
+// Evaluation of a state without iterating: the check sums of the state
+// itself (quantities 0, 2..7; 1 is 0) into partials, plus the certificate:
+// cert_partials[n][4] = {max ||D*a||, dual objective, primal-feasible
+// objective, unused} finalised into cert_out[4].
+int cert_num_blocks(const Geometry& g);
+cudaError_t launch_evaluate(const Geometry& g, const CertCoeffs& cc, const float* Mx,
+                            const float* My, const float* a, const float* x0, const float* x1,
+                            const float* r, const float* p0, const float* p1, double* partials,
+                            double* sums_out, double* cert_partials, double* cert_out,
+                            cudaStream_t st);
+
+}  // namespace otp

@@ -1,0 +1,758 @@
+// Algorithm 1 (Sec. III-B) of arXiv:1909.00149 on sm_103a.
+//
+// One iteration of Algorithm 1 (lines 3-7) is fused into a single pass over
+// HBM: each CTA reads the state of its tile once, computes
+//   M'  = shrink_{tau1}(M - tau1 D*(a))              (line 3, eq. Prox_UOT_M_prox)
+//   x'  = Pi_+((tau1 p + rho x -/+ rho tau1 a) / (rho + tau1))   (line 4)
+//   r'  = shrink^{l1}_{mu tau1}(r + tau1 a)          (line 5)
+//   a'  = a + tau2 (2 K(z') - K(z))                  (lines 6-7)
+// and writes the new state once.  K is linear, so 2K(z') - K(z) = K(2z' - z):
+// the kernel forms Mbar = 2M' - M in shared memory and applies D to it once.
+// D(Mbar) at a pixel needs Mbar one row up and one column left, so the CTA
+// recomputes M' on a one-sided halo (top row, left column) from a's tile
+// with a one-pixel ring.  Zero flux (Sec. III-A): Mx[H-1,:] = My[:,W-1] = 0.
+//
+// Layout: planes [B][H][Wp] float32, Wp = W rounded up to 4; padding
+// columns are kept at zero by every writer.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "otprox_internal.cuh"
+
+namespace otp {
+namespace {
+
+__device__ __forceinline__ float4 ld4(const float* p) { return __ldg(reinterpret_cast<const float4*>(p)); }
+__device__ __forceinline__ void st4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
+__device__ __forceinline__ float& comp(float4& v, int e) { return (&v.x)[e]; }
+__device__ __forceinline__ float compc(const float4& v, int e) { return (&v.x)[e]; }
+
+// Line 3 for one pixel: q = m - tau1 D*(a); vector (or componentwise) soft
+// shrinkage with threshold tau1.  ex / ey: the x / y edge exists here.
+__device__ __forceinline__ void flux_step(float mx, float my, float a_c, float a_down, float a_right,
+                                          bool ex, bool ey, const IterCoeffs& c, float& ox, float& oy) {
+  const float qx = ex ? fmaf(-c.tau1, a_c - a_down, mx) : 0.f;
+  const float qy = ey ? fmaf(-c.tau1, a_c - a_right, my) : 0.f;
+  if (c.iso) {
+    const float n2 = fmaf(qx, qx, qy * qy);
+    const float s = (n2 > c.tau1 * c.tau1) ? (1.f - c.tau1 * rsqrtf(n2)) : 0.f;
+    ox = qx * s;
+    oy = qy * s;
+  } else {
+    ox = copysignf(fmaxf(fabsf(qx) - c.tau1, 0.f), qx);
+    oy = copysignf(fmaxf(fabsf(qy) - c.tau1, 0.f), qy);
+  }
+}
+
+__device__ __forceinline__ float r_step(float r, float a, const IterCoeffs& c) {
+  const float q = fmaf(c.tau1, a, r);
+  if (c.pexp == 1) return copysignf(fmaxf(fabsf(q) - c.mu_tau1, 0.f), q);
+  return q * c.r2;
+}
+
+__device__ __forceinline__ float norm_term(float mx, float my, int iso) {
+  return iso ? sqrtf(fmaf(mx, mx, my * my)) : fabsf(mx) + fabsf(my);
+}
+
+__device__ __forceinline__ bool nonfinite(float v) { return !isfinite(v); }
+
+// Sum kNumSums doubles over the block; thread 0 writes them to out.
+template <int NT>
+__device__ void block_sum_store(double (&v)[kNumSums], double* out) {
+  constexpr int NW = NT / 32;
+  __shared__ double red[NW][kNumSums];
+  const int tid = threadIdx.x + threadIdx.y * blockDim.x;
+  const int lane = tid & 31, warp = tid >> 5;
+#pragma unroll
+  for (int k = 0; k < kNumSums; ++k) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+  }
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < kNumSums; ++k) red[warp][k] = v[k];
+  }
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int k = 0; k < kNumSums; ++k) {
+      double t = lane < NW ? red[lane][k] : 0.0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+      if (lane == 0) out[k] = t;
+    }
+  }
+}
+
+// ===================================================================== K1
+template <int MODE, bool BAL, bool RED>
+__global__ void __launch_bounds__(kTiledThreads, 2)
+prox_tiled_kernel(const Geometry G, const IterCoeffs C, const StatePtrs S, double* __restrict__ partials) {
+  constexpr int A4 = kTW / 4 + 2;                 // a tile: columns j0-4 .. j0+kTW+3
+  __shared__ __align__(16) float4 s_a[kTH + 2][A4];
+  __shared__ __align__(16) float s_mbx[kTH + 1][kTW];       // rows i0-1 .. i0+kTH-1
+  __shared__ __align__(16) float s_mby[kTH][kTW + 4];       // cols j0-4 .. j0+kTW-1
+  __shared__ __align__(16) float s_mnx[RED ? kTH + 1 : 1][RED ? kTW : 4];
+  __shared__ __align__(16) float s_mny[RED ? kTH : 1][RED ? kTW + 4 : 4];
+
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * kTX + tx;
+  int t = blockIdx.x;
+  const int bx = t % G.tiles_x;
+  t /= G.tiles_x;
+  const int by = t % G.tiles_y;
+  const int b = t / G.tiles_y;
+  const int i0 = by * kTH, j0 = bx * kTW;
+  const int H = G.H, W = G.W, Wp = G.Wp;
+  const long long base = (long long)b * G.plane;
+
+  // ---- stage a^k on the tile plus a one-pixel ring (float4-aligned: 4 extra columns each side)
+  for (int idx = tid; idx < (kTH + 2) * A4; idx += kTiledThreads) {
+    const int rr = idx / A4, c4 = idx - rr * A4;
+    const int gi = i0 - 1 + rr, gj = j0 - 4 + 4 * c4;
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (gi >= 0 && gi < H && gj >= 0 && gj < Wp) v = ld4(S.a_in + base + (long long)gi * Wp + gj);
+    s_a[rr][c4] = v;
+  }
+
+  // ---- own state
+  const int j = j0 + 4 * tx;
+  const bool colok = j < Wp;
+  const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+  float4 mx[kRPT], my[kRPT], x0[kRPT], x1[kRPT], rv[kRPT], p0[kRPT], p1[kRPT];
+#pragma unroll
+  for (int q = 0; q < kRPT; ++q) {
+    const int i = i0 + ty + kTY * q;
+    const bool ok = colok && i < H;
+    const long long off = base + (long long)i * Wp + j;
+    mx[q] = ok ? ld4(S.Mx_in + off) : z4;
+    my[q] = ok ? ld4(S.My_in + off) : z4;
+    p0[q] = ok ? ld4(S.p0 + off) : z4;
+    p1[q] = ok ? ld4(S.p1 + off) : z4;
+    x0[q] = (ok && MODE == 0) ? ld4(S.x0 + off) : p0[q];
+    x1[q] = (ok && MODE != 2) ? ld4(S.x1 + off) : p1[q];
+    rv[q] = (ok && !BAL) ? ld4(S.r + off) : z4;
+  }
+  // ---- halo flux M^k: row i0-1 (threads ty == 0), column j0-1 (threads tx == 0)
+  float4 hmx = z4, hmy = z4;
+  if (ty == 0 && i0 >= 1 && colok) {
+    const long long off = base + (long long)(i0 - 1) * Wp + j;
+    hmx = ld4(S.Mx_in + off);
+    hmy = ld4(S.My_in + off);
+  }
+  float lmx[kRPT], lmy[kRPT];
+#pragma unroll
+  for (int q = 0; q < kRPT; ++q) {
+    const int i = i0 + ty + kTY * q;
+    lmx[q] = lmy[q] = 0.f;
+    if (tx == 0 && j0 >= 1 && i < H) {
+      const long long off = base + (long long)i * Wp + (j0 - 1);
+      lmx[q] = __ldg(S.Mx_in + off);
+      lmy[q] = __ldg(S.My_in + off);
+    }
+  }
+  __syncthreads();
+
+  // ---- line 3 on own pixels
+  float4 nmx[kRPT], nmy[kRPT];
+#pragma unroll
+  for (int q = 0; q < kRPT; ++q) {
+    const int rr = ty + kTY * q + 1;
+    const int i = i0 + rr - 1;
+    const float4 ac = s_a[rr][tx + 1];
+    const float an = s_a[rr][tx + 2].x;
+    const float4 ad = s_a[rr + 1][tx + 1];
+    float4 bx4, by4;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int jj = j + e;
+      const bool in = (i < H) && (jj < W);
+      const float a_r = e < 3 ? compc(ac, e + 1) : an;
+      float ox, oy;
+      flux_step(compc(mx[q], e), compc(my[q], e), compc(ac, e), compc(ad, e), a_r,
+                in && i < H - 1, in && jj < W - 1, C, ox, oy);
+      comp(nmx[q], e) = ox;
+      comp(nmy[q], e) = oy;
+      comp(bx4, e) = 2.f * ox - compc(mx[q], e);
+      comp(by4, e) = 2.f * oy - compc(my[q], e);
+    }
+    *reinterpret_cast<float4*>(&s_mbx[rr][4 * tx]) = bx4;
+    *reinterpret_cast<float4*>(&s_mby[rr - 1][4 * tx + 4]) = by4;
+    if (RED) {
+      *reinterpret_cast<float4*>(&s_mnx[rr][4 * tx]) = nmx[q];
+      *reinterpret_cast<float4*>(&s_mny[rr - 1][4 * tx + 4]) = nmy[q];
+    }
+  }
+  // ---- halo row i0-1: only Mbar_x is consumed, both components enter the shrink
+  if (ty == 0) {
+    float4 bx4 = z4, nx4 = z4;
+    if (i0 >= 1) {
+      const int i = i0 - 1;
+      const float4 ac = s_a[0][tx + 1];
+      const float an = s_a[0][tx + 2].x;
+      const float4 ad = s_a[1][tx + 1];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int jj = j + e;
+        const bool in = jj < W;
+        const float a_r = e < 3 ? compc(ac, e + 1) : an;
+        float ox, oy;
+        flux_step(compc(hmx, e), compc(hmy, e), compc(ac, e), compc(ad, e), a_r, in && i < H - 1,
+                  in && jj < W - 1, C, ox, oy);
+        comp(bx4, e) = 2.f * ox - compc(hmx, e);
+        comp(nx4, e) = ox;
+      }
+    }
+    *reinterpret_cast<float4*>(&s_mbx[0][4 * tx]) = bx4;
+    if (RED) *reinterpret_cast<float4*>(&s_mnx[0][4 * tx]) = nx4;
+  }
+  // ---- halo column j0-1: only Mbar_y is consumed
+  if (tx == 0) {
+#pragma unroll
+    for (int q = 0; q < kRPT; ++q) {
+      const int rr = ty + kTY * q + 1;
+      const int i = i0 + rr - 1;
+      float by = 0.f, ny = 0.f;
+      if (j0 >= 1 && i < H) {
+        const float a_c = s_a[rr][0].w, a_r = s_a[rr][1].x, a_d = s_a[rr + 1][0].w;
+        float ox, oy;
+        flux_step(lmx[q], lmy[q], a_c, a_d, a_r, i < H - 1, true, C, ox, oy);
+        by = 2.f * oy - lmy[q];
+        ny = oy;
+      }
+      s_mby[rr - 1][3] = by;
+      if (RED) s_mny[rr - 1][3] = ny;
+    }
+  }
+  __syncthreads();
+
+  // ---- lines 4-7 on own pixels
+  double acc[kNumSums];
+#pragma unroll
+  for (int k = 0; k < kNumSums; ++k) acc[k] = 0.0;
+#pragma unroll
+  for (int q = 0; q < kRPT; ++q) {
+    const int rr = ty + kTY * q + 1;
+    const int i = i0 + rr - 1;
+    if (!(colok && i < H)) continue;
+    const float4 a4 = s_a[rr][tx + 1];
+    const float4 mbx = *reinterpret_cast<const float4*>(&s_mbx[rr][4 * tx]);
+    const float4 mbx_up = *reinterpret_cast<const float4*>(&s_mbx[rr - 1][4 * tx]);
+    const float4 mby = *reinterpret_cast<const float4*>(&s_mby[rr - 1][4 * tx + 4]);
+    const float mby_l = s_mby[rr - 1][4 * tx + 3];
+    float4 nx0, nx1, nr, na;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int jj = j + e;
+      const bool in = jj < W;
+      const float a = compc(a4, e);
+      float vx0 = compc(p0[q], e), vx1 = compc(p1[q], e);
+      if (MODE == 0) vx0 = fmaxf(fmaf(C.cp, compc(p0[q], e), fmaf(C.cx, compc(x0[q], e), C.ca * a)), 0.f);
+      if (MODE != 2) vx1 = fmaxf(fmaf(C.cp, compc(p1[q], e), fmaf(C.cx, compc(x1[q], e), -C.ca * a)), 0.f);
+      const float vr = BAL ? 0.f : r_step(compc(rv[q], e), a, C);
+      const float dmb = (compc(mbx, e) - compc(mbx_up, e)) +
+                        (compc(mby, e) - (e == 0 ? mby_l : compc(mby, e - 1)));
+      float bk = dmb - (2.f * vx0 - compc(x0[q], e)) + (2.f * vx1 - compc(x1[q], e));
+      if (!BAL) bk -= 2.f * vr - compc(rv[q], e);
+      const float va = fmaf(C.tau2, bk, a);
+      comp(nx0, e) = in ? vx0 : 0.f;
+      comp(nx1, e) = in ? vx1 : 0.f;
+      comp(nr, e) = in ? vr : 0.f;
+      comp(na, e) = in ? va : 0.f;
+      if (RED && in) {
+        const float nmxe = compc(nmx[q], e), nmye = compc(nmy[q], e);
+        const float nmx_up = s_mnx[rr - 1][4 * tx + e];
+        const float nmy_l = s_mny[rr - 1][4 * tx + 3 + e];
+        const float kz = (nmxe - nmx_up) + (nmye - nmy_l) - vx0 + vx1 - (BAL ? 0.f : vr);
+        acc[0] += (double)kz * kz;
+        const double d0 = nmxe - compc(mx[q], e), d1 = nmye - compc(my[q], e);
+        const double d2 = vx0 - compc(x0[q], e), d3 = vx1 - compc(x1[q], e);
+        const double d4 = vr - compc(rv[q], e), d5 = va - a;
+        acc[1] += d0 * d0 + d1 * d1 + d2 * d2 + d3 * d3 + d4 * d4 + d5 * d5;
+        acc[2] += (double)nmxe * nmxe + (double)nmye * nmye + (double)vx0 * vx0 + (double)vx1 * vx1 +
+                  (double)vr * vr + (double)va * va;
+        acc[3] += norm_term(nmxe, nmye, C.iso);
+        acc[4] += C.pexp == 1 ? fabs((double)vr) : (double)vr * vr;
+        if (MODE == 0) acc[5] += ((double)vx0 - compc(p0[q], e)) * ((double)vx0 - compc(p0[q], e));
+        if (MODE != 2) acc[5] += ((double)vx1 - compc(p1[q], e)) * ((double)vx1 - compc(p1[q], e));
+        acc[6] += (double)compc(p0[q], e) * compc(p0[q], e) + (double)compc(p1[q], e) * compc(p1[q], e);
+        acc[7] += (nonfinite(va) || nonfinite(nmxe) || nonfinite(nmye) || nonfinite(vx0) || nonfinite(vx1) ||
+                   nonfinite(vr)) ? 1.0 : 0.0;
+      }
+    }
+    const long long off = base + (long long)i * Wp + j;
+    st4(S.Mx_out + off, nmx[q]);
+    st4(S.My_out + off, nmy[q]);
+    st4(S.a_out + off, na);
+    if (MODE == 0) st4(S.x0 + off, nx0);
+    if (MODE != 2) st4(S.x1 + off, nx1);
+    if (!BAL) st4(S.r + off, nr);
+  }
+  if (RED) block_sum_store<kTiledThreads>(acc, partials + (size_t)blockIdx.x * kNumSums);
+}
+
+// ===================================================================== K2
+// Whole problem resident in shared memory, one CTA per problem, n_iter
+// iterations per launch.  Shared planes (pitch Wp): Mx, My, Mbx, Mby, a, r,
+// x0, x1, p0, p1 (frozen x and balanced r omitted).  Each iteration has two
+// phases separated by a barrier: (A) line 3 per pixel, M updated in place
+// and Mbar = 2M' - M stored; (B) lines 4-7 per pixel, a updated in place.
+struct ResidentLayout {
+  int nplanes;
+  int oMx, oMy, oMbx, oMby, oA, oR, oX0, oX1, oP0, oP1;
+};
+
+__host__ __device__ inline ResidentLayout resident_layout(int mode, bool bal) {
+  ResidentLayout L;
+  int n = 0;
+  L.oMx = n++;
+  L.oMy = n++;
+  L.oMbx = n++;
+  L.oMby = n++;
+  L.oA = n++;
+  L.oP0 = n++;
+  L.oP1 = n++;
+  L.oR = bal ? -1 : n++;
+  L.oX0 = mode == 0 ? n++ : -1;
+  L.oX1 = mode != 2 ? n++ : -1;
+  L.nplanes = n;
+  return L;
+}
+
+template <int MODE, bool BAL>
+__global__ void __launch_bounds__(kResidentThreads, 1)
+prox_resident_kernel(const Geometry G, const IterCoeffs C, float* __restrict__ gMx, float* __restrict__ gMy,
+                     float* __restrict__ ga, float* __restrict__ gx0, float* __restrict__ gx1,
+                     float* __restrict__ gr, const float* __restrict__ gp0, const float* __restrict__ gp1,
+                     int n_iter, int reduce_last, double* __restrict__ partials) {
+  extern __shared__ __align__(16) float smem[];
+  const ResidentLayout L = resident_layout(MODE, BAL);
+  const int H = G.H, W = G.W, Wp = G.Wp;
+  const int P = H * Wp;
+  const int P4 = P / 4;
+  const int W4 = Wp / 4;
+  const long long base = (long long)blockIdx.x * G.plane;
+  float* sMx = smem + (size_t)L.oMx * P;
+  float* sMy = smem + (size_t)L.oMy * P;
+  float* sMbx = smem + (size_t)L.oMbx * P;
+  float* sMby = smem + (size_t)L.oMby * P;
+  float* sA = smem + (size_t)L.oA * P;
+  float* sP0 = smem + (size_t)L.oP0 * P;
+  float* sP1 = smem + (size_t)L.oP1 * P;
+  float* sR = BAL ? nullptr : smem + (size_t)L.oR * P;
+  float* sX0 = MODE == 0 ? smem + (size_t)L.oX0 * P : sP0;
+  float* sX1 = MODE != 2 ? smem + (size_t)L.oX1 * P : sP1;
+  const int tid = threadIdx.x;
+
+  for (int g = tid; g < P4; g += kResidentThreads) {
+    const long long off = base + 4LL * g;
+    st4(sMx + 4 * g, ld4(gMx + off));
+    st4(sMy + 4 * g, ld4(gMy + off));
+    st4(sA + 4 * g, ld4(ga + off));
+    st4(sP0 + 4 * g, ld4(gp0 + off));
+    st4(sP1 + 4 * g, ld4(gp1 + off));
+    if (!BAL) st4(sR + 4 * g, ld4(gr + off));
+    if (MODE == 0) st4(sX0 + 4 * g, ld4(gx0 + off));
+    if (MODE != 2) st4(sX1 + 4 * g, ld4(gx1 + off));
+  }
+  __syncthreads();
+
+  double acc[kNumSums];
+#pragma unroll
+  for (int k = 0; k < kNumSums; ++k) acc[k] = 0.0;
+
+  for (int it = 0; it < n_iter; ++it) {
+    const bool red = reduce_last && (it == n_iter - 1);
+    // phase A: line 3
+    for (int g = tid; g < P4; g += kResidentThreads) {
+      const int i = g / W4, j = 4 * (g - i * W4);
+      const int o = i * Wp + j;
+      const float4 m4x = *reinterpret_cast<const float4*>(sMx + o);
+      const float4 m4y = *reinterpret_cast<const float4*>(sMy + o);
+      const float4 ac = *reinterpret_cast<const float4*>(sA + o);
+      const float an = (j + 4 < Wp) ? sA[o + 4] : 0.f;
+      const float4 ad = (i + 1 < H) ? *reinterpret_cast<const float4*>(sA + o + Wp) : make_float4(0.f, 0.f, 0.f, 0.f);
+      float4 nx, ny, bx, by;
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int jj = j + e;
+        const bool in = jj < W;
+        const float a_r = e < 3 ? compc(ac, e + 1) : an;
+        float ox, oy;
+        flux_step(compc(m4x, e), compc(m4y, e), compc(ac, e), compc(ad, e), a_r, in && i < H - 1,
+                  in && jj < W - 1, C, ox, oy);
+        comp(nx, e) = ox;
+        comp(ny, e) = oy;
+        comp(bx, e) = 2.f * ox - compc(m4x, e);
+        comp(by, e) = 2.f * oy - compc(m4y, e);
+        if (red && in) {
+          const double d0 = ox - compc(m4x, e), d1 = oy - compc(m4y, e);
+          acc[1] += d0 * d0 + d1 * d1;
+          acc[2] += (double)ox * ox + (double)oy * oy;
+          acc[3] += norm_term(ox, oy, C.iso);
+          acc[7] += (nonfinite(ox) || nonfinite(oy)) ? 1.0 : 0.0;
+        }
+      }
+      st4(sMx + o, nx);
+      st4(sMy + o, ny);
+      st4(sMbx + o, bx);
+      st4(sMby + o, by);
+    }
+    __syncthreads();
+    // phase B: lines 4-7
+    for (int g = tid; g < P4; g += kResidentThreads) {
+      const int i = g / W4, j = 4 * (g - i * W4);
+      const int o = i * Wp + j;
+      const float4 a4 = *reinterpret_cast<const float4*>(sA + o);
+      const float4 p04 = *reinterpret_cast<const float4*>(sP0 + o);
+      const float4 p14 = *reinterpret_cast<const float4*>(sP1 + o);
+      const float4 x04 = *reinterpret_cast<const float4*>(sX0 + o);
+      const float4 x14 = *reinterpret_cast<const float4*>(sX1 + o);
+      const float4 r4 = BAL ? make_float4(0.f, 0.f, 0.f, 0.f) : *reinterpret_cast<const float4*>(sR + o);
+      const float4 mbx = *reinterpret_cast<const float4*>(sMbx + o);
+      const float4 mbx_up = i > 0 ? *reinterpret_cast<const float4*>(sMbx + o - Wp) : make_float4(0.f, 0.f, 0.f, 0.f);
+      const float4 mby = *reinterpret_cast<const float4*>(sMby + o);
+      const float mby_l = j > 0 ? sMby[o - 1] : 0.f;
+      float4 nx0, nx1, nr, na;
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int jj = j + e;
+        const bool in = jj < W;
+        const float a = compc(a4, e);
+        float vx0 = compc(p04, e), vx1 = compc(p14, e);
+        if (MODE == 0) vx0 = fmaxf(fmaf(C.cp, compc(p04, e), fmaf(C.cx, compc(x04, e), C.ca * a)), 0.f);
+        if (MODE != 2) vx1 = fmaxf(fmaf(C.cp, compc(p14, e), fmaf(C.cx, compc(x14, e), -C.ca * a)), 0.f);
+        const float vr = BAL ? 0.f : r_step(compc(r4, e), a, C);
+        const float dmb = (compc(mbx, e) - compc(mbx_up, e)) +
+                          (compc(mby, e) - (e == 0 ? mby_l : compc(mby, e - 1)));
+        float bk = dmb - (2.f * vx0 - compc(x04, e)) + (2.f * vx1 - compc(x14, e));
+        if (!BAL) bk -= 2.f * vr - compc(r4, e);
+        const float va = fmaf(C.tau2, bk, a);
+        comp(nx0, e) = in ? vx0 : 0.f;
+        comp(nx1, e) = in ? vx1 : 0.f;
+        comp(nr, e) = in ? vr : 0.f;
+        comp(na, e) = in ? va : 0.f;
+        if (red && in) {
+          const float mxn = sMx[o + e], myn = sMy[o + e];
+          const float mx_up = i > 0 ? sMx[o + e - Wp] : 0.f;
+          const float my_l = (j + e) > 0 ? sMy[o + e - 1] : 0.f;
+          const float kz = (mxn - mx_up) + (myn - my_l) - vx0 + vx1 - (BAL ? 0.f : vr);
+          acc[0] += (double)kz * kz;
+          const double d2 = vx0 - compc(x04, e), d3 = vx1 - compc(x14, e);
+          const double d4 = vr - compc(r4, e), d5 = va - a;
+          acc[1] += d2 * d2 + d3 * d3 + d4 * d4 + d5 * d5;
+          acc[2] += (double)vx0 * vx0 + (double)vx1 * vx1 + (double)vr * vr + (double)va * va;
+          acc[4] += C.pexp == 1 ? fabs((double)vr) : (double)vr * vr;
+          if (MODE == 0) acc[5] += ((double)vx0 - compc(p04, e)) * ((double)vx0 - compc(p04, e));
+          if (MODE != 2) acc[5] += ((double)vx1 - compc(p14, e)) * ((double)vx1 - compc(p14, e));
+          acc[6] += (double)compc(p04, e) * compc(p04, e) + (double)compc(p14, e) * compc(p14, e);
+          acc[7] += (nonfinite(va) || nonfinite(vx0) || nonfinite(vx1) || nonfinite(vr)) ? 1.0 : 0.0;
+        }
+      }
+      st4(sA + o, na);
+      if (MODE == 0) st4(sX0 + o, nx0);
+      if (MODE != 2) st4(sX1 + o, nx1);
+      if (!BAL) st4(sR + o, nr);
+    }
+    __syncthreads();
+  }
+
+  for (int g = tid; g < P4; g += kResidentThreads) {
+    const long long off = base + 4LL * g;
+    st4(gMx + off, *reinterpret_cast<const float4*>(sMx + 4 * g));
+    st4(gMy + off, *reinterpret_cast<const float4*>(sMy + 4 * g));
+    st4(ga + off, *reinterpret_cast<const float4*>(sA + 4 * g));
+    if (!BAL) st4(gr + off, *reinterpret_cast<const float4*>(sR + 4 * g));
+    if (MODE == 0) st4(gx0 + off, *reinterpret_cast<const float4*>(sX0 + 4 * g));
+    if (MODE != 2) st4(gx1 + off, *reinterpret_cast<const float4*>(sX1 + 4 * g));
+  }
+  if (reduce_last && n_iter > 0) {
+    __syncthreads();
+    block_sum_store<kResidentThreads>(acc, partials + (size_t)blockIdx.x * kNumSums);
+  }
+}
+
+// ===================================================================== K3
+// Fixed-order FP64 sum of per-CTA partials (deterministic: no atomics).
+template <int NQ>
+__global__ void __launch_bounds__(256) finalize_kernel(const double* __restrict__ partials, int n,
+                                                       unsigned max_mask, double* __restrict__ out) {
+  __shared__ double red[8][NQ];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  double v[NQ];
+#pragma unroll
+  for (int k = 0; k < NQ; ++k) v[k] = 0.0;
+  for (int p = tid; p < n; p += 256) {
+#pragma unroll
+    for (int k = 0; k < NQ; ++k) {
+      const double x = partials[(size_t)p * NQ + k];
+      v[k] = ((max_mask >> k) & 1u) ? fmax(v[k], x) : v[k] + x;
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < NQ; ++k) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double y = __shfl_down_sync(0xffffffffu, v[k], o);
+      v[k] = ((max_mask >> k) & 1u) ? fmax(v[k], y) : v[k] + y;
+    }
+    if (lane == 0) red[warp][k] = v[k];
+  }
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int k = 0; k < NQ; ++k) {
+      double t = lane < 8 ? red[lane][k] : 0.0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const double y = __shfl_down_sync(0xffffffffu, t, o);
+        t = ((max_mask >> k) & 1u) ? fmax(t, y) : t + y;
+      }
+      if (lane == 0) out[k] = t;
+    }
+  }
+}
+
+// ===================================================================== evaluation
+// Check sums and duality-gap certificate of a state (not on the hot loop).
+// Pass 1: sums 0, 2..7 of the state itself and max_i ||(D* a)_i||.
+// Pass 2: dual objective at a_bar = clip(a / max(1, max||D*a||), -mu, mu) and
+// the objective of the feasible primal point r' = D(M) + A x.
+constexpr int kCertThreads = 256;
+constexpr int kCertQ = 4;
+
+__device__ __forceinline__ float at(const float* p, long long base, int i, int j, int Wp) {
+  return p[base + (long long)i * Wp + j];
+}
+
+__global__ void __launch_bounds__(kCertThreads)
+eval_pass1_kernel(const Geometry G, const CertCoeffs cc, const float* __restrict__ Mx, const float* __restrict__ My,
+                  const float* __restrict__ a, const float* __restrict__ x0, const float* __restrict__ x1,
+                  const float* __restrict__ r, const float* __restrict__ p0, const float* __restrict__ p1,
+                  double* __restrict__ partials, double* __restrict__ cpart) {
+  const long long total = (long long)G.B * G.H * G.W;
+  double acc[kNumSums];
+#pragma unroll
+  for (int k = 0; k < kNumSums; ++k) acc[k] = 0.0;
+  double nmax = 0.0;
+  const int H = G.H, W = G.W, Wp = G.Wp;
+  for (long long idx = blockIdx.x * (long long)kCertThreads + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * kCertThreads) {
+    const int jj = (int)(idx % W);
+    const long long t = idx / W;
+    const int i = (int)(t % H);
+    const long long b = t / H;
+    const long long base = b * G.plane;
+    const double mx = at(Mx, base, i, jj, Wp), my = at(My, base, i, jj, Wp);
+    const double mx_up = i > 0 ? at(Mx, base, i - 1, jj, Wp) : 0.0;
+    const double my_l = jj > 0 ? at(My, base, i, jj - 1, Wp) : 0.0;
+    const double vp0 = at(p0, base, i, jj, Wp), vp1 = at(p1, base, i, jj, Wp);
+    const double vx0 = cc.mode == 0 ? at(x0, base, i, jj, Wp) : vp0;
+    const double vx1 = cc.mode != 2 ? at(x1, base, i, jj, Wp) : vp1;
+    const double vr = cc.balanced ? 0.0 : at(r, base, i, jj, Wp);
+    const double va = at(a, base, i, jj, Wp);
+    const double kz = (mx - mx_up) + (my - my_l) - vx0 + vx1 - vr;
+    acc[0] += kz * kz;
+    acc[2] += mx * mx + my * my + vx0 * vx0 + vx1 * vx1 + vr * vr + va * va;
+    acc[3] += cc.iso ? sqrt(mx * mx + my * my) : fabs(mx) + fabs(my);
+    acc[4] += cc.pexp == 1 ? fabs(vr) : vr * vr;
+    if (cc.mode == 0) acc[5] += (vx0 - vp0) * (vx0 - vp0);
+    if (cc.mode != 2) acc[5] += (vx1 - vp1) * (vx1 - vp1);
+    acc[6] += vp0 * vp0 + vp1 * vp1;
+    acc[7] += (isfinite(mx) && isfinite(my) && isfinite(va) && isfinite(vx0) && isfinite(vx1) && isfinite(vr)) ? 0.0 : 1.0;
+    const double gx = i < H - 1 ? va - at(a, base, i + 1, jj, Wp) : 0.0;
+    const double gy = jj < W - 1 ? va - at(a, base, i, jj + 1, Wp) : 0.0;
+    const double n = cc.iso ? sqrt(gx * gx + gy * gy) : fmax(fabs(gx), fabs(gy));
+    nmax = fmax(nmax, n);
+  }
+  block_sum_store<kCertThreads>(acc, partials + (size_t)blockIdx.x * kNumSums);
+  // block max of nmax
+  __shared__ double smax[kCertThreads / 32];
+  for (int o = 16; o > 0; o >>= 1) nmax = fmax(nmax, __shfl_down_sync(0xffffffffu, nmax, o));
+  if ((threadIdx.x & 31) == 0) smax[threadIdx.x >> 5] = nmax;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double m = 0.0;
+    for (int w = 0; w < kCertThreads / 32; ++w) m = fmax(m, smax[w]);
+    cpart[(size_t)blockIdx.x * kCertQ + 0] = m;
+  }
+}
+
+__global__ void __launch_bounds__(kCertThreads)
+eval_pass2_kernel(const Geometry G, const CertCoeffs cc, const float* __restrict__ Mx, const float* __restrict__ My,
+                  const float* __restrict__ a, const float* __restrict__ x0, const float* __restrict__ x1,
+                  const float* __restrict__ p0, const float* __restrict__ p1, const double* __restrict__ cert_out,
+                  double* __restrict__ cpart) {
+  const long long total = (long long)G.B * G.H * G.W;
+  const double scale = fmax(1.0, cert_out[0]);
+  double dual = 0.0, primal = 0.0;
+  const int H = G.H, W = G.W, Wp = G.Wp;
+  for (long long idx = blockIdx.x * (long long)kCertThreads + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * kCertThreads) {
+    const int jj = (int)(idx % W);
+    const long long t = idx / W;
+    const int i = (int)(t % H);
+    const long long b = t / H;
+    const long long base = b * G.plane;
+    double ab = at(a, base, i, jj, Wp) / scale;
+    if (!cc.balanced && cc.pexp == 1) ab = fmin(fmax(ab, -cc.mu), cc.mu);
+    const double vp0 = at(p0, base, i, jj, Wp), vp1 = at(p1, base, i, jj, Wp);
+    const double vx0 = cc.mode == 0 ? at(x0, base, i, jj, Wp) : vp0;
+    const double vx1 = cc.mode != 2 ? at(x1, base, i, jj, Wp) : vp1;
+    // dual: x0 enters K with -1, x1 with +1
+    if (cc.mode == 0) {
+      const double c = -ab, xs = fmax(vp0 - cc.rho * c, 0.0);
+      dual += (xs - vp0) * (xs - vp0) / (2.0 * cc.rho) + c * xs;
+    } else {
+      dual += -ab * vp0;
+    }
+    if (cc.mode != 2) {
+      const double c = ab, xs = fmax(vp1 - cc.rho * c, 0.0);
+      dual += (xs - vp1) * (xs - vp1) / (2.0 * cc.rho) + c * xs;
+    } else {
+      dual += ab * vp1;
+    }
+    if (!cc.balanced && cc.pexp == 2) dual -= ab * ab / (4.0 * cc.mu);
+    // feasible primal
+    const double mx = at(Mx, base, i, jj, Wp), my = at(My, base, i, jj, Wp);
+    const double mx_up = i > 0 ? at(Mx, base, i - 1, jj, Wp) : 0.0;
+    const double my_l = jj > 0 ? at(My, base, i, jj - 1, Wp) : 0.0;
+    const double rp = (mx - mx_up) + (my - my_l) - vx0 + vx1;
+    primal += cc.iso ? sqrt(mx * mx + my * my) : fabs(mx) + fabs(my);
+    if (!cc.balanced) primal += cc.mu * (cc.pexp == 1 ? fabs(rp) : rp * rp);
+    if (cc.mode == 0) primal += (vx0 - vp0) * (vx0 - vp0) / (2.0 * cc.rho);
+    if (cc.mode != 2) primal += (vx1 - vp1) * (vx1 - vp1) / (2.0 * cc.rho);
+  }
+  __shared__ double s[2][kCertThreads / 32];
+  for (int o = 16; o > 0; o >>= 1) {
+    dual += __shfl_down_sync(0xffffffffu, dual, o);
+    primal += __shfl_down_sync(0xffffffffu, primal, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    s[0][threadIdx.x >> 5] = dual;
+    s[1][threadIdx.x >> 5] = primal;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double d = 0.0, p = 0.0;
+    for (int w = 0; w < kCertThreads / 32; ++w) {
+      d += s[0][w];
+      p += s[1][w];
+    }
+    cpart[(size_t)blockIdx.x * kCertQ + 1] = d;
+    cpart[(size_t)blockIdx.x * kCertQ + 2] = p;
+    cpart[(size_t)blockIdx.x * kCertQ + 3] = 0.0;
+  }
+}
+
+template <int MODE, bool BAL, bool RED>
+cudaError_t launch_tiled_t(const Geometry& g, const IterCoeffs& c, const StatePtrs& s, double* partials,
+                           cudaStream_t st) {
+  const dim3 block(kTX, kTY);
+  prox_tiled_kernel<MODE, BAL, RED><<<tiled_num_ctas(g), block, 0, st>>>(g, c, s, partials);
+  return cudaGetLastError();
+}
+
+template <int MODE, bool BAL>
+cudaError_t prepare_resident_t(const Geometry& g) {
+  return cudaFuncSetAttribute(prox_resident_kernel<MODE, BAL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)resident_smem_bytes(g, MODE, BAL));
+}
+
+template <int MODE, bool BAL>
+cudaError_t launch_resident_t(const Geometry& g, const IterCoeffs& c, float* Mx, float* My, float* a, float* x0,
+                              float* x1, float* r, const float* p0, const float* p1, int n_iter, bool reduce_last,
+                              double* partials, cudaStream_t st) {
+  const size_t smem = resident_smem_bytes(g, MODE, BAL);
+  prox_resident_kernel<MODE, BAL><<<g.B, kResidentThreads, smem, st>>>(g, c, Mx, My, a, x0, x1, r, p0, p1, n_iter,
+                                                                        reduce_last ? 1 : 0, partials);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+int tiled_num_ctas(const Geometry& g) { return g.B * g.tiles_x * g.tiles_y; }
+
+cudaError_t launch_prox_tiled(int mode, bool balanced, bool reduce, const Geometry& g, const IterCoeffs& c,
+                              const StatePtrs& s, double* partials, cudaStream_t st) {
+#define OTP_TILED(M, BL)                                                                     \
+  if (mode == M && balanced == BL)                                                           \
+    return reduce ? launch_tiled_t<M, BL, true>(g, c, s, partials, st)                       \
+                  : launch_tiled_t<M, BL, false>(g, c, s, partials, st);
+  OTP_TILED(0, false)
+  OTP_TILED(0, true)
+  OTP_TILED(1, false)
+  OTP_TILED(1, true)
+  OTP_TILED(2, false)
+  OTP_TILED(2, true)
+#undef OTP_TILED
+  return cudaErrorInvalidValue;
+}
+
+size_t resident_smem_bytes(const Geometry& g, int mode, bool balanced) {
+  const ResidentLayout L = resident_layout(mode, balanced);
+  return (size_t)L.nplanes * (size_t)g.H * (size_t)g.Wp * sizeof(float);
+}
+
+bool resident_fits(const Geometry& g, int mode, bool balanced) {
+  return resident_smem_bytes(g, mode, balanced) <= kResidentSmemCap;
+}
+
+cudaError_t launch_prox_resident(int mode, bool balanced, const Geometry& g, const IterCoeffs& c, float* Mx,
+                                 float* My, float* a, float* x0, float* x1, float* r, const float* p0,
+                                 const float* p1, int n_iter, bool reduce_last, double* partials,
+                                 cudaStream_t st) {
+#define OTP_RES(M, BL) \
+  if (mode == M && balanced == BL) return launch_resident_t<M, BL>(g, c, Mx, My, a, x0, x1, r, p0, p1, n_iter, reduce_last, partials, st);
+  OTP_RES(0, false)
+  OTP_RES(0, true)
+  OTP_RES(1, false)
+  OTP_RES(1, true)
+  OTP_RES(2, false)
+  OTP_RES(2, true)
+#undef OTP_RES
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t prepare_prox_resident(int mode, bool balanced, const Geometry& g) {
+#define OTP_PREP(M, BL) \
+  if (mode == M && balanced == BL) return prepare_resident_t<M, BL>(g);
+  OTP_PREP(0, false)
+  OTP_PREP(0, true)
+  OTP_PREP(1, false)
+  OTP_PREP(1, true)
+  OTP_PREP(2, false)
+  OTP_PREP(2, true)
+#undef OTP_PREP
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_finalize_sums(const double* partials, int n, double* out, cudaStream_t st) {
+  finalize_kernel<kNumSums><<<1, 256, 0, st>>>(partials, n, 0u, out);
+  return cudaGetLastError();
+}
+
+int cert_num_blocks(const Geometry& g) {
+  const long long total = (long long)g.B * g.H * g.W;
+  long long nb = (total + kCertThreads - 1) / kCertThreads;
+  if (nb > 152 * 8) nb = 152 * 8;
+  if (nb < 1) nb = 1;
+  return (int)nb;
+}
+
+cudaError_t launch_evaluate(const Geometry& g, const CertCoeffs& cc, const float* Mx, const float* My,
+                            const float* a, const float* x0, const float* x1, const float* r, const float* p0,
+                            const float* p1, double* partials, double* sums_out, double* cert_partials,
+                            double* cert_out, cudaStream_t st) {
+  const int nb = cert_num_blocks(g);
+  eval_pass1_kernel<<<nb, kCertThreads, 0, st>>>(g, cc, Mx, My, a, x0, x1, r, p0, p1, partials, cert_partials);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  finalize_kernel<kNumSums><<<1, 256, 0, st>>>(partials, nb, 0u, sums_out);
+  finalize_kernel<kCertQ><<<1, 256, 0, st>>>(cert_partials, nb, 1u, cert_out);
+  eval_pass2_kernel<<<nb, kCertThreads, 0, st>>>(g, cc, Mx, My, a, x0, x1, p0, p1, cert_out, cert_partials);
+  finalize_kernel<kCertQ><<<1, 256, 0, st>>>(cert_partials, nb, 1u, cert_out);
+  return cudaGetLastError();
+}
+
+}  // namespace otp
