@@ -49,7 +49,7 @@ def measured_peaks() -> dict:
 
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
-    with open(os.path.join(ROOT, "paper_1909_00149_gb300", "csrc", "prox_kernels.cu"), "rb") as f:
+    with open(os.path.join(ROOT, "paper_1909_00149_gb300", "csrc", "prox_tma.cu"), "rb") as f:
         h.update(f.read())
     return h.hexdigest()[:16]
 
@@ -57,7 +57,7 @@ def kernel_source_hash() -> str:
 def ncu_traffic(kernel_tag: str) -> float | None:
     """DRAM bytes per launch of the tiled iteration kernel from the committed
     ncu summary, if it was taken on the current kernel source."""
-    path = os.path.join(ROOT, "profiles", "prox_tiled_63x256x256.md")
+    path = os.path.join(ROOT, "profiles", "prox_tma_63x256x256.md")
     if not os.path.exists(path):
         return None
     src_hash, traffic = None, None
@@ -127,7 +127,7 @@ def prox_inputs(rank: int):
     return np.ascontiguousarray(v[:-1]), np.ascontiguousarray(v[1:])
 
 
-PROX_KW = dict(mu=3.0, rho=0.01, kernel="tiled", use_graph=True, check_every=ITERS_PER_STEP)
+PROX_KW = dict(mu=3.0, rho=0.01, kernel="tma", use_graph=True, check_every=ITERS_PER_STEP)
 
 
 def run_ours(args, rank, world, local_rank):
@@ -213,11 +213,11 @@ def run_ours(args, rank, world, local_rank):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": "prox_63_pairs_256x256 (64-frame 256x256 blob video, Algorithm 1)",
                    "B": B, "H": H, "W": W, "iters_per_step": ITERS_PER_STEP, "mu": PROX_KW["mu"],
-                   "rho": PROX_KW["rho"], "kernel": "tiled", "cuda_graph": True,
+                   "rho": PROX_KW["rho"], "kernel": PROX_KW["kernel"], "cuda_graph": True,
                    "l2": "inputs larger than L2 (11 state planes = %.0f MB; 231 MB moved per iteration)" % (11 * px * 4 / 1e6)},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                      "frac": achieved / peaks["hbm_gbs"], "traffic": ncu_traffic("nored"),
-                     "kernel": "prox_tiled_kernel (Algorithm 1 iteration, no reduction)",
+                     "kernel": "prox_tma_kernel (Algorithm 1 iteration, no reduction)",
                      "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_ms": k_ms,
                      "peak_source": peaks["source"] + " copy bandwidth (of measured)"},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 2 * px * 4, "d2h_bytes_per_step": 8 * 8},

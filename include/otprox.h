@@ -63,10 +63,14 @@ extern "C" {
 #define OT_NORM_ISO   0
 #define OT_NORM_ANISO 1
 /* Kernel choice for Algorithm 1: AUTO picks RESIDENT when one problem's
- * state fits in one CTA's shared memory, TILED otherwise. */
+ * state fits in one CTA's shared memory, TMA otherwise.
+ *  TILED    -- one CTA per 16 x 128 tile, loads through the L1 path;
+ *  RESIDENT -- one CTA per problem, all iterations of a call in shared memory;
+ *  TMA      -- persistent CTAs (one per SM) fed by a multi-stage TMA pipeline. */
 #define OT_KERNEL_AUTO     0
 #define OT_KERNEL_TILED    1
 #define OT_KERNEL_RESIDENT 2
+#define OT_KERNEL_TMA      3
 
 typedef struct ot_prox* ot_prox_t;
 

@@ -19,7 +19,7 @@ STATUS_NAMES = {0: "OT_OK", -1: "OT_EINVAL", -2: "OT_ENOMEM", -3: "OT_ECUDA", -4
 
 MODES = {"prox": 0, "fixed_first": 1, "eval": 2}
 NORMS = {"iso": 0, "aniso": 1}
-KERNELS = {"auto": 0, "tiled": 1, "resident": 2}
+KERNELS = {"auto": 0, "tiled": 1, "resident": 2, "tma": 3}
 
 c_float_p = ctypes.POINTER(ctypes.c_float)
 c_double_p = ctypes.POINTER(ctypes.c_double)

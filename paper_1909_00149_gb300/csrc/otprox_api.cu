@@ -57,6 +57,11 @@ struct ot_prox {
   float* p1;
   int cur;                   // ping-pong index of the current M, a
   bool resident;
+  bool tma;
+  int tma_grid;              // persistent CTAs (one per SM, at most one per tile)
+  TmaMaps maps[2];           // by ping-pong parity of the input M, a
+  int* derr;                 // device error flag (bounded waits)
+  int* herr;                 // pinned host mirror
   double* partials;          // [max(n_ctas, n_cert)][kNumSums]
   double* cert_partials;     // [n_cert][4]
   double* dsums;             // device: [kNumSums] sums + [4] certificate
@@ -138,11 +143,16 @@ static cudaError_t enqueue_iterations(ot_prox* h, int parity, int n, bool reduce
   }
   for (int k = 0; k < n; ++k) {
     const bool red = reduce && (k == n - 1);
-    e = launch_prox_tiled(mode, bal, red, h->G, h->C, state_ptrs(h, parity), h->partials, h->stream);
+    if (h->tma)
+      e = launch_prox_tma(mode, bal, red, h->maps[parity], h->G, h->C, state_ptrs(h, parity), h->partials, h->derr,
+                          h->tma_grid, h->stream);
+    else
+      e = launch_prox_tiled(mode, bal, red, h->G, h->C, state_ptrs(h, parity), h->partials, h->stream);
     if (e != cudaSuccess) return e;
     parity ^= 1;
   }
-  if (reduce && n > 0) e = launch_finalize_sums(h->partials, tiled_num_ctas(h->G), h->dsums, h->stream);
+  if (reduce && n > 0)
+    e = launch_finalize_sums(h->partials, h->tma ? h->tma_grid : tiled_num_ctas(h->G), h->dsums, h->stream);
   return e;
 }
 
@@ -161,6 +171,7 @@ static int run_check_interval(ot_prox* h, int n) {
       cudaError_t e = enqueue_iterations(h, parity, n, true);
       if (e == cudaSuccess)
         e = cudaMemcpyAsync(h->hsums, h->dsums, kNumSums * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(h->herr, h->derr, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
       cudaError_t e2 = cudaStreamEndCapture(h->stream, &g);
       if (e != cudaSuccess) {
         if (g) cudaGraphDestroy(g);
@@ -177,10 +188,20 @@ static int run_check_interval(ot_prox* h, int n) {
     OT_CUDA(enqueue_iterations(h, parity, n, true), "launching Algorithm 1 iterations");
     OT_CUDA(cudaMemcpyAsync(h->hsums, h->dsums, kNumSums * sizeof(double), cudaMemcpyDeviceToHost, h->stream),
             "copying check sums");
+    OT_CUDA(cudaMemcpyAsync(h->herr, h->derr, sizeof(int), cudaMemcpyDeviceToHost, h->stream), "copying the error flag");
   }
   h->cur = parity_after(h, parity, n);
   OT_CUDA(cudaStreamSynchronize(h->stream), "synchronising after a check interval");
+  if (*h->herr) return fail(OT_ETIMEOUT, "a bounded device wait expired in the iteration kernel");
   return OT_OK;
+}
+
+// Any NaN/Inf in the iterates or the inputs shows in one of the check sums.
+static bool sums_nonfinite(const double* s) {
+  if (s[7] > 0) return true;
+  for (int k = 0; k < 7; ++k)
+    if (!isfinite(s[k])) return true;
+  return false;
 }
 
 static void fill_result_from_sums(const ot_prox* h, const double* s, ot_prox_result* res) {
@@ -215,7 +236,7 @@ static int evaluate_into(ot_prox* h, ot_prox_result* res) {
   res->dual_obj = s[kNumSums + 1];
   res->primal_feasible = s[kNumSums + 2];
   res->rel_gap = (res->primal_feasible - res->dual_obj) / fmax(fabs(res->primal_feasible), 1e-30);
-  if (s[7] > 0 || !isfinite(s[0]) || !isfinite(s[2])) return OT_ENONFINITE;
+  if (sums_nonfinite(s)) return OT_ENONFINITE;
   return OT_OK;
 }
 
@@ -251,7 +272,7 @@ int ot_prox_create(const ot_prox_params* params, void* cuda_stream, ot_prox_t* o
   if (!(p.tol >= 0) || !isfinite(p.tol)) return fail(OT_EINVAL, "ot_prox_create: tol must be >= 0");
   if (p.max_iter < 0) return fail(OT_EINVAL, "ot_prox_create: max_iter must be >= 0");
   if (p.check_every < 1) return fail(OT_EINVAL, "ot_prox_create: check_every must be >= 1");
-  if (p.kernel < 0 || p.kernel > 2) return fail(OT_EINVAL, "ot_prox_create: unknown kernel %d", p.kernel);
+  if (p.kernel < 0 || p.kernel > 3) return fail(OT_EINVAL, "ot_prox_create: unknown kernel %d", p.kernel);
   if (!isfinite(p.tau1) || !isfinite(p.tau2)) return fail(OT_EINVAL, "ot_prox_create: steps must be finite");
   // Theorem 1: tau1 tau2 < 1 / (lambda_max + n_id)
   const double L = ot_lambda_max(p.H, p.W) + (double)ot_n_identity_blocks(p.mode, p.balanced);
@@ -278,12 +299,15 @@ int ot_prox_create(const ot_prox_params* params, void* cuda_stream, ot_prox_t* o
   if ((double)plane_elems * nplanes * 4.0 > 2.6e11) return fail(OT_ENOMEM, "ot_prox_create: state would exceed device memory");
 
   const bool fits = resident_fits(G, p.mode, p.balanced != 0);
-  bool resident = false;
+  bool resident = false, tma = false;
   if (p.kernel == OT_KERNEL_RESIDENT) {
     if (!fits) return fail(OT_EINVAL, "ot_prox_create: H x W = %d x %d does not fit the resident kernel", p.H, p.W);
     resident = true;
   } else if (p.kernel == OT_KERNEL_AUTO) {
     resident = fits;
+    tma = !fits;
+  } else if (p.kernel == OT_KERNEL_TMA) {
+    tma = true;
   }
 
   ot_prox* h = (ot_prox*)calloc(1, sizeof(ot_prox));
@@ -293,6 +317,7 @@ int ot_prox_create(const ot_prox_params* params, void* cuda_stream, ot_prox_t* o
   h->G = G;
   h->plane_elems = plane_elems;
   h->resident = resident;
+  h->tma = tma;
   const float t1 = (float)p.tau1;
   h->C.tau1 = t1;
   h->C.tau2 = (float)p.tau2;
@@ -321,21 +346,52 @@ int ot_prox_create(const ot_prox_params* params, void* cuda_stream, ot_prox_t* o
   h->r = q; q += plane_elems;
   h->p0 = q; q += plane_elems;
   h->p1 = q; q += plane_elems;
+  int n_sm = 0, dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    n_sm = 152;
+  h->tma_grid = (int)(ctas < (double)n_sm ? ctas : n_sm);
   const int n_parts = (int)(ctas > (double)G.B ? ctas : G.B);
   const int n_cert = cert_num_blocks(G);
   const int np = n_parts > n_cert ? n_parts : n_cert;
-  e = cudaMalloc(&h->partials, (size_t)np * kNumSums * sizeof(double) + (size_t)n_cert * 4 * sizeof(double) +
-                                   (kNumSums + 4) * sizeof(double));
+  const size_t ws_bytes = (size_t)np * kNumSums * sizeof(double) + (size_t)n_cert * 4 * sizeof(double) +
+                          (kNumSums + 4) * sizeof(double) + 16;
+  e = cudaMalloc(&h->partials, ws_bytes);
   if (e == cudaSuccess) {
     h->cert_partials = h->partials + (size_t)np * kNumSums;
     h->dsums = h->cert_partials + (size_t)n_cert * 4;
-    e = cudaMallocHost(&h->hsums, (kNumSums + 4) * sizeof(double));
+    h->derr = reinterpret_cast<int*>(h->dsums + kNumSums + 4);
+    e = cudaMallocHost(&h->hsums, (kNumSums + 4) * sizeof(double) + 16);
+    if (e == cudaSuccess) h->herr = reinterpret_cast<int*>(h->hsums + kNumSums + 4);
   }
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->partials, 0, ws_bytes, h->stream);
   if (e != cudaSuccess) {
     ot_prox_destroy(h);
     return cuda_fail(e, "ot_prox_create: workspace allocation");
   }
   if (resident) e = prepare_prox_resident(p.mode, p.balanced != 0, G);
+  if (tma && e == cudaSuccess) {
+    e = prepare_prox_tma(p.mode, p.balanced != 0);
+    int bw, bh;
+    for (int par = 0; par < 2 && e == cudaSuccess; ++par) {
+      TmaMaps& m = h->maps[par];
+      int rc = 0;
+      tma_box(0, &bw, &bh);
+      rc |= encode_plane_map(&m.a, h->a[par], G, bw, bh);
+      tma_box(1, &bw, &bh);
+      rc |= encode_plane_map(&m.Mx, h->Mx[par], G, bw, bh);
+      rc |= encode_plane_map(&m.My, h->My[par], G, bw, bh);
+      tma_box(2, &bw, &bh);
+      rc |= encode_plane_map(&m.x0, h->x0, G, bw, bh);
+      rc |= encode_plane_map(&m.x1, h->x1, G, bw, bh);
+      rc |= encode_plane_map(&m.r, h->r, G, bw, bh);
+      rc |= encode_plane_map(&m.p0, h->p0, G, bw, bh);
+      rc |= encode_plane_map(&m.p1, h->p1, G, bw, bh);
+      if (rc != 0) {
+        ot_prox_destroy(h);
+        return fail(OT_ECUDA, "ot_prox_create: cuTensorMapEncodeTiled failed (%d)", rc);
+      }
+    }
+  }
   if (e == cudaSuccess) e = cudaMemsetAsync(h->slab, 0, plane_elems * nplanes * sizeof(float), h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) {
@@ -387,7 +443,7 @@ int ot_prox_check_interval(ot_prox_t h, int32_t n_iter, ot_prox_result* res) {
   const double* s = h->hsums;
   fill_result_from_sums(h, s, &r);
   r.iters = n_iter;
-  const bool bad = s[7] > 0 || !isfinite(s[0]) || !isfinite(s[1]) || !isfinite(s[2]);
+  const bool bad = sums_nonfinite(s);
   r.status = bad ? OT_ENONFINITE : OT_OK;
   if (res) *res = r;
   if (bad) return fail(OT_ENONFINITE, "ot_prox_check_interval: non-finite values in the iterates");
@@ -431,7 +487,7 @@ int ot_prox_solve(ot_prox_t h, ot_prox_result* res) {
     const double* s = h->hsums;
     fill_result_from_sums(h, s, &r);
     r.iters = k;
-    if (s[7] > 0 || !isfinite(s[0]) || !isfinite(s[1]) || !isfinite(s[2])) {
+    if (sums_nonfinite(s)) {
       status = OT_ENONFINITE;
       break;
     }

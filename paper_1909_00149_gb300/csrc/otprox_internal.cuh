@@ -2,6 +2,7 @@
 // Nothing here is part of the C ABI (include/otprox.h is).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -56,6 +57,11 @@ struct StatePtrs {
   const float* p1;
 };
 
+// TMA descriptors of the planes one iteration reads (ping-pong resolved).
+struct TmaMaps {
+  CUtensorMap a, Mx, My, x0, x1, r, p0, p1;
+};
+
 struct CertCoeffs {
   double mu, rho;
   int iso, pexp, mode, balanced;
@@ -77,6 +83,18 @@ cudaError_t launch_prox_resident(int mode, bool balanced, const Geometry& g, con
                                  float* Mx, float* My, float* a, float* x0, float* x1, float* r,
                                  const float* p0, const float* p1, int n_iter, bool reduce_last,
                                  double* partials, cudaStream_t st);
+
+// Persistent TMA-fed iteration (prox_tma.cu): one CTA per SM (grid =
+// min(tiles, SMs)); partials[grid][kNumSums] when reduce; *err set to 1 if a
+// bounded mbarrier wait expired.
+cudaError_t prepare_prox_tma(int mode, bool balanced);
+cudaError_t launch_prox_tma(int mode, bool balanced, bool reduce, const TmaMaps& maps, const Geometry& g,
+                            const IterCoeffs& c, const StatePtrs& s, double* partials, int* err, int grid,
+                            cudaStream_t st);
+// Encode a TMA descriptor for a [B][H][Wp] plane with a box_w x box_h box;
+// 0 on success.  tma_box(0|1|2) gives the box of a / M / pointwise planes.
+int encode_plane_map(CUtensorMap* map, const float* base, const Geometry& g, int box_w, int box_h);
+int tma_box(int which, int* w, int* h);
 
 // Sum partials[n][kNumSums] in a fixed order into out[kNumSums].
 cudaError_t launch_finalize_sums(const double* partials, int n, double* out, cudaStream_t st);

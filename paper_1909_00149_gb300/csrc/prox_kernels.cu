@@ -57,9 +57,39 @@ __device__ __forceinline__ float norm_term(float mx, float my, int iso) {
 
 __device__ __forceinline__ bool nonfinite(float v) { return !isfinite(v); }
 
-// Sum kNumSums doubles over the block; thread 0 writes them to out.
+// Sum kNumSums values over the block in FP64; thread 0 writes them to out.
+// Each thread's own partial sums (a handful of pixels) are FP32: FP64
+// arithmetic is scarce on this GPU, so it is used only across threads.
 template <int NT>
-__device__ void block_sum_store(double (&v)[kNumSums], double* out) {
+__device__ void block_sum_store(float (&v)[kNumSums], double* out) {
+  constexpr int NW = NT / 32;
+  __shared__ double red[NW][kNumSums];
+  const int tid = threadIdx.x + threadIdx.y * blockDim.x;
+  const int lane = tid & 31, warp = tid >> 5;
+  // within a warp in FP32 (32 partials), across warps and blocks in FP64
+#pragma unroll
+  for (int k = 0; k < kNumSums; ++k) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+  }
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < kNumSums; ++k) red[warp][k] = (double)v[k];
+  }
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int k = 0; k < kNumSums; ++k) {
+      double t = lane < NW ? red[lane][k] : 0.0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+      if (lane == 0) out[k] = t;
+    }
+  }
+}
+
+template <int NT>
+__device__ void block_sum_store_d(double (&v)[kNumSums], double* out) {
   constexpr int NW = NT / 32;
   __shared__ double red[NW][kNumSums];
   const int tid = threadIdx.x + threadIdx.y * blockDim.x;
@@ -227,9 +257,9 @@ prox_tiled_kernel(const Geometry G, const IterCoeffs C, const StatePtrs S, doubl
   __syncthreads();
 
   // ---- lines 4-7 on own pixels
-  double acc[kNumSums];
+  float acc[kNumSums];
 #pragma unroll
-  for (int k = 0; k < kNumSums; ++k) acc[k] = 0.0;
+  for (int k = 0; k < kNumSums; ++k) acc[k] = 0.f;
 #pragma unroll
   for (int q = 0; q < kRPT; ++q) {
     const int rr = ty + kTY * q + 1;
@@ -264,20 +294,20 @@ prox_tiled_kernel(const Geometry G, const IterCoeffs C, const StatePtrs S, doubl
         const float nmx_up = s_mnx[rr - 1][4 * tx + e];
         const float nmy_l = s_mny[rr - 1][4 * tx + 3 + e];
         const float kz = (nmxe - nmx_up) + (nmye - nmy_l) - vx0 + vx1 - (BAL ? 0.f : vr);
-        acc[0] += (double)kz * kz;
-        const double d0 = nmxe - compc(mx[q], e), d1 = nmye - compc(my[q], e);
-        const double d2 = vx0 - compc(x0[q], e), d3 = vx1 - compc(x1[q], e);
-        const double d4 = vr - compc(rv[q], e), d5 = va - a;
+        acc[0] = fmaf(kz, kz, acc[0]);
+        const float d0 = nmxe - compc(mx[q], e), d1 = nmye - compc(my[q], e);
+        const float d2 = vx0 - compc(x0[q], e), d3 = vx1 - compc(x1[q], e);
+        const float d4 = vr - compc(rv[q], e), d5 = va - a;
         acc[1] += d0 * d0 + d1 * d1 + d2 * d2 + d3 * d3 + d4 * d4 + d5 * d5;
-        acc[2] += (double)nmxe * nmxe + (double)nmye * nmye + (double)vx0 * vx0 + (double)vx1 * vx1 +
-                  (double)vr * vr + (double)va * va;
+        acc[2] += nmxe * nmxe + nmye * nmye + vx0 * vx0 + vx1 * vx1 + vr * vr + va * va;
         acc[3] += norm_term(nmxe, nmye, C.iso);
-        acc[4] += C.pexp == 1 ? fabs((double)vr) : (double)vr * vr;
-        if (MODE == 0) acc[5] += ((double)vx0 - compc(p0[q], e)) * ((double)vx0 - compc(p0[q], e));
-        if (MODE != 2) acc[5] += ((double)vx1 - compc(p1[q], e)) * ((double)vx1 - compc(p1[q], e));
-        acc[6] += (double)compc(p0[q], e) * compc(p0[q], e) + (double)compc(p1[q], e) * compc(p1[q], e);
+        acc[4] += C.pexp == 1 ? fabsf(vr) : vr * vr;
+        const float e0 = vx0 - compc(p0[q], e), e1 = vx1 - compc(p1[q], e);
+        if (MODE == 0) acc[5] = fmaf(e0, e0, acc[5]);
+        if (MODE != 2) acc[5] = fmaf(e1, e1, acc[5]);
+        acc[6] += compc(p0[q], e) * compc(p0[q], e) + compc(p1[q], e) * compc(p1[q], e);
         acc[7] += (nonfinite(va) || nonfinite(nmxe) || nonfinite(nmye) || nonfinite(vx0) || nonfinite(vx1) ||
-                   nonfinite(vr)) ? 1.0 : 0.0;
+                   nonfinite(vr) || nonfinite(compc(p0[q], e)) || nonfinite(compc(p1[q], e))) ? 1.f : 0.f;
       }
     }
     const long long off = base + (long long)i * Wp + j;
@@ -357,9 +387,9 @@ prox_resident_kernel(const Geometry G, const IterCoeffs C, float* __restrict__ g
   }
   __syncthreads();
 
-  double acc[kNumSums];
+  float acc[kNumSums];
 #pragma unroll
-  for (int k = 0; k < kNumSums; ++k) acc[k] = 0.0;
+  for (int k = 0; k < kNumSums; ++k) acc[k] = 0.f;
 
   for (int it = 0; it < n_iter; ++it) {
     const bool red = reduce_last && (it == n_iter - 1);
@@ -386,11 +416,11 @@ prox_resident_kernel(const Geometry G, const IterCoeffs C, float* __restrict__ g
         comp(bx, e) = 2.f * ox - compc(m4x, e);
         comp(by, e) = 2.f * oy - compc(m4y, e);
         if (red && in) {
-          const double d0 = ox - compc(m4x, e), d1 = oy - compc(m4y, e);
+          const float d0 = ox - compc(m4x, e), d1 = oy - compc(m4y, e);
           acc[1] += d0 * d0 + d1 * d1;
-          acc[2] += (double)ox * ox + (double)oy * oy;
+          acc[2] += ox * ox + oy * oy;
           acc[3] += norm_term(ox, oy, C.iso);
-          acc[7] += (nonfinite(ox) || nonfinite(oy)) ? 1.0 : 0.0;
+          acc[7] += (nonfinite(ox) || nonfinite(oy)) ? 1.f : 0.f;
         }
       }
       st4(sMx + o, nx);
@@ -437,16 +467,18 @@ prox_resident_kernel(const Geometry G, const IterCoeffs C, float* __restrict__ g
           const float mx_up = i > 0 ? sMx[o + e - Wp] : 0.f;
           const float my_l = (j + e) > 0 ? sMy[o + e - 1] : 0.f;
           const float kz = (mxn - mx_up) + (myn - my_l) - vx0 + vx1 - (BAL ? 0.f : vr);
-          acc[0] += (double)kz * kz;
-          const double d2 = vx0 - compc(x04, e), d3 = vx1 - compc(x14, e);
-          const double d4 = vr - compc(r4, e), d5 = va - a;
+          acc[0] = fmaf(kz, kz, acc[0]);
+          const float d2 = vx0 - compc(x04, e), d3 = vx1 - compc(x14, e);
+          const float d4 = vr - compc(r4, e), d5 = va - a;
           acc[1] += d2 * d2 + d3 * d3 + d4 * d4 + d5 * d5;
-          acc[2] += (double)vx0 * vx0 + (double)vx1 * vx1 + (double)vr * vr + (double)va * va;
-          acc[4] += C.pexp == 1 ? fabs((double)vr) : (double)vr * vr;
-          if (MODE == 0) acc[5] += ((double)vx0 - compc(p04, e)) * ((double)vx0 - compc(p04, e));
-          if (MODE != 2) acc[5] += ((double)vx1 - compc(p14, e)) * ((double)vx1 - compc(p14, e));
-          acc[6] += (double)compc(p04, e) * compc(p04, e) + (double)compc(p14, e) * compc(p14, e);
-          acc[7] += (nonfinite(va) || nonfinite(vx0) || nonfinite(vx1) || nonfinite(vr)) ? 1.0 : 0.0;
+          acc[2] += vx0 * vx0 + vx1 * vx1 + vr * vr + va * va;
+          acc[4] += C.pexp == 1 ? fabsf(vr) : vr * vr;
+          const float e0 = vx0 - compc(p04, e), e1 = vx1 - compc(p14, e);
+          if (MODE == 0) acc[5] = fmaf(e0, e0, acc[5]);
+          if (MODE != 2) acc[5] = fmaf(e1, e1, acc[5]);
+          acc[6] += compc(p04, e) * compc(p04, e) + compc(p14, e) * compc(p14, e);
+          acc[7] += (nonfinite(va) || nonfinite(vx0) || nonfinite(vx1) || nonfinite(vr) || nonfinite(compc(p04, e)) ||
+                     nonfinite(compc(p14, e))) ? 1.f : 0.f;
         }
       }
       st4(sA + o, na);
@@ -565,7 +597,7 @@ eval_pass1_kernel(const Geometry G, const CertCoeffs cc, const float* __restrict
     const double n = cc.iso ? sqrt(gx * gx + gy * gy) : fmax(fabs(gx), fabs(gy));
     nmax = fmax(nmax, n);
   }
-  block_sum_store<kCertThreads>(acc, partials + (size_t)blockIdx.x * kNumSums);
+  block_sum_store_d<kCertThreads>(acc, partials + (size_t)blockIdx.x * kNumSums);
   // block max of nmax
   __shared__ double smax[kCertThreads / 32];
   for (int o = 16; o > 0; o >>= 1) nmax = fmax(nmax, __shfl_down_sync(0xffffffffu, nmax, o));

@@ -13,8 +13,12 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 @pytest.fixture(scope="module")
 def cdll():
-    from paper_1909_00149_gb300 import build
-    path = build.build()
+    import importlib.util
+    spec = importlib.util.spec_from_file_location(
+        "otprox_build", os.path.join(ROOT, "paper_1909_00149_gb300", "build.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    path = mod.build()
     return ctypes.CDLL(path)
 
 

@@ -56,7 +56,7 @@ def check_state(g, o: P.ProxState, tol, scale):
         assert e <= tol, f"{name}: relative error {e:.3e} > {tol:g}"
 
 
-@pytest.mark.parametrize("kernel", ["tiled", "resident"])
+@pytest.mark.parametrize("kernel", ["tiled", "resident", "tma"])
 @pytest.mark.parametrize("k,tol", [(1, 1e-6), (10, 1e-5), (500, 1e-5)])
 def test_trajectory_parity_64x64_pair(lib, kernel, k, tol):
     """The 64x64 frame pair: 3 blobs, shifts in [-4, 4], one blob rescaled."""
@@ -73,7 +73,7 @@ VARIANTS = [dict(), dict(mode="fixed_first"), dict(mode="eval"), dict(balanced=T
 
 @pytest.mark.parametrize("shape", SHAPES)
 @pytest.mark.parametrize("variant", range(len(VARIANTS)))
-@pytest.mark.parametrize("kernel", ["tiled", "resident"])
+@pytest.mark.parametrize("kernel", ["tiled", "resident", "tma"])
 def test_shapes_and_modes(lib, shape, variant, kernel):
     B, H, W = shape
     kw = dict(mu=1.5, rho=0.02, **VARIANTS[variant])
@@ -119,7 +119,7 @@ def _gpu_masks(g):
     return {"M": np.hypot(g["Mx"], g["My"]) > 0, "r": g["r"] != 0, "x0": g["x0"] > 0, "x1": g["x1"] > 0}
 
 
-@pytest.mark.parametrize("kernel", ["tiled", "resident"])
+@pytest.mark.parametrize("kernel", ["tiled", "resident", "tma"])
 def test_support_masks_bit_exact_one_step(lib, kernel):
     """One iteration from an identical FP32 state: the flux, source and
     non-negativity masks agree bit for bit outside a 1e-5 guard band."""
@@ -139,7 +139,7 @@ def test_support_masks_bit_exact_one_step(lib, kernel):
     assert int(ref["M"].sum()) > 100 and int(ref["r"].sum()) > 50   # the masks are not trivial
 
 
-@pytest.mark.parametrize("kernel", ["tiled", "resident"])
+@pytest.mark.parametrize("kernel", ["tiled", "resident", "tma"])
 def test_support_masks_after_500_iterations(lib, kernel):
     p0, p1 = config1_pair()
     prm = oracle_params()
@@ -154,7 +154,7 @@ def test_support_masks_after_500_iterations(lib, kernel):
         assert not mism.any(), f"{key}: {int(mism.sum())} mismatches outside the 1e-4 band"
 
 
-@pytest.mark.parametrize("kernel", ["tiled", "resident"])
+@pytest.mark.parametrize("kernel", ["tiled", "resident", "tma"])
 def test_solve_matches_oracle(lib, kernel):
     """ot_prox_solve to 1e-5: same stopping rule as the oracle's; compare the
     state after the iterations the GPU ran, and the reported quantities."""
@@ -196,7 +196,7 @@ def test_evaluate_matches_oracle_certificate(lib):
     assert abs(res["rel_gap"] - cert["rel_gap"]) <= 1e-8
 
 
-@pytest.mark.parametrize("kernel", ["tiled", "resident"])
+@pytest.mark.parametrize("kernel", ["tiled", "resident", "tma"])
 def test_warm_restart_is_bit_exact(lib, kernel):
     """Checkpoint/resume: 500 iterations == 250 + get_state/set_state + 250."""
     p0, p1 = config1_pair()
@@ -208,12 +208,25 @@ def test_warm_restart_is_bit_exact(lib, kernel):
         assert np.array_equal(a[k], b[k]), k
 
 
-def test_tiled_and_resident_agree(lib):
+@pytest.mark.parametrize("other", ["resident", "tma"])
+def test_kernels_agree(lib, other):
     p0, p1 = config1_pair()
     a = gpu_iterate(lib, p0, p1, 200, mu=MU, rho=RHO, kernel="tiled")
-    b = gpu_iterate(lib, p0, p1, 200, mu=MU, rho=RHO, kernel="resident")
+    b = gpu_iterate(lib, p0, p1, 200, mu=MU, rho=RHO, kernel=other)
     for k in NAMES:
         assert rel_err(a[k], b[k], np.linalg.norm(p0)) <= 1e-6, k
+
+
+def test_tma_and_tiled_bit_identical(lib):
+    """Same arithmetic in the same order: the TMA pipeline changes only how
+    the inputs reach shared memory, so its iterates equal the tiled kernel's."""
+    from synth import blob_video
+    v = blob_video(rng_for(1, 4), 9, 200, 300, n_blobs=5)
+    p0, p1 = np.ascontiguousarray(v[:-1]), np.ascontiguousarray(v[1:])
+    a = gpu_iterate(lib, p0, p1, 30, mu=MU, rho=RHO, kernel="tiled")
+    b = gpu_iterate(lib, p0, p1, 30, mu=MU, rho=RHO, kernel="tma")
+    for k in NAMES:
+        assert np.array_equal(a[k], b[k]), k
 
 
 def test_host_pointers_equal_device_pointers(lib):
@@ -250,13 +263,13 @@ def test_max_iter_reports_not_converged(lib):
 
 
 def test_full_size_video_batch_parity(lib):
-    """The 63 frame pairs of a 64-frame 256x256 sequence, tiled kernel with the
+    """The 63 frame pairs of a 64-frame 256x256 sequence, TMA kernel with the
     CUDA-graph check loop as in the benchmark: the whole state after 20
     iterations (two check intervals) against the oracle."""
     from synth import blob_video
     v = blob_video(rng_for(1, 3), 64, 256, 256, n_blobs=8)
     p0, p1 = np.ascontiguousarray(v[:-1]), np.ascontiguousarray(v[1:])
-    with lib.OtProx(63, 256, 256, mu=MU, rho=RHO, kernel="tiled", use_graph=True, max_iter=20, tol=0.0) as s:
+    with lib.OtProx(63, 256, 256, mu=MU, rho=RHO, kernel="tma", use_graph=True, max_iter=20, tol=0.0) as s:
         s.set_input(torch.from_numpy(p0).cuda(), torch.from_numpy(p1).cuda())
         res = s.solve()
         g = {k: v.double().cpu().numpy() for k, v in s.get_state().items()}
