@@ -174,6 +174,32 @@ int ot_prox_get_params(ot_prox_t h, ot_prox_params* out);
 /* Free everything the handle owns; NULL is accepted. */
 int ot_prox_destroy(ot_prox_t h);
 
+/* ot_prox_evaluate for a state the caller holds, without allocating.
+ * The paper has no counterpart: this is a convenience for callers that
+ * cannot allocate device memory when they need the answer -- for example
+ * code running inside another framework's memory pool that forbids
+ * allocations outside it, or a latency-critical loop where cudaMalloc or
+ * cudaFree would synchronise the device.  It calls no cudaMalloc, cudaFree
+ * or allocating library routine; its scratch is a fixed array of about
+ * 114 KB inside the library, present on every GPU that loads it until the
+ * process exits.
+ *  - params: only B, H, W, mode, norm, balanced, p_exp, mu, rho are read.
+ *    B*H*W may be at most 2^31 - 1; larger inputs return OT_EINVAL.
+ *  - p0 ... a: DEVICE pointers, dense [B][H][W] float32 (no padding).  x0
+ *    may be NULL unless mode is PROX, x1 may be NULL in EVAL mode, r may be
+ *    NULL when balanced (frozen x take p0 / p1).
+ *  - res: host; filled as by ot_prox_evaluate (res_fp and iters are 0).
+ *  - cuda_stream: cudaStream_t or NULL.  Sync: returns after the stream
+ *    reaches the end of the evaluation.
+ * The first call on a device looks up the scratch array's device address
+ * for that device; make that first call before any stream capture.  All
+ * calls share the one array, so calls that overlap on the GPU (other
+ * streams, other threads) race and give wrong results; every call rewrites
+ * all the scratch it reads, so nothing needs clearing between calls. */
+int ot_prox_evaluate_noalloc(const ot_prox_params* params, const float* p0, const float* p1,
+                             const float* Mx, const float* My, const float* x0, const float* x1,
+                             const float* r, const float* a, ot_prox_result* res, void* cuda_stream);
+
 /* Message of the last failing call on this thread ("" if none). */
 const char* ot_last_error(void);
 

@@ -63,6 +63,8 @@ PROTOTYPES = [
     ("ot_prox_reset", ctypes.c_int, [ctypes.c_void_p]),
     ("ot_prox_get_params", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ot_prox_params)]),
     ("ot_prox_destroy", ctypes.c_int, [ctypes.c_void_p]),
+    ("ot_prox_evaluate_noalloc", ctypes.c_int, [ctypes.POINTER(ot_prox_params)] + [ctypes.c_void_p] * 8 +
+     [ctypes.POINTER(ot_prox_result), ctypes.c_void_p]),
 ]
 
 
