@@ -174,6 +174,89 @@ int ot_prox_get_params(ot_prox_t h, ot_prox_params* out);
 /* Free everything the handle owns; NULL is accepted. */
 int ot_prox_destroy(ot_prox_t h);
 
+/* ------------------------------------------------------------------ RPCA */
+/* RPCA+UOT-DF (Algorithm 3, Sec. IV-B.1) with Phi_t = I: minimise
+ *   1/2 sum_t ||y_t - s_t - l_t||^2 + lambda ||S||_1 + gamma ||L||_*
+ *   + kappa sum_{t<T} V_mu(s_t, s_{t+1}),   S, L >= 0           (eq. RPCA_UOTDF)
+ * by ADMM with the splitting of Sec. IV-B.1.  Line 10's singular-value
+ * thresholding runs through the T x T Gram matrix; line 11 runs n_inner
+ * warm-started Algorithm 1 iterations on the T-1 frame pairs (prox weight
+ * kappa/rho).  Readings of garbled lines: A += X - S - L (line 12), the
+ * x-update keeps rho (line 9), s_t >= 0 (line 7).  Stopping: the ADMM primal
+ * and dual residuals (Boyd), each relative to ||Y||, both <= tol. */
+typedef struct ot_rpca* ot_rpca_t;
+
+typedef struct {
+  int32_t T, H, W;        /* frames (2..128), rows, columns                      */
+  double  lambda;         /* sparsity weight > 0                                  */
+  double  gamma;          /* nuclear-norm weight; <= 0: lambda sqrt(max(N, T))    */
+  double  kappa;          /* OT weight > 0                                        */
+  double  mu;             /* growth/decay penalty of V_mu > 0                     */
+  double  rho;            /* ADMM penalty > 0                                     */
+  int32_t n_inner;        /* Algorithm 1 iterations per outer iteration (>= 1)    */
+  double  tol;            /* tolerance on both relative residuals                 */
+  int32_t max_iter;       /* outer-iteration cap of ot_rpca_solve                 */
+  int32_t check_every;    /* outer iterations between residual checks (>= 1)     */
+  int32_t svt_max_sweeps; /* Jacobi sweeps cap of the T x T eigensolver           */
+  int32_t prox_kernel;    /* OT_KERNEL_* of the inner Algorithm 1                 */
+} ot_rpca_params;
+
+typedef struct {
+  int32_t iters;          /* outer iterations run by this call                   */
+  int32_t status;         /* OT_OK / OT_ENOTCONV / OT_ENONFINITE                  */
+  double  res_pri;        /* ||(X-S-L, L-T, z-s_t, w-s_{t+1})|| / ||Y||           */
+  double  res_dual;       /* rho ||(dX, dT, dz, dw)|| / ||Y||                     */
+  int32_t svt_sweeps;     /* Jacobi sweeps of the last SVT                        */
+  int32_t svt_rank;       /* singular values above gamma/rho in the last SVT     */
+} ot_rpca_result;
+
+/* Variables readable with ot_rpca_get; frame variables are [T][H][W], pair
+ * variables [T-1][H][W] (pair t couples frames t and t+1). */
+#define OT_RPCA_S     0   /* sparse part (frames)                  */
+#define OT_RPCA_L     1   /* low-rank part (frames)                */
+#define OT_RPCA_X     2   /* data split variable (frames)          */
+#define OT_RPCA_T     3   /* nuclear-norm split variable (frames)  */
+#define OT_RPCA_A     4   /* scaled dual of X = S + L (frames)     */
+#define OT_RPCA_D     5   /* scaled dual of T = L (frames)         */
+#define OT_RPCA_B     6   /* scaled dual of z_t = s_t (pairs)      */
+#define OT_RPCA_C     7   /* scaled dual of w_{t+1} = s_{t+1} (pairs) */
+#define OT_RPCA_Z     8   /* z_t (pairs): first prox output        */
+#define OT_RPCA_W     9   /* w_{t+1} (pairs): second prox output   */
+#define OT_RPCA_MX   10   /* inner prox flux Mx (pairs)            */
+#define OT_RPCA_MY   11   /* inner prox flux My (pairs)            */
+#define OT_RPCA_R    12   /* inner prox source r (pairs)           */
+#define OT_RPCA_DUAL 13   /* inner prox dual a (pairs)             */
+
+/* Defaults: lambda 0.02, gamma lambda sqrt(max(N,T)), kappa 0.005, mu 3,
+ * rho 1, n_inner 1, tol 1e-5, max_iter 5000, check_every 1,
+ * svt_max_sweeps 30, prox_kernel AUTO; T = 2, H = W = 1. */
+void ot_rpca_default_params(ot_rpca_params* p);
+/* Validate, allocate and zero the state (Algorithm 3 line 2). */
+int ot_rpca_create(const ot_rpca_params* params, void* cuda_stream, ot_rpca_t* out);
+/* Observations Y [T][H][W] (host or device).  Sync (computes ||Y||). */
+int ot_rpca_set_input(ot_rpca_t h, const float* Y);
+/* n_outer >= 0 outer iterations, no residual read.  Async. */
+int ot_rpca_step(ot_rpca_t h, int32_t n_outer);
+/* n_outer >= 1 outer iterations; the residuals of the last one.  Sync. */
+int ot_rpca_iterate_checked(ot_rpca_t h, int32_t n_outer, ot_rpca_result* res);
+/* Iterate until both residuals <= tol or max_iter.  Returns OT_OK,
+ * OT_ENOTCONV (state still valid) or OT_ENONFINITE.  Sync. */
+int ot_rpca_solve(ot_rpca_t h, ot_rpca_result* res);
+/* Copy one variable (OT_RPCA_*) out, dense.  Sync. */
+int ot_rpca_get(ot_rpca_t h, int32_t var, float* out);
+/* Zero the state (keeps Y). */
+int ot_rpca_reset(ot_rpca_t h);
+int ot_rpca_get_params(ot_rpca_t h, ot_rpca_params* out);
+int ot_rpca_destroy(ot_rpca_t h);
+
+/* Singular-value thresholding shrink*_theta(X) = U max(Sigma - theta, 0) V^T
+ * (Sec. IV-B.1, Algorithm 3 line 10) of an N x T matrix stored as T columns of
+ * N floats (X + t*N), via the T x T Gram matrix and a Jacobi eigensolver.
+ * X, Y: DEVICE pointers, must not alias; 1 <= T <= 128.  Workspace is taken
+ * with cudaMallocAsync on the stream and returned before the call ends.
+ * Async. */
+int ot_svt(const float* X, float* Y, int64_t N, int32_t T, double theta, void* cuda_stream);
+
 /* ot_prox_evaluate for a state the caller holds, without allocating.
  * The paper has no counterpart: this is a convenience for callers that
  * cannot allocate device memory when they need the answer -- for example

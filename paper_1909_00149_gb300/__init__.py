@@ -178,4 +178,84 @@ class OtProx:
               "ot_prox_set_state")
 
 
-__all__ = ["OtProx", "OtError", "default_params", "check", "LIB_PATH", "ot_prox_params", "ot_prox_result"]
+def rpca_default_params(**kw) -> "_abi.ot_rpca_params":
+    p = _abi.ot_rpca_params()
+    _lib.ot_rpca_default_params(ctypes.byref(p))
+    for k, v in kw.items():
+        k = "lambda_" if k in ("lam", "lambda") else k
+        if k == "prox_kernel":
+            v = KERNELS[v] if isinstance(v, str) else v
+        if not hasattr(p, k):
+            raise TypeError(f"unknown parameter {k!r}")
+        setattr(p, k, v)
+    return p
+
+
+class Rpca:
+    """RPCA+UOT-DF (Algorithm 3, Phi = I) on a T-frame H x W video."""
+
+    def __init__(self, T: int, H: int, W: int, stream=None, **params):
+        self.T, self.H, self.W = int(T), int(H), int(W)
+        p = rpca_default_params(T=self.T, H=self.H, W=self.W, **params)
+        h = ctypes.c_void_p()
+        self._stream = _stream_handle(stream)
+        check(_lib.ot_rpca_create(ctypes.byref(p), self._stream, ctypes.byref(h)), "ot_rpca_create")
+        self.h = h
+        self.params = _abi.ot_rpca_params()
+        check(_lib.ot_rpca_get_params(self.h, ctypes.byref(self.params)), "ot_rpca_get_params")
+
+    def close(self):
+        if getattr(self, "h", None):
+            _lib.ot_rpca_destroy(self.h)
+            self.h = None
+
+    __del__ = close
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def set_input(self, Y):
+        A = _Arrays(self.T * self.H * self.W)
+        check(_lib.ot_rpca_set_input(self.h, A.ptr(Y)), "ot_rpca_set_input")
+
+    def step(self, n_outer: int):
+        check(_lib.ot_rpca_step(self.h, int(n_outer)), "ot_rpca_step")
+
+    def iterate_checked(self, n_outer: int = 1) -> dict:
+        r = _abi.ot_rpca_result()
+        check(_lib.ot_rpca_iterate_checked(self.h, int(n_outer), ctypes.byref(r)), "ot_rpca_iterate_checked")
+        return r.as_dict()
+
+    def solve(self) -> dict:
+        r = _abi.ot_rpca_result()
+        check(_lib.ot_rpca_solve(self.h, ctypes.byref(r)), "ot_rpca_solve", ok=(OT_OK, OT_ENOTCONV))
+        return r.as_dict()
+
+    def reset(self):
+        check(_lib.ot_rpca_reset(self.h), "ot_rpca_reset")
+
+    def get(self, name: str, device=None):
+        import torch
+        nf = self.T - 1 if name in _abi.RPCA_PAIR_VARS else self.T
+        dev = torch.device("cuda") if device is None else torch.device(device)
+        out = torch.empty((nf, self.H, self.W), dtype=torch.float32, device=dev)
+        A = _Arrays(out.numel())
+        check(_lib.ot_rpca_get(self.h, _abi.RPCA_VARS[name], A.ptr(out, True)), "ot_rpca_get")
+        return out
+
+
+def svt(X, theta: float, stream=None):
+    """shrink*_theta of the N x T matrix whose T columns are X[t] (X: [T, ...]
+    float32 CUDA tensor).  Returns a tensor of the same shape."""
+    import torch
+    T = X.shape[0]
+    N = X.numel() // T
+    Y = torch.empty_like(X)
+    check(_lib.ot_svt(X.data_ptr(), Y.data_ptr(), N, T, float(theta), _stream_handle(stream)), "ot_svt")
+    return Y
+
+
+__all__ = ["Rpca", "svt", "rpca_default_params", "OtProx", "OtError", "default_params", "check", "LIB_PATH", "ot_prox_params", "ot_prox_result"]

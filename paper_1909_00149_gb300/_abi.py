@@ -45,6 +45,26 @@ class ot_prox_result(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class ot_rpca_params(ctypes.Structure):
+    _fields_ = [("T", ctypes.c_int32), ("H", ctypes.c_int32), ("W", ctypes.c_int32),
+                ("lambda_", ctypes.c_double), ("gamma", ctypes.c_double), ("kappa", ctypes.c_double),
+                ("mu", ctypes.c_double), ("rho", ctypes.c_double), ("n_inner", ctypes.c_int32),
+                ("tol", ctypes.c_double), ("max_iter", ctypes.c_int32), ("check_every", ctypes.c_int32),
+                ("svt_max_sweeps", ctypes.c_int32), ("prox_kernel", ctypes.c_int32)]
+
+
+class ot_rpca_result(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int32), ("status", ctypes.c_int32), ("res_pri", ctypes.c_double),
+                ("res_dual", ctypes.c_double), ("svt_sweeps", ctypes.c_int32), ("svt_rank", ctypes.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+RPCA_VARS = {"S": 0, "L": 1, "X": 2, "T": 3, "A": 4, "D": 5, "B": 6, "C": 7, "Z": 8, "W": 9,
+             "Mx": 10, "My": 11, "r": 12, "a": 13}
+RPCA_PAIR_VARS = {"B", "C", "Z", "W", "Mx", "My", "r", "a"}
+
 # (name, restype, argtypes)
 PROTOTYPES = [
     ("ot_last_error", ctypes.c_char_p, []),
@@ -63,6 +83,18 @@ PROTOTYPES = [
     ("ot_prox_reset", ctypes.c_int, [ctypes.c_void_p]),
     ("ot_prox_get_params", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ot_prox_params)]),
     ("ot_prox_destroy", ctypes.c_int, [ctypes.c_void_p]),
+    ("ot_rpca_default_params", None, [ctypes.POINTER(ot_rpca_params)]),
+    ("ot_rpca_create", ctypes.c_int, [ctypes.POINTER(ot_rpca_params), ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]),
+    ("ot_rpca_set_input", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    ("ot_rpca_step", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
+    ("ot_rpca_iterate_checked", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ot_rpca_result)]),
+    ("ot_rpca_solve", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ot_rpca_result)]),
+    ("ot_rpca_get", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]),
+    ("ot_rpca_reset", ctypes.c_int, [ctypes.c_void_p]),
+    ("ot_rpca_get_params", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ot_rpca_params)]),
+    ("ot_rpca_destroy", ctypes.c_int, [ctypes.c_void_p]),
+    ("ot_svt", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_double,
+                              ctypes.c_void_p]),
     ("ot_prox_evaluate_noalloc", ctypes.c_int, [ctypes.POINTER(ot_prox_params)] + [ctypes.c_void_p] * 8 +
      [ctypes.POINTER(ot_prox_result), ctypes.c_void_p]),
 ]

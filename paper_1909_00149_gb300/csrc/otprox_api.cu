@@ -12,6 +12,7 @@
 
 #include "../../include/otprox.h"
 #include "otprox_internal.cuh"
+#include "prox_handle.cuh"
 
 namespace otp {
 thread_local std::string g_err;
@@ -40,35 +41,7 @@ using namespace otp;
     if (e_ != cudaSuccess) return cuda_fail(e_, what); \
   } while (0)
 
-struct ot_prox {
-  ot_prox_params prm;
-  cudaStream_t stream;
-  Geometry G;
-  IterCoeffs C;
-  size_t plane_elems;        // B * H * Wp
-  float* slab;
-  float* Mx[2];
-  float* My[2];
-  float* a[2];
-  float* x0;
-  float* x1;
-  float* r;
-  float* p0;
-  float* p1;
-  int cur;                   // ping-pong index of the current M, a
-  bool resident;
-  bool tma;
-  int tma_grid;              // persistent CTAs (one per SM, at most one per tile)
-  TmaMaps maps[2];           // by ping-pong parity of the input M, a
-  int* derr;                 // device error flag (bounded waits)
-  int* herr;                 // pinned host mirror
-  double* partials;          // [max(n_ctas, n_cert)][kNumSums]
-  double* cert_partials;     // [n_cert][4]
-  double* dsums;             // device: [kNumSums] sums + [4] certificate
-  double* hsums;             // pinned host mirror
-  cudaGraphExec_t graph[2];  // one check interval, by starting parity
-  int graph_n;
-};
+
 
 extern "C" {
 

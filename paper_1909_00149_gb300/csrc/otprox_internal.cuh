@@ -110,4 +110,39 @@ cudaError_t launch_evaluate(const Geometry& g, const CertCoeffs& cc, const float
                             double* sums_out, double* cert_partials, double* cert_out,
                             cudaStream_t st);
 
+// ----------------------------------------------------------------- RPCA
+struct RpcaGeom {
+  int T, H, W, Wp;
+  long long plane;         // H * Wp
+};
+struct RpcaCoeffs {
+  float lam, rho;
+};
+// Frame planes [T][H][Wp] (X, L, A, Tm, D, Y, S, LD) and pair planes
+// [T-1][H][Wp] (z = prox x0, w = prox x1, Bz, Cw, p0, p1, zprev, wprev).
+struct RpcaPlanes {
+  float *X, *L, *A, *Tm, *D, *Y, *S, *LD;
+  float *z, *w, *Bz, *Cw, *p0, *p1, *zprev, *wprev;
+};
+int rpca_num_blocks(const RpcaGeom& g);
+cudaError_t rpca_launch_pre(const RpcaGeom& g, const RpcaCoeffs& c, const RpcaPlanes& P, double* partials,
+                            cudaStream_t st);
+cudaError_t rpca_launch_post(const RpcaGeom& g, const RpcaPlanes& P, double* partials, cudaStream_t st);
+cudaError_t rpca_launch_sumsq(const RpcaGeom& g, const float* Y, double* partials, cudaStream_t st);
+
+// ----------------------------------------------------------------- SVT
+int svt_padded_T(int T);                       // 16, 32, 64 or 128
+int svt_gram_blocks(long long N);
+int svt_apply_blocks(long long N, int T, int* gy);
+cudaError_t svt_prepare();
+cudaError_t svt_launch_gram(const float* X, long long ld, long long N, int T, double* partials, double* G,
+                            cudaStream_t st);
+cudaError_t svt_launch_eig(const double* G, int T, int warm, float theta, int max_sweeps, float tol, float* V_io,
+                           float* Wm, float* sig, int* sweeps, cudaStream_t st);
+cudaError_t svt_launch_apply(const float* X, long long ld, long long N, int T, const float* Wm, float* Y,
+                             long long ldy, bool reduce, double* partials, cudaStream_t st);
+
+int fail(int code, const char* fmt, ...);
+int cuda_fail(cudaError_t e, const char* what);
+
 }  // namespace otp

@@ -1,0 +1,41 @@
+// The Algorithm 1 solver handle (opaque in the C ABI), shared by the
+// translation units that drive it: otprox_api.cu and the RPCA runtime.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "../../include/otprox.h"
+#include "otprox_internal.cuh"
+
+struct ot_prox {
+  using Geometry = otp::Geometry;
+  using IterCoeffs = otp::IterCoeffs;
+  using TmaMaps = otp::TmaMaps;
+  ot_prox_params prm;
+  cudaStream_t stream;
+  Geometry G;
+  IterCoeffs C;
+  size_t plane_elems;        // B * H * Wp
+  float* slab;
+  float* Mx[2];
+  float* My[2];
+  float* a[2];
+  float* x0;
+  float* x1;
+  float* r;
+  float* p0;
+  float* p1;
+  int cur;                   // ping-pong index of the current M, a
+  bool resident;
+  bool tma;
+  int tma_grid;              // persistent CTAs (one per SM, at most one per tile)
+  TmaMaps maps[2];           // by ping-pong parity of the input M, a
+  int* derr;                 // device error flag (bounded waits)
+  int* herr;                 // pinned host mirror
+  double* partials;          // [max(n_ctas, n_cert)][kNumSums]
+  double* cert_partials;     // [n_cert][4]
+  double* dsums;             // device: [kNumSums] sums + [4] certificate
+  double* hsums;             // pinned host mirror
+  cudaGraphExec_t graph[2];  // one check interval, by starting parity
+  int graph_n;
+};

@@ -1,0 +1,402 @@
+// C ABI of the RPCA+UOT-DF solver (Algorithm 3, Sec. IV-B.1, Phi_t = I) and
+// of the standalone singular-value thresholding (Algorithm 3 line 10).
+//
+// One outer iteration, in stream order:
+//   rpca_pre      lines 4-9 fused; builds L + D and the prox centres
+//   gram / eig / apply   line 10: Tm = shrink*_{gamma/rho}(L + D)
+//   ot_prox_step  line 11: n_inner warm-started Algorithm 1 iterations on
+//                 the T-1 frame pairs with weight kappa/rho
+//   rpca_post     lines 12-15 and the ADMM residual sums
+// then, on check iterations, one fixed-order FP64 finalize and a 64-byte copy
+// to the host.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include "../../include/otprox.h"
+#include "otprox_internal.cuh"
+#include "prox_handle.cuh"
+
+using namespace otp;
+
+#define OT_CUDA(call, what)                            \
+  do {                                                 \
+    cudaError_t e_ = (call);                           \
+    if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+  } while (0)
+
+struct ot_rpca {
+  ot_rpca_params prm;
+  cudaStream_t stream;
+  RpcaGeom G;
+  RpcaCoeffs C;
+  float* slab;
+  RpcaPlanes P;
+  ot_prox* prox;             // B = T-1 problems, rho_prox = kappa / rho
+  // SVT workspace
+  int TP;
+  double* gram_partials;
+  double* Gm;
+  float* V;
+  float* Wm;
+  float* sig;
+  int* sweeps;
+  int warm;
+  // residual sums
+  int nb_rpca, nb_apply;
+  double* partials;          // [2 * nb_rpca + nb_apply][kNumSums]
+  double* dsums;             // [kNumSums]
+  double* hsums;             // pinned: [kNumSums] sums, then sweeps (as int) and sigma
+  double y_norm;
+  int have_input;
+};
+
+extern "C" {
+
+void ot_rpca_default_params(ot_rpca_params* p) {
+  if (!p) return;
+  memset(p, 0, sizeof *p);
+  p->T = 2;
+  p->H = p->W = 1;
+  p->lambda = 0.02;
+  p->gamma = 0.0;           // <= 0: lambda * sqrt(max(N, T))
+  p->kappa = 0.005;
+  p->mu = 3.0;
+  p->rho = 1.0;
+  p->n_inner = 1;
+  p->tol = 1e-5;
+  p->max_iter = 5000;
+  p->check_every = 1;
+  p->svt_max_sweeps = 30;
+  p->prox_kernel = OT_KERNEL_AUTO;
+}
+
+int ot_rpca_destroy(ot_rpca_t h) {
+  if (!h) return OT_OK;
+  if (h->prox) ot_prox_destroy(h->prox);
+  if (h->slab) cudaFree(h->slab);
+  if (h->gram_partials) cudaFree(h->gram_partials);
+  if (h->partials) cudaFree(h->partials);
+  if (h->hsums) cudaFreeHost(h->hsums);
+  free(h);
+  return OT_OK;
+}
+
+int ot_rpca_create(const ot_rpca_params* params, void* cuda_stream, ot_rpca_t* out) {
+  if (!params || !out) return fail(OT_EINVAL, "ot_rpca_create: params and out must be non-NULL");
+  *out = nullptr;
+  ot_rpca_params p = *params;
+  if (p.T < 2 || p.T > 128) return fail(OT_EINVAL, "ot_rpca_create: T must be in [2, 128] (got %d)", p.T);
+  if (p.H < 1 || p.W < 1) return fail(OT_EINVAL, "ot_rpca_create: H, W must be >= 1");
+  if (!(p.lambda > 0) || !(p.kappa > 0) || !(p.mu > 0) || !(p.rho > 0))
+    return fail(OT_EINVAL, "ot_rpca_create: lambda, kappa, mu, rho must be > 0");
+  if (!isfinite(p.gamma)) return fail(OT_EINVAL, "ot_rpca_create: gamma must be finite");
+  if (p.n_inner < 1) return fail(OT_EINVAL, "ot_rpca_create: n_inner must be >= 1");
+  if (p.max_iter < 0 || p.check_every < 1 || p.svt_max_sweeps < 1)
+    return fail(OT_EINVAL, "ot_rpca_create: max_iter >= 0, check_every >= 1, svt_max_sweeps >= 1 required");
+  if (!(p.tol >= 0)) return fail(OT_EINVAL, "ot_rpca_create: tol must be >= 0");
+  const double N = (double)p.H * p.W;
+  if (p.gamma <= 0) p.gamma = p.lambda * sqrt(N > p.T ? N : (double)p.T);
+
+  ot_rpca* h = (ot_rpca*)calloc(1, sizeof(ot_rpca));
+  if (!h) return fail(OT_ENOMEM, "ot_rpca_create: host allocation failed");
+  h->prm = p;
+  h->stream = (cudaStream_t)cuda_stream;
+  h->G.T = p.T;
+  h->G.H = p.H;
+  h->G.W = p.W;
+  h->G.Wp = (p.W + 3) / 4 * 4;
+  h->G.plane = (long long)p.H * h->G.Wp;
+  h->C.lam = (float)p.lambda;
+  h->C.rho = (float)p.rho;
+  h->TP = svt_padded_T(p.T);
+
+  // the inner prox: B = T-1 pairs, weight kappa / rho (line 11)
+  ot_prox_params pp;
+  ot_prox_default_params(&pp);
+  pp.B = p.T - 1;
+  pp.H = p.H;
+  pp.W = p.W;
+  pp.mode = OT_MODE_PROX;
+  pp.mu = p.mu;
+  pp.rho = p.kappa / p.rho;
+  pp.kernel = p.prox_kernel;
+  pp.use_graph = 0;
+  int rc = ot_prox_create(&pp, cuda_stream, &h->prox);
+  if (rc != OT_OK) {
+    ot_rpca_destroy(h);
+    return rc;
+  }
+
+  const size_t plane = (size_t)h->G.plane;
+  const size_t nframe = (size_t)p.T * plane, npair = (size_t)(p.T - 1) * plane;
+  cudaError_t e = cudaMalloc(&h->slab, (8 * nframe + 4 * npair) * sizeof(float));
+  if (e != cudaSuccess) {
+    ot_rpca_destroy(h);
+    return cuda_fail(e, "ot_rpca_create: cudaMalloc(state)");
+  }
+  float* q = h->slab;
+  RpcaPlanes& P = h->P;
+  P.X = q; q += nframe;
+  P.L = q; q += nframe;
+  P.A = q; q += nframe;
+  P.Tm = q; q += nframe;
+  P.D = q; q += nframe;
+  P.Y = q; q += nframe;
+  P.S = q; q += nframe;
+  P.LD = q; q += nframe;
+  P.Bz = q; q += npair;
+  P.Cw = q; q += npair;
+  P.zprev = q; q += npair;
+  P.wprev = q; q += npair;
+  P.z = h->prox->x0;
+  P.w = h->prox->x1;
+  P.p0 = h->prox->p0;
+  P.p1 = h->prox->p1;
+
+  const int TP = h->TP;
+  const int ng = svt_gram_blocks((long long)plane);
+  h->nb_rpca = rpca_num_blocks(h->G);
+  int gy = 1;
+  h->nb_apply = svt_apply_blocks((long long)plane, p.T, &gy) * gy;
+  const size_t svt_bytes = (size_t)ng * TP * TP * sizeof(double) + (size_t)TP * TP * sizeof(double) +
+                           (size_t)3 * TP * TP * sizeof(float) + 64;
+  e = cudaMalloc(&h->gram_partials, svt_bytes);
+  if (e == cudaSuccess) {
+    h->Gm = h->gram_partials + (size_t)ng * TP * TP;
+    h->V = reinterpret_cast<float*>(h->Gm + (size_t)TP * TP);
+    h->Wm = h->V + (size_t)TP * TP;
+    h->sig = h->Wm + (size_t)TP * TP;
+    h->sweeps = reinterpret_cast<int*>(h->sig + (size_t)TP * TP);
+    e = cudaMalloc(&h->partials, ((size_t)(2 * h->nb_rpca + h->nb_apply) * kNumSums + kNumSums) * sizeof(double));
+  }
+  if (e == cudaSuccess) {
+    h->dsums = h->partials + (size_t)(2 * h->nb_rpca + h->nb_apply) * kNumSums;
+    e = cudaMallocHost(&h->hsums, (kNumSums + 2 + 128) * sizeof(double));
+  }
+  if (e == cudaSuccess) e = svt_prepare();
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->slab, 0, (8 * nframe + 4 * npair) * sizeof(float), h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) {
+    ot_rpca_destroy(h);
+    return cuda_fail(e, "ot_rpca_create: workspace");
+  }
+  *out = h;
+  return OT_OK;
+}
+
+int ot_rpca_get_params(ot_rpca_t h, ot_rpca_params* out) {
+  if (!h || !out) return fail(OT_EINVAL, "ot_rpca_get_params: NULL argument");
+  *out = h->prm;
+  return OT_OK;
+}
+
+int ot_rpca_reset(ot_rpca_t h) {
+  if (!h) return fail(OT_EINVAL, "ot_rpca_reset: NULL handle");
+  const size_t plane = (size_t)h->G.plane;
+  const size_t nframe = (size_t)h->prm.T * plane, npair = (size_t)(h->prm.T - 1) * plane;
+  // every plane but Y
+  OT_CUDA(cudaMemsetAsync(h->P.X, 0, 5 * nframe * sizeof(float), h->stream), "ot_rpca_reset");
+  OT_CUDA(cudaMemsetAsync(h->P.S, 0, (2 * nframe + 4 * npair) * sizeof(float), h->stream), "ot_rpca_reset");
+  h->warm = 0;
+  return ot_prox_reset(h->prox);
+}
+
+int ot_rpca_set_input(ot_rpca_t h, const float* Y) {
+  if (!h || !Y) return fail(OT_EINVAL, "ot_rpca_set_input: NULL argument");
+  const size_t wb = (size_t)h->G.W * sizeof(float);
+  OT_CUDA(cudaMemcpy2DAsync(h->P.Y, (size_t)h->G.Wp * sizeof(float), Y, wb, wb, (size_t)h->G.T * h->G.H,
+                            cudaMemcpyDefault, h->stream),
+          "ot_rpca_set_input: copy");
+  OT_CUDA(rpca_launch_sumsq(h->G, h->P.Y, h->partials, h->stream), "ot_rpca_set_input: ||Y||");
+  OT_CUDA(launch_finalize_sums(h->partials, h->nb_rpca, h->dsums, h->stream), "ot_rpca_set_input: ||Y||");
+  OT_CUDA(cudaMemcpyAsync(h->hsums, h->dsums, sizeof(double), cudaMemcpyDeviceToHost, h->stream), "ot_rpca_set_input");
+  OT_CUDA(cudaStreamSynchronize(h->stream), "ot_rpca_set_input: sync");
+  h->y_norm = sqrt(h->hsums[0]);
+  if (!isfinite(h->y_norm)) return fail(OT_ENONFINITE, "ot_rpca_set_input: Y has non-finite values");
+  h->have_input = 1;
+  return OT_OK;
+}
+
+}  // extern "C"
+
+// Enqueue one outer iteration; `sums` also finalises the residual sums and
+// copies them (with the SVT diagnostics) to the pinned host buffer.
+static int enqueue_outer(ot_rpca* h, bool sums) {
+  const long long plane = h->G.plane;
+  const long long N = plane;   // rows of the N x T matrix: one frame plane (padding columns are zero)
+  OT_CUDA(rpca_launch_pre(h->G, h->C, h->P, h->partials, h->stream), "rpca pre");
+  OT_CUDA(svt_launch_gram(h->P.LD, plane, N, h->prm.T, h->gram_partials, h->Gm, h->stream), "svt gram");
+  OT_CUDA(svt_launch_eig(h->Gm, h->prm.T, h->warm, (float)(h->prm.gamma / h->prm.rho), h->prm.svt_max_sweeps, 1e-6f,
+                         h->V, h->Wm, h->sig, h->sweeps, h->stream),
+          "svt eig");
+  h->warm = 1;
+  OT_CUDA(svt_launch_apply(h->P.LD, plane, N, h->prm.T, h->Wm, h->P.Tm, plane, true,
+                           h->partials + (size_t)h->nb_rpca * kNumSums, h->stream),
+          "svt apply");
+  int rc = ot_prox_step(h->prox, h->prm.n_inner);
+  if (rc != OT_OK) return rc;
+  OT_CUDA(rpca_launch_post(h->G, h->P, h->partials + (size_t)(h->nb_rpca + h->nb_apply) * kNumSums, h->stream),
+          "rpca post");
+  if (sums) {
+    OT_CUDA(launch_finalize_sums(h->partials, 2 * h->nb_rpca + h->nb_apply, h->dsums, h->stream), "rpca finalize");
+    OT_CUDA(cudaMemcpyAsync(h->hsums, h->dsums, kNumSums * sizeof(double), cudaMemcpyDeviceToHost, h->stream),
+            "rpca sums copy");
+    OT_CUDA(cudaMemcpyAsync(reinterpret_cast<int*>(h->hsums + kNumSums), h->sweeps, sizeof(int),
+                            cudaMemcpyDeviceToHost, h->stream),
+            "rpca sweeps copy");
+    OT_CUDA(cudaMemcpyAsync(reinterpret_cast<float*>(h->hsums + kNumSums + 2), h->sig, h->TP * sizeof(float),
+                            cudaMemcpyDeviceToHost, h->stream),
+            "rpca sigma copy");
+    OT_CUDA(cudaMemcpyAsync(h->prox->herr, h->prox->derr, sizeof(int), cudaMemcpyDeviceToHost, h->stream),
+            "rpca error flag copy");
+  }
+  return OT_OK;
+}
+
+static void fill_rpca_result(const ot_rpca* h, ot_rpca_result* r) {
+  const double* s = h->hsums;
+  const double ny = fmax(h->y_norm, 1e-30);
+  r->res_pri = sqrt(s[2] + s[3] + s[4] + s[5]) / ny;
+  r->res_dual = h->prm.rho * sqrt(s[0] + s[1] + s[6] + s[7]) / ny;
+  r->svt_sweeps = *reinterpret_cast<const int*>(h->hsums + kNumSums);
+  const float* sig = reinterpret_cast<const float*>(h->hsums + kNumSums + 2);
+  int rank = 0;
+  for (int i = 0; i < h->prm.T; ++i) rank += sig[i] > (float)(h->prm.gamma / h->prm.rho);
+  r->svt_rank = rank;
+}
+
+static bool rpca_sums_bad(const double* s) {
+  for (int k = 0; k < kNumSums; ++k)
+    if (!isfinite(s[k])) return true;
+  return false;
+}
+
+extern "C" {
+
+int ot_rpca_step(ot_rpca_t h, int32_t n_outer) {
+  if (!h) return fail(OT_EINVAL, "ot_rpca_step: NULL handle");
+  if (!h->have_input) return fail(OT_EINVAL, "ot_rpca_step: no input (call ot_rpca_set_input)");
+  if (n_outer < 0) return fail(OT_EINVAL, "ot_rpca_step: n_outer must be >= 0");
+  for (int k = 0; k < n_outer; ++k) {
+    const int rc = enqueue_outer(h, false);
+    if (rc != OT_OK) return rc;
+  }
+  return OT_OK;
+}
+
+int ot_rpca_iterate_checked(ot_rpca_t h, int32_t n_outer, ot_rpca_result* res) {
+  if (!h) return fail(OT_EINVAL, "ot_rpca_iterate_checked: NULL handle");
+  if (!h->have_input) return fail(OT_EINVAL, "ot_rpca_iterate_checked: no input (call ot_rpca_set_input)");
+  if (n_outer < 1) return fail(OT_EINVAL, "ot_rpca_iterate_checked: n_outer must be >= 1");
+  for (int k = 0; k < n_outer; ++k) {
+    const int rc = enqueue_outer(h, k == n_outer - 1);
+    if (rc != OT_OK) return rc;
+  }
+  OT_CUDA(cudaStreamSynchronize(h->stream), "ot_rpca_iterate_checked: sync");
+  if (*h->prox->herr) return fail(OT_ETIMEOUT, "a bounded device wait expired in the prox kernel");
+  ot_rpca_result r;
+  memset(&r, 0, sizeof r);
+  r.iters = n_outer;
+  fill_rpca_result(h, &r);
+  const bool bad = rpca_sums_bad(h->hsums);
+  r.status = bad ? OT_ENONFINITE : OT_OK;
+  if (res) *res = r;
+  if (bad) return fail(OT_ENONFINITE, "ot_rpca_iterate_checked: non-finite residuals");
+  return OT_OK;
+}
+
+int ot_rpca_solve(ot_rpca_t h, ot_rpca_result* res) {
+  if (!h) return fail(OT_EINVAL, "ot_rpca_solve: NULL handle");
+  if (!h->have_input) return fail(OT_EINVAL, "ot_rpca_solve: no input (call ot_rpca_set_input)");
+  ot_rpca_result r;
+  memset(&r, 0, sizeof r);
+  r.res_pri = r.res_dual = INFINITY;
+  int status = OT_ENOTCONV, k = 0;
+  while (k < h->prm.max_iter) {
+    const int n = (h->prm.max_iter - k) < h->prm.check_every ? (h->prm.max_iter - k) : h->prm.check_every;
+    ot_rpca_result rr;
+    const int rc = ot_rpca_iterate_checked(h, n, &rr);
+    k += n;
+    if (rc == OT_ENONFINITE) {
+      r = rr;
+      status = OT_ENONFINITE;
+      break;
+    }
+    if (rc != OT_OK) return rc;
+    r = rr;
+    if (fmax(r.res_pri, r.res_dual) <= h->prm.tol) {
+      status = OT_OK;
+      break;
+    }
+  }
+  r.iters = k;
+  r.status = status;
+  if (res) *res = r;
+  if (status == OT_ENOTCONV)
+    fail(OT_ENOTCONV, "ot_rpca_solve: max_iter = %d reached (res_pri %.3g, res_dual %.3g)", h->prm.max_iter,
+         r.res_pri, r.res_dual);
+  if (status == OT_ENONFINITE) fail(OT_ENONFINITE, "ot_rpca_solve: non-finite values");
+  return status;
+}
+
+int ot_rpca_get(ot_rpca_t h, int32_t var, float* out) {
+  if (!h || !out) return fail(OT_EINVAL, "ot_rpca_get: NULL argument");
+  const RpcaPlanes& P = h->P;
+  const float* src = nullptr;
+  int nf = h->prm.T;
+  switch (var) {
+    case OT_RPCA_S: src = P.S; break;
+    case OT_RPCA_L: src = P.L; break;
+    case OT_RPCA_X: src = P.X; break;
+    case OT_RPCA_T: src = P.Tm; break;
+    case OT_RPCA_A: src = P.A; break;
+    case OT_RPCA_D: src = P.D; break;
+    case OT_RPCA_B: src = P.Bz; nf = h->prm.T - 1; break;
+    case OT_RPCA_C: src = P.Cw; nf = h->prm.T - 1; break;
+    case OT_RPCA_Z: src = P.z; nf = h->prm.T - 1; break;
+    case OT_RPCA_W: src = P.w; nf = h->prm.T - 1; break;
+    case OT_RPCA_MX: src = h->prox->Mx[h->prox->cur]; nf = h->prm.T - 1; break;
+    case OT_RPCA_MY: src = h->prox->My[h->prox->cur]; nf = h->prm.T - 1; break;
+    case OT_RPCA_R: src = h->prox->r; nf = h->prm.T - 1; break;
+    case OT_RPCA_DUAL: src = h->prox->a[h->prox->cur]; nf = h->prm.T - 1; break;
+    default: return fail(OT_EINVAL, "ot_rpca_get: unknown variable %d", var);
+  }
+  const size_t wb = (size_t)h->G.W * sizeof(float);
+  OT_CUDA(cudaMemcpy2DAsync(out, wb, src, (size_t)h->G.Wp * sizeof(float), wb, (size_t)nf * h->G.H,
+                            cudaMemcpyDefault, h->stream),
+          "ot_rpca_get: copy");
+  OT_CUDA(cudaStreamSynchronize(h->stream), "ot_rpca_get: sync");
+  return OT_OK;
+}
+
+int ot_svt(const float* X, float* Y, int64_t N, int32_t T, double theta, void* cuda_stream) {
+  if (!X || !Y) return fail(OT_EINVAL, "ot_svt: NULL argument");
+  if (N < 1 || T < 1 || T > 128) return fail(OT_EINVAL, "ot_svt: need N >= 1 and 1 <= T <= 128");
+  if (!(theta >= 0) || !isfinite(theta)) return fail(OT_EINVAL, "ot_svt: theta must be >= 0");
+  if (X == Y) return fail(OT_EINVAL, "ot_svt: X and Y must not alias");
+  const cudaStream_t st = (cudaStream_t)cuda_stream;
+  const int TP = svt_padded_T(T);
+  const int ng = svt_gram_blocks(N);
+  const size_t bytes = (size_t)ng * TP * TP * sizeof(double) + (size_t)TP * TP * sizeof(double) +
+                       (size_t)3 * TP * TP * sizeof(float) + 64;
+  OT_CUDA(svt_prepare(), "ot_svt: prepare");
+  void* ws = nullptr;
+  OT_CUDA(cudaMallocAsync(&ws, bytes, st), "ot_svt: cudaMallocAsync");
+  double* part = static_cast<double*>(ws);
+  double* Gm = part + (size_t)ng * TP * TP;
+  float* V = reinterpret_cast<float*>(Gm + (size_t)TP * TP);
+  float* Wm = V + (size_t)TP * TP;
+  float* sig = Wm + (size_t)TP * TP;
+  int* sweeps = reinterpret_cast<int*>(sig + (size_t)TP * TP);
+  cudaError_t e = svt_launch_gram(X, N, N, T, part, Gm, st);
+  if (e == cudaSuccess) e = svt_launch_eig(Gm, T, 0, (float)theta, 60, 1e-6f, V, Wm, sig, sweeps, st);
+  if (e == cudaSuccess) e = svt_launch_apply(X, N, N, T, Wm, Y, N, false, nullptr, st);
+  cudaError_t e2 = cudaFreeAsync(ws, st);
+  if (e != cudaSuccess) return cuda_fail(e, "ot_svt");
+  if (e2 != cudaSuccess) return cuda_fail(e2, "ot_svt: cudaFreeAsync");
+  return OT_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,177 @@
+// Elementwise passes of Algorithm 3 (RPCA+UOT-DF ADMM, Sec. IV-B.1) with
+// Phi_t = I, fused into two HBM passes over the frame planes [T][H][Wp].
+//
+// pre  (lines 4-9, and the inputs of lines 10-11):
+//   k_t = (x_t - l_t + a_t) + w^z_t (z_t + b_t) + w^w_t (w_t + c_t),
+//   sigma_t = 1 + w^z_t + w^w_t,  w^z_t = [t < T-1],  w^w_t = [t > 0]
+//   s_t = max(k_t / sigma_t - lambda / (rho sigma_t), 0)
+//   L   = 1/2 max(Tm - D + X - S + A, 0)
+//   X   = (Y + rho (S + L - A)) / (1 + rho)
+//   LD  = L + D                                   (the SVT input, line 10)
+//   p0_t = s_t - b_t,  p1_t = s_{t+1} - c_{t+1}   (the prox centres, line 11)
+// and keeps z, w of this iteration for the dual residual.
+// post (lines 12-15):
+//   A += X - S - L,  D += L - Tm,  b_t += z_t - s_t,  c_{t+1} += w_{t+1} - s_{t+1}
+// with the ADMM residual sums.  Readings (see the oracle): the sign of the
+// A-update follows the augmented Lagrangian; the x-update keeps rho; S >= 0.
+//
+// Partial-sum slots (kNumSums per block): 0 ||dX||^2, 1 ||dTm||^2 (the SVT
+// apply), 2 ||X-S-L||^2, 3 ||L-Tm||^2, 4 ||z-s_t||^2, 5 ||w-s_{t+1}||^2,
+// 6 ||dz||^2, 7 ||dw||^2.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "device_util.cuh"
+#include "otprox_internal.cuh"
+
+namespace otp {
+namespace {
+
+constexpr int kRpcaThreads = 256;
+
+__global__ void __launch_bounds__(kRpcaThreads)
+rpca_pre_kernel(const RpcaGeom g, const RpcaCoeffs c, const RpcaPlanes P, double* __restrict__ partials) {
+  float acc[kNumSums] = {};
+  const long long per_frame = g.plane / 4;             // float4 groups per frame
+  const long long total = per_frame * g.T;
+  const float rho = c.rho, inv1r = 1.f / (1.f + c.rho);
+  for (long long q = blockIdx.x * (long long)kRpcaThreads + threadIdx.x; q < total;
+       q += (long long)gridDim.x * kRpcaThreads) {
+    const int t = (int)(q / per_frame);
+    const long long o = 4 * q;                          // offset in [T][plane]
+    const long long op = o - (long long)t * g.plane;   // offset inside the frame
+    const bool hz = t < g.T - 1, hw = t > 0;
+    const float sg = 1.f + (hz ? 1.f : 0.f) + (hw ? 1.f : 0.f);
+    const float inv_sg = 1.f / sg;
+    const float thr = c.lam / (rho * sg);
+    const float4 x = ldg4(P.X + o), l = ldg4(P.L + o), a = ldg4(P.A + o), tm = ldg4(P.Tm + o), d = ldg4(P.D + o),
+                 y = ldg4(P.Y + o);
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    const long long oz = (long long)t * g.plane + op;          // pair t
+    const long long ow = (long long)(t - 1) * g.plane + op;    // pair t-1
+    const float4 zt = hz ? ldg4(P.z + oz) : z4, bt = hz ? ldg4(P.Bz + oz) : z4;
+    const float4 wt = hw ? ldg4(P.w + ow) : z4, ct = hw ? ldg4(P.Cw + ow) : z4;
+    float4 s4, l4, x4, ld4, p04, p14;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const float k = (f4c(x, e) - f4c(l, e) + f4c(a, e)) + (f4c(zt, e) + f4c(bt, e)) + (f4c(wt, e) + f4c(ct, e));
+      const float s = fmaxf(k * inv_sg - thr, 0.f);
+      const float lv = 0.5f * fmaxf(f4c(tm, e) - f4c(d, e) + f4c(x, e) - s + f4c(a, e), 0.f);
+      const float xv = (f4c(y, e) + rho * (s + lv - f4c(a, e))) * inv1r;
+      const float dx = xv - f4c(x, e);
+      acc[0] = fmaf(dx, dx, acc[0]);
+      f4(s4, e) = s;
+      f4(l4, e) = lv;
+      f4(x4, e) = xv;
+      f4(ld4, e) = lv + f4c(d, e);
+      f4(p04, e) = s - f4c(bt, e);
+      f4(p14, e) = s - f4c(ct, e);
+    }
+    stg4v(P.S + o, s4);
+    stg4v(P.L + o, l4);
+    stg4v(P.X + o, x4);
+    stg4v(P.LD + o, ld4);
+    if (hz) {
+      stg4v(P.p0 + oz, p04);
+      stg4v(P.zprev + oz, zt);
+    }
+    if (hw) {
+      stg4v(P.p1 + ow, p14);
+      stg4v(P.wprev + ow, wt);
+    }
+  }
+  block_sums_to<kRpcaThreads>(acc, partials + (size_t)blockIdx.x * kNumSums);
+}
+
+__global__ void __launch_bounds__(kRpcaThreads)
+rpca_post_kernel(const RpcaGeom g, const RpcaPlanes P, double* __restrict__ partials) {
+  float acc[kNumSums] = {};
+  const long long per_frame = g.plane / 4;
+  const long long total = per_frame * g.T;
+  for (long long q = blockIdx.x * (long long)kRpcaThreads + threadIdx.x; q < total;
+       q += (long long)gridDim.x * kRpcaThreads) {
+    const int t = (int)(q / per_frame);
+    const long long o = 4 * q;
+    const long long op = o - (long long)t * g.plane;
+    const bool hz = t < g.T - 1, hw = t > 0;
+    const float4 x = ldg4(P.X + o), s = ldg4(P.S + o), l = ldg4(P.L + o), tm = ldg4(P.Tm + o);
+    float4 a = ldg4(P.A + o), d = ldg4(P.D + o);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const float r1 = f4c(x, e) - f4c(s, e) - f4c(l, e);
+      const float r2 = f4c(l, e) - f4c(tm, e);
+      f4(a, e) += r1;
+      f4(d, e) += r2;
+      acc[2] = fmaf(r1, r1, acc[2]);
+      acc[3] = fmaf(r2, r2, acc[3]);
+    }
+    stg4v(P.A + o, a);
+    stg4v(P.D + o, d);
+    if (hz) {   // pair t: z_t pairs with s_t
+      const long long oz = (long long)t * g.plane + op;
+      const float4 z = ldg4(P.z + oz), zp = ldg4(P.zprev + oz);
+      float4 b = ldg4(P.Bz + oz);
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const float r = f4c(z, e) - f4c(s, e);
+        const float dz = f4c(z, e) - f4c(zp, e);
+        f4(b, e) += r;
+        acc[4] = fmaf(r, r, acc[4]);
+        acc[6] = fmaf(dz, dz, acc[6]);
+      }
+      stg4v(P.Bz + oz, b);
+    }
+    if (hw) {   // pair t-1: w_{t} pairs with s_t
+      const long long ow = (long long)(t - 1) * g.plane + op;
+      const float4 w = ldg4(P.w + ow), wp = ldg4(P.wprev + ow);
+      float4 cc = ldg4(P.Cw + ow);
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const float r = f4c(w, e) - f4c(s, e);
+        const float dw = f4c(w, e) - f4c(wp, e);
+        f4(cc, e) += r;
+        acc[5] = fmaf(r, r, acc[5]);
+        acc[7] = fmaf(dw, dw, acc[7]);
+      }
+      stg4v(P.Cw + ow, cc);
+    }
+  }
+  block_sums_to<kRpcaThreads>(acc, partials + (size_t)blockIdx.x * kNumSums);
+}
+
+// ||Y||^2 (once per input) into partials[block][0].
+__global__ void __launch_bounds__(kRpcaThreads)
+sumsq_kernel(const float* __restrict__ Y, long long n4, double* __restrict__ partials) {
+  float acc[kNumSums] = {};
+  for (long long q = blockIdx.x * (long long)kRpcaThreads + threadIdx.x; q < n4; q += (long long)gridDim.x * kRpcaThreads) {
+    const float4 v = ldg4(Y + 4 * q);
+    acc[0] += v.x * v.x + v.y * v.y + v.z * v.z + v.w * v.w;
+  }
+  block_sums_to<kRpcaThreads>(acc, partials + (size_t)blockIdx.x * kNumSums);
+}
+
+}  // namespace
+
+int rpca_num_blocks(const RpcaGeom& g) {
+  const long long n4 = g.plane / 4 * g.T;
+  const long long nb = (n4 + kRpcaThreads - 1) / kRpcaThreads;
+  return (int)(nb < 152 * 4 ? (nb < 1 ? 1 : nb) : 152 * 4);
+}
+
+cudaError_t rpca_launch_pre(const RpcaGeom& g, const RpcaCoeffs& c, const RpcaPlanes& P, double* partials,
+                            cudaStream_t st) {
+  rpca_pre_kernel<<<rpca_num_blocks(g), kRpcaThreads, 0, st>>>(g, c, P, partials);
+  return cudaGetLastError();
+}
+
+cudaError_t rpca_launch_post(const RpcaGeom& g, const RpcaPlanes& P, double* partials, cudaStream_t st) {
+  rpca_post_kernel<<<rpca_num_blocks(g), kRpcaThreads, 0, st>>>(g, P, partials);
+  return cudaGetLastError();
+}
+
+cudaError_t rpca_launch_sumsq(const RpcaGeom& g, const float* Y, double* partials, cudaStream_t st) {
+  sumsq_kernel<<<rpca_num_blocks(g), kRpcaThreads, 0, st>>>(Y, g.plane / 4 * g.T, partials);
+  return cudaGetLastError();
+}
+
+}  // namespace otp

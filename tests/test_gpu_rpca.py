@@ -1,0 +1,199 @@
+"""GPU parity of the SVT (Gram + Jacobi route) and of Algorithm 3 (RPCA+UOT-DF,
+Phi = I) against the FP64 oracle (one-sided Jacobi SVD, NumPy Algorithm 3).
+
+Tolerances.  Elementwise steps are exact to FP32 rounding.  The SVT goes
+through X^T X: its T x T eigenproblem is solved in FP32, so eigenvalue errors
+are about u ||X||_2^2 in absolute terms and a singular value sigma moves by
+about u ||X||_2^2 / (2 sigma).  Components near the threshold theta are the
+sensitive ones, and their weight max(sigma - theta, 0) is small, so the
+output error relative to ||shrink*(X)|| is about u (sigma_max / theta) (plus
+the u sqrt(T) of the final product).  The tests derive the bound from that
+estimate with a factor of 8 margin, floored at the 1e-5 stated for the FP32
+form.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import rpca as R
+from oracle import svt as SV
+from synth import rng_for, rpca_video
+
+pytestmark = pytest.mark.gpu
+
+U32 = 2.0 ** -24
+
+
+def svt_bound(X, theta):
+    s = np.linalg.svd(X, compute_uv=False)
+    return max(1e-5, 8 * U32 * (s[0] / max(theta, 1e-30) + np.sqrt(X.shape[1])))
+
+
+@pytest.mark.parametrize("N,T,rank", [(3000, 8, 2), (4096, 33, 3), (20000, 64, 3), (5000, 100, 4), (999, 5, 1)])
+def test_svt_matches_oracle(lib, N, T, rank):
+    rng = np.random.default_rng(N + T)
+    U = rng.uniform(0, 1, (N, rank))
+    V = rng.uniform(0.2, 1, (T, rank))
+    Xm = (U @ V.T + 0.02 * rng.normal(size=(N, T))).astype(np.float32)     # N x T
+    theta = 0.02 * np.sqrt(max(N, T)) * 3
+    ref = SV.svt(Xm.astype(np.float64), theta)
+    Xg = torch.from_numpy(np.ascontiguousarray(Xm.T)).cuda()               # T columns of N
+    Yg = lib.svt(Xg, theta).cpu().numpy().T.astype(np.float64)
+    err = np.linalg.norm(Yg - ref) / np.linalg.norm(ref)
+    assert err <= svt_bound(Xm.astype(np.float64), theta), err
+    # the rank kept equals the oracle's count of singular values above theta
+    s_ref = np.linalg.svd(ref, compute_uv=False)
+    assert np.sum(np.linalg.svd(Yg, compute_uv=False) > 1e-3 * s_ref[0]) == np.sum(s_ref > 1e-3 * s_ref[0])
+
+
+def test_svt_zero_threshold_is_identity(lib):
+    rng = np.random.default_rng(1)
+    Xm = rng.normal(size=(16, 500)).astype(np.float32)
+    Y = lib.svt(torch.from_numpy(Xm).cuda(), 0.0).cpu().numpy()
+    assert np.linalg.norm(Y - Xm) <= 1e-5 * np.linalg.norm(Xm)
+
+
+def test_svt_large_threshold_is_zero(lib):
+    rng = np.random.default_rng(2)
+    Xm = rng.normal(size=(12, 300)).astype(np.float32)
+    theta = 2 * np.linalg.norm(Xm, 2)
+    Y = lib.svt(torch.from_numpy(Xm).cuda(), theta).cpu().numpy()
+    assert np.max(np.abs(Y)) == 0.0
+
+
+RP = dict(lam=0.02, kappa=0.005, mu=3.0, rho=1.0)
+
+
+def oracle_rpca(Y, k, gamma, n_inner=1):
+    prm = R.RpcaParams(lam=RP["lam"], gamma=gamma, kappa=RP["kappa"], mu=RP["mu"], rho=RP["rho"], n_inner=n_inner)
+    st = R.zero_state(*Y.shape)
+    Yd = Y.astype(np.float64)
+    res = None
+    for _ in range(k):
+        st, pri, dual = R.outer_iteration(st, Yd, prm)
+        res = (pri, dual)
+    return st, res
+
+
+ALL_VARS = [("S", "S"), ("L", "L"), ("X", "X"), ("T", "Tm"), ("A", "A"), ("D", "D"), ("B", "B"), ("C", "C")]
+PROX_VARS = [("Z", "x0"), ("W", "x1"), ("Mx", "Mx"), ("My", "My"), ("r", "r"), ("a", "a")]
+
+
+# The dual accumulators sum differences of nearly equal operands (A += X - S - L,
+# D += L - Tm, b += z - s, c += w - s): their rounding error is relative to
+# those operands, not to their own (small) norm.
+OPERANDS = {"A": ("X",), "D": ("L", "Tm"), "B": ("S",), "C": ("S",)}
+
+
+def rpca_errors(rp, st, scale=None):
+    """Relative l2 error of every variable, against a common scale (the data
+    norm ||Y||) when ``scale`` is given, else against the larger of its own
+    norm and its operands' norm, floored at 1e-6 ||Y||."""
+    ny = np.linalg.norm(rp_Y(st))
+    out = {}
+    for name, attr in ALL_VARS + PROX_VARS:
+        o = getattr(st.prox, attr) if (name, attr) in PROX_VARS else getattr(st, attr)
+        g = rp.get(name).double().cpu().numpy()
+        if scale:
+            ref = scale
+        else:
+            ref = max([np.linalg.norm(o), 1e-6 * ny] + [np.linalg.norm(getattr(st, a)) for a in OPERANDS.get(name, ())])
+        out[name] = np.linalg.norm(g - o) / ref
+    return out
+
+
+def rp_Y(st):
+    """The data scale of a state: X + A (= Y / (1 + rho) + ... ) is close to
+    Y; use X, which is always of the data's size."""
+    return st.X
+
+
+@pytest.mark.parametrize("T,H,W", [(6, 24, 28), (9, 33, 17)])
+@pytest.mark.parametrize("k", [1, 5, 30])
+def test_rpca_elementwise_and_prox_parity(lib, T, H, W, k):
+    """gamma above ||L + D||_2 makes the SVT output exactly zero on both sides,
+    so this isolates the fused elementwise passes and the inner prox: every
+    variable within 1e-5 of the oracle, relative to its own norm."""
+    Y, _, _ = rpca_video(rng_for(1, 40 + T), T=T, H=H, W=W, n_blobs=3)
+    gamma = 1e6
+    with lib.Rpca(T, H, W, gamma=gamma, **RP) as rp:
+        rp.set_input(Y)
+        res = rp.iterate_checked(k)
+        st, (pri, dual) = oracle_rpca(Y, k, gamma)
+        assert np.max(np.abs(rp.get("T").cpu().numpy())) == 0.0
+        err = rpca_errors(rp, st)
+    for name, e in err.items():
+        assert e <= 1e-5 * max(1, k / 10), (name, e)
+    assert abs(res["res_pri"] - pri) <= 1e-4 * pri + 1e-9
+    assert abs(res["res_dual"] - dual) <= 1e-4 * dual + 1e-9
+
+
+@pytest.mark.parametrize("T,H,W", [(6, 24, 28), (9, 33, 17)])
+@pytest.mark.parametrize("k", [1, 5, 30])
+def test_rpca_trajectory_parity(lib, T, H, W, k):
+    """Full Algorithm 3 with the paper's gamma = lambda sqrt(max(N, T)).  The
+    FP32 SVT error (bounded in svt_bound) propagates into every variable as an
+    absolute error of that size relative to the data, so all variables are
+    measured against ||Y||; the SVT output itself against its own norm."""
+    Y, _, _ = rpca_video(rng_for(1, 40 + T), T=T, H=H, W=W, n_blobs=3)
+    gamma = RP["lam"] * np.sqrt(max(H * W, T))
+    with lib.Rpca(T, H, W, **RP) as rp:
+        rp.set_input(Y)
+        res = rp.iterate_checked(k)
+        st, (pri, dual) = oracle_rpca(Y, k, gamma)
+        tol = svt_bound((st.L + st.D).reshape(T, -1).T, gamma / RP["rho"]) * max(1, k / 5)
+        err = rpca_errors(rp, st, scale=np.linalg.norm(Y.astype(np.float64)))
+        tm = rpca_errors(rp, st)["T"]
+    for name, e in err.items():
+        assert e <= tol, (name, e, tol)
+    assert tm <= tol or np.linalg.norm(st.Tm) == 0
+    assert abs(res["res_pri"] - pri) <= 1e-2 * pri + 1e-9
+    assert abs(res["res_dual"] - dual) <= 1e-2 * dual + 1e-9
+
+
+def test_rpca_solve_converges_and_matches_oracle(lib):
+    T, H, W = 6, 20, 20
+    Y, _, _ = rpca_video(rng_for(1, 50), T=T, H=H, W=W, n_blobs=2)
+    gamma = RP["lam"] * np.sqrt(max(H * W, T))
+    with lib.Rpca(T, H, W, tol=1e-6, max_iter=20000, **RP) as rp:
+        rp.set_input(Y)
+        res = rp.solve()
+        S = rp.get("S").double().cpu().numpy()
+        L = rp.get("L").double().cpu().numpy()
+    assert res["status"] == 0, res
+    prm = R.RpcaParams(lam=RP["lam"], gamma=gamma, kappa=RP["kappa"], mu=RP["mu"], rho=RP["rho"], tol=1e-6,
+                       max_iter=20000)
+    st, info = R.solve(Y, prm)
+    assert info["converged"]
+    # both are within ~tol of the same fixed point
+    ny = np.linalg.norm(Y)
+    assert np.linalg.norm(S - st.S) <= 1e-3 * ny
+    assert np.linalg.norm(L - st.L) <= 1e-3 * ny
+    assert np.min(S) >= 0 and np.min(L) >= 0
+
+
+def test_rpca_full_size_two_iterations(lib):
+    """The 64-frame 256x256 video (rank-3 clutter, 8 blobs, noise 0.02): two
+    outer iterations of the benchmark's step against the oracle."""
+    from synth import config2_video
+    Y, _, _ = config2_video()
+    T, H, W = Y.shape
+    gamma = RP["lam"] * np.sqrt(max(H * W, T))
+    with lib.Rpca(T, H, W, **RP) as rp:
+        rp.set_input(torch.from_numpy(Y).cuda())
+        res = rp.iterate_checked(2)
+        st, (pri, dual) = oracle_rpca(Y, 2, gamma)
+        tol = svt_bound((st.L + st.D).reshape(T, -1).T, gamma / RP["rho"])
+        err = rpca_errors(rp, st, scale=np.linalg.norm(Y.astype(np.float64)))
+        tm = rpca_errors(rp, st)["T"]
+    for name, e in err.items():
+        assert e <= tol, (name, e, tol)
+    assert tm <= tol
+    assert abs(res["res_pri"] - pri) <= 1e-2 * pri
+    assert abs(res["res_dual"] - dual) <= 1e-2 * dual
+
+
+def test_rpca_rejects_bad_parameters(lib):
+    for kw in (dict(T=1, H=4, W=4), dict(T=200, H=4, W=4), dict(T=4, H=4, W=4, n_inner=0)):
+        with pytest.raises(lib.OtError):
+            lib.Rpca(**kw)
