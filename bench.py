@@ -2,25 +2,35 @@
 """Benchmark of the unbalanced Beckmann-OT proximal hot path on GB300.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload prox|rpca]
+                    [--workload rpca|prox] [--n-inner I]
 
 Prints ONE JSON line (rank 0).  Workloads (synthetic, seeded):
 
-* ``prox`` -- Algorithm 1 on the 63 frame pairs of a 64-frame 256x256 blob
-  video (the prox batch of line 11 of Algorithm 3).  A step is one check
-  interval: 10 fused iterations, the last computing the FP64 stopping sums,
-  and the read-back of those sums.
+* ``rpca`` (default) -- one outer iteration of Algorithm 3 (RPCA+UOT-DF,
+  Phi = I) on a 64-frame 256x256 video (rank-3 clutter, 8 moving blobs that
+  appear and disappear, noise 0.02): the fused elementwise passes, the SVT
+  through the 64 x 64 Gram matrix, ``n_inner`` Algorithm 1 iterations on the
+  63 frame pairs, the dual updates, and the ADMM residuals read back.
+* ``prox`` -- one check interval of Algorithm 1 alone on the 63 frame pairs
+  of a 64-frame 256x256 blob video: 10 fused iterations, the last computing
+  the FP64 stopping sums, read back.
 
-The metric is prox pixel-iterations per second (B * H * W * iterations / s).
-Multi-GPU (torchrun): every rank solves its own batch (replicas, weak
-scaling); timing is the max over ranks.
+The metric is OT-prox pixel-iterations per second (B * H * W * prox
+iterations / s, B = 63 frame pairs).  Multi-GPU (torchrun): every rank solves
+its own video (replicas, weak scaling); timing is the max over ranks.
 """
 from __future__ import annotations
+
+import os
+
+# The oracle timings report one core: keep NumPy's BLAS and OpenMP pools to
+# one thread (set before NumPy loads).
+for _v in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
 
 import argparse
 import hashlib
 import json
-import os
 import statistics
 import subprocess
 import sys
@@ -34,8 +44,17 @@ sys.path.insert(0, ROOT)
 
 METRIC = "OT-prox pixel-iters/s"
 UNIT = "pixel-iter/s"
-BYTES_PER_PIXEL_ITER = {"prox": 56, "fixed_first": 48, "eval": 40}
-ITERS_PER_STEP = 10
+PROX_ITERS_PER_STEP = 10
+T_FRAMES, HEIGHT, WIDTH = 64, 256, 256
+PROX_KW = dict(mu=3.0, rho=0.01, kernel="tma", use_graph=True, check_every=PROX_ITERS_PER_STEP)
+RPCA_KW = dict(lam=0.02, kappa=0.005, mu=3.0, rho=1.0, check_every=1)
+PHASES = ["rpca_pre_kernel (Alg. 3 lines 4-9)", "gram_partial/reduce (SVT Gram)", "jacobi_svt_kernel (T x T eig)",
+          "svt_apply_kernel (SVT apply)", "prox_tma_kernel (Alg. 1 iterations)", "rpca_post_kernel (Alg. 3 lines 12-15)"]
+PROFILE_FILES = {  # kernel -> (ncu summary holding its DRAM traffic per launch, its source file)
+    "prox_tma_kernel": ("prox_tma_63x256x256.md", "prox_tma.cu"),
+    "rpca_pre_kernel": ("rpca_step_64x256x256.md", "rpca_kernels.cu"),
+    "rpca_post_kernel": ("rpca_step_64x256x256.md", "rpca_kernels.cu"),
+}
 
 
 def measured_peaks() -> dict:
@@ -43,32 +62,42 @@ def measured_peaks() -> dict:
     if os.path.exists(path):
         with open(path) as f:
             d = json.load(f)
-        return {"hbm_gbs": d["hbm_gbs"], "source": "measured"}
-    return {"hbm_gbs": 6800.0, "source": "fallback"}
+        return {"hbm_gbs": d["hbm_gbs"], "sm_max_mhz": d.get("sm_max_mhz", 2070.0), "source": "measured"}
+    return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0, "source": "fallback"}
 
 
-def kernel_source_hash() -> str:
+def jacobi_flops(T: int, sweeps: int) -> float:
+    """FP32 flops of one SVT eigensolve: per sweep (TP-1) rounds, each
+    rotating all TP^2 entries of A twice (rows, columns) and TP^2 of V at ~3
+    flops per entry; plus the three TP^3 products (warm start, final
+    V diag V^T)."""
+    TP = 16 if T <= 16 else 32 if T <= 32 else 64 if T <= 64 else 128
+    return sweeps * (TP - 1) * 9.0 * TP * TP + 3 * 2.0 * TP ** 3
+
+
+def source_hash(name: str) -> str:
     h = hashlib.sha256()
-    with open(os.path.join(ROOT, "paper_1909_00149_gb300", "csrc", "prox_tma.cu"), "rb") as f:
+    with open(os.path.join(ROOT, "paper_1909_00149_gb300", "csrc", name), "rb") as f:
         h.update(f.read())
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(kernel_tag: str) -> float | None:
-    """DRAM bytes per launch of the tiled iteration kernel from the committed
-    ncu summary, if it was taken on the current kernel source."""
-    path = os.path.join(ROOT, "profiles", "prox_tma_63x256x256.md")
+def ncu_traffic(kernel: str, tag: str) -> float | None:
+    """DRAM bytes per launch of ``kernel`` from its committed ncu summary, if
+    that summary was taken on the current kernel source (else None)."""
+    if kernel not in PROFILE_FILES:
+        return None
+    md, src = PROFILE_FILES[kernel]
+    path = os.path.join(ROOT, "profiles", md)
     if not os.path.exists(path):
         return None
     src_hash, traffic = None, None
     for line in open(path):
-        if line.startswith("source_sha256_16:"):
+        if line.startswith(f"source_sha256_16[{src}]:") or line.startswith("source_sha256_16:"):
             src_hash = line.split(":", 1)[1].strip()
-        if line.startswith(f"traffic_bytes_per_launch[{kernel_tag}]:"):
+        if line.startswith(f"traffic_bytes_per_launch[{tag}]:"):
             traffic = float(line.split(":", 1)[1].strip())
-    if src_hash != kernel_source_hash():
-        return None
-    return traffic
+    return traffic if src_hash == source_hash(src) else None
 
 
 class ClockSampler:
@@ -120,20 +149,146 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
-# --------------------------------------------------------------------- workloads
+# --------------------------------------------------------------------- inputs
+def rpca_inputs(rank: int, T=T_FRAMES, H=HEIGHT, W=WIDTH):
+    from synth import config2_video, rng_for, rpca_video
+    if rank == 0 and (T, H, W) == (T_FRAMES, HEIGHT, WIDTH):
+        return config2_video()[0]
+    return rpca_video(rng_for(1, 100 + rank), T, H, W)[0]
+
+
 def prox_inputs(rank: int):
     from synth import blob_video, rng_for
-    v = blob_video(rng_for(1, 100 + rank), 64, 256, 256, n_blobs=8)
+    v = blob_video(rng_for(1, 100 + rank), T_FRAMES, HEIGHT, WIDTH, n_blobs=8)
     return np.ascontiguousarray(v[:-1]), np.ascontiguousarray(v[1:])
 
 
-PROX_KW = dict(mu=3.0, rho=0.01, kernel="tma", use_graph=True, check_every=ITERS_PER_STEP)
+def rpca_phase_bytes(T: int, N: int, n_inner: int) -> list:
+    """Algorithmic DRAM bytes of each phase of one outer iteration (one read
+    and one write of each plane touched; frames T, pairs T-1, N pixels)."""
+    P = T - 1
+    return [4.0 * N * (10 * T + 8 * P),        # pre: reads X L A Tm D Y z b w c, writes S L X LD p0 p1 z' w'
+            4.0 * N * T,                      # Gram: reads L+D
+            0.0,                              # T x T eigensolver
+            4.0 * N * 3 * T,                  # apply: reads L+D, Tm; writes Tm
+            56.0 * N * P * n_inner,           # Algorithm 1: 56 B per pixel-iteration
+            4.0 * N * (8 * T + 8 * P)]        # post: reads X S L Tm A D z z' b w w' c, writes A D b c
 
 
-def run_ours(args, rank, world, local_rank):
+# --------------------------------------------------------------------- our arm
+def run_ours_rpca(args, rank, world, local_rank):
     import torch
     import paper_1909_00149_gb300 as otp
+    torch.cuda.set_device(local_rank)
+    stream = torch.cuda.Stream()
+    Y = rpca_inputs(rank)
+    T, H, W = Y.shape
+    P = T - 1
+    px = P * H * W * args.n_inner
+    dist = world > 1
 
+    def barrier():
+        if dist:
+            torch.distributed.barrier()
+
+    with torch.cuda.stream(stream):
+        rp = otp.Rpca(T, H, W, stream=stream, n_inner=args.n_inner, **RPCA_KW)
+        rp.set_input(torch.from_numpy(Y).cuda())
+        for _ in range(args.warmup):
+            res = rp.iterate_checked(1)
+        sampler = ClockSampler(local_rank)
+        barrier()
+        torch.cuda.synchronize()
+        sampler.start()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(args.steps):
+            res = rp.iterate_checked(1)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        clocks = sampler.stop()
+        ms = ev0.elapsed_time(ev1)
+
+        # per-phase device times (events on the library's stream)
+        prof = [rp.step_profiled() for _ in range(max(args.steps, 5))]
+        phase_ms = [statistics.median(p[k] for p in prof) for k in range(6)]
+
+        # end to end through the C ABI: pinned host Y in, residuals out, every step
+        hY = torch.from_numpy(Y).pin_memory()
+        for _ in range(max(1, args.warmup // 2)):
+            rp.set_input(hY)
+            rp.iterate_checked(1)
+        barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            rp.set_input(hY)
+            rp.iterate_checked(1)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        e2e_ms = e0.elapsed_time(e1)
+        rp.close()
+
+    if dist:
+        t = torch.tensor([ms, e2e_ms] + phase_ms, device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms, e2e_ms, *phase_ms = t.tolist()
+    if rank != 0:
+        return None
+    units = px * args.steps * world
+    peaks = measured_peaks()
+    pbytes = rpca_phase_bytes(T, H * W, args.n_inner)
+    dom = int(np.argmax(phase_ms))
+    kname = PHASES[dom].split(" ")[0]
+    launches = 1 if dom != 4 else args.n_inner
+    if pbytes[dom] > 0:
+        roof = {"bound": "hbm", "achieved": pbytes[dom] / (phase_ms[dom] / 1e3) / 1e9, "peak": peaks["hbm_gbs"],
+                "unit": "GB/s", "traffic": ncu_traffic(kname, "step"),
+                "algorithmic_bytes_per_launch": pbytes[dom] / launches,
+                "peak_source": peaks["source"] + " copy bandwidth (of measured)"}
+    else:
+        # the T x T eigensolver is one CTA by design: its ceiling is one SM's
+        # FP32 FMA rate (128 lanes x 2 flop x max SM clock)
+        flops = jacobi_flops(T, res["svt_sweeps"])
+        sm_peak = 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e9
+        roof = {"bound": "alu", "achieved": flops / (phase_ms[dom] / 1e3) / 1e9, "peak": sm_peak,
+                "unit": "GFLOP/s", "traffic": None, "algorithmic_flops_per_launch": flops,
+                "peak_source": "one SM's FP32 FMA rate at the measured max SM clock (the kernel is a single CTA)"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof.update({"kernel": PHASES[dom], "avg_launch_ms": phase_ms[dom] / launches})
+    phases = {PHASES[k]: {"ms": phase_ms[k], "alg_bytes": pbytes[k],
+                          "GB/s": (pbytes[k] / (phase_ms[k] / 1e3) / 1e9) if pbytes[k] else None}
+              for k in range(6)}
+    line = {
+        "metric": METRIC, "value": units / (ms / 1e3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "rpca_uotdf_T64_256x256: one Algorithm 3 outer iteration (Phi = I) on a 64-frame "
+                               "256x256 video, 63 frame pairs in the prox",
+                   "T": T, "H": H, "W": W, "n_inner": args.n_inner, **{k: v for k, v in RPCA_KW.items()},
+                   "prox_kernel": "tma",
+                   "l2": "inputs larger than L2 (state %.0f MB; %.0f MB moved per step)" %
+                         ((12 * T + 15 * P) * H * W * 4 / 1e6, sum(pbytes) / 1e6)},
+        "roofline": roof,
+        "phases": phases,
+        "last_residuals": {"res_pri": res["res_pri"], "res_dual": res["res_dual"], "svt_sweeps": res["svt_sweeps"],
+                           "svt_rank": res["svt_rank"]},
+        "e2e": {"value": units / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": T * H * W * 4,
+                "d2h_bytes_per_step": 8 * 8 + 4 + 4 * 64 + 4},
+        "gpu_launches": (7 + args.n_inner) * args.steps,
+        "clocks": clocks,
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_rpca(Y, args.n_inner, budget_s=args.cpu_seconds)
+    return line
+
+
+def run_ours_prox(args, rank, world, local_rank):
+    import torch
+    import paper_1909_00149_gb300 as otp
     torch.cuda.set_device(local_rank)
     stream = torch.cuda.Stream()
     p0, p1 = prox_inputs(rank)
@@ -147,14 +302,10 @@ def run_ours(args, rank, world, local_rank):
 
     with torch.cuda.stream(stream):
         s = otp.OtProx(B, H, W, stream=stream, **PROX_KW)
-        d0 = torch.from_numpy(p0).cuda()
-        d1 = torch.from_numpy(p1).cuda()
-        s.set_input(d0, d1)
+        s.set_input(torch.from_numpy(p0).cuda(), torch.from_numpy(p1).cuda())
         torch.cuda.synchronize()
-
-        # ---- device-resident throughput
         for _ in range(args.warmup):
-            s.check_interval(ITERS_PER_STEP)
+            s.check_interval(PROX_ITERS_PER_STEP)
         sampler = ClockSampler(local_rank)
         barrier()
         torch.cuda.synchronize()
@@ -162,77 +313,69 @@ def run_ours(args, rank, world, local_rank):
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         ev0.record(stream)
         for _ in range(args.steps):
-            s.check_interval(ITERS_PER_STEP)
+            s.check_interval(PROX_ITERS_PER_STEP)
         ev1.record(stream)
         torch.cuda.synchronize()
         barrier()
         clocks = sampler.stop()
         ms = ev0.elapsed_time(ev1)
-
-        # ---- the iteration kernel alone (events on the library's stream)
-        kernel_ms = []
-        for _ in range(max(args.steps, 3)):
-            kernel_ms.append(s.step_timed(ITERS_PER_STEP) / ITERS_PER_STEP)
-        k_ms = statistics.median(kernel_ms)
-
-        # ---- end to end through the C ABI with pinned host buffers
+        k_ms = statistics.median(s.step_timed(PROX_ITERS_PER_STEP) / PROX_ITERS_PER_STEP
+                                 for _ in range(max(args.steps, 3)))
         h0 = torch.from_numpy(p0).pin_memory()
         h1 = torch.from_numpy(p1).pin_memory()
         for _ in range(max(1, args.warmup // 2)):
             s.set_input(h0, h1)
-            s.check_interval(ITERS_PER_STEP)
+            s.check_interval(PROX_ITERS_PER_STEP)
         barrier()
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for _ in range(args.steps):
-            s.set_input(h0, h1)            # H2D of this step's inputs
-            s.check_interval(ITERS_PER_STEP)   # D2H of the step's stopping sums
+            s.set_input(h0, h1)
+            s.check_interval(PROX_ITERS_PER_STEP)
         e1.record(stream)
         torch.cuda.synchronize()
         barrier()
         e2e_ms = e0.elapsed_time(e1)
         s.close()
-
     if dist:
         t = torch.tensor([ms, e2e_ms, k_ms], device="cuda", dtype=torch.float64)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         ms, e2e_ms, k_ms = t.tolist()
     if rank != 0:
         return None
-
-    units = px * ITERS_PER_STEP * args.steps * world
-    value = units / (ms / 1e3)
-    e2e_value = units / (e2e_ms / 1e3)
+    units = px * PROX_ITERS_PER_STEP * args.steps * world
     peaks = measured_peaks()
-    alg_bytes = BYTES_PER_PIXEL_ITER["prox"] * px
+    alg_bytes = 56 * px
     achieved = alg_bytes / (k_ms / 1e3) / 1e9
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "prox_63_pairs_256x256 (64-frame 256x256 blob video, Algorithm 1)",
-                   "B": B, "H": H, "W": W, "iters_per_step": ITERS_PER_STEP, "mu": PROX_KW["mu"],
-                   "rho": PROX_KW["rho"], "kernel": PROX_KW["kernel"], "cuda_graph": True,
-                   "l2": "inputs larger than L2 (11 state planes = %.0f MB; 231 MB moved per iteration)" % (11 * px * 4 / 1e6)},
+        "metric": METRIC, "value": units / (ms / 1e3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "prox_63_pairs_256x256: Algorithm 1 check interval on the 63 pairs of a 64-frame "
+                               "256x256 blob video", "B": B, "H": H, "W": W, "iters_per_step": PROX_ITERS_PER_STEP,
+                   "mu": PROX_KW["mu"], "rho": PROX_KW["rho"], "kernel": PROX_KW["kernel"], "cuda_graph": True,
+                   "l2": "inputs larger than L2 (state %.0f MB; 231 MB moved per iteration)" % (11 * px * 4 / 1e6)},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                     "frac": achieved / peaks["hbm_gbs"], "traffic": ncu_traffic("nored"),
+                     "frac": achieved / peaks["hbm_gbs"], "traffic": ncu_traffic("prox_tma_kernel", "nored"),
                      "kernel": "prox_tma_kernel (Algorithm 1 iteration, no reduction)",
                      "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_ms": k_ms,
                      "peak_source": peaks["source"] + " copy bandwidth (of measured)"},
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 2 * px * 4, "d2h_bytes_per_step": 8 * 8},
-        "gpu_launches": (ITERS_PER_STEP + 1) * args.steps,
+        "e2e": {"value": units / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": 2 * px * 4,
+                "d2h_bytes_per_step": 8 * 8},
+        "gpu_launches": (PROX_ITERS_PER_STEP + 1) * args.steps,
         "clocks": clocks,
     }
     if not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(p0, p1, budget_s=args.cpu_seconds)
+        rate, n, el = oracle_prox_rate(p0, p1, args.cpu_seconds)
+        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"FP64 NumPy oracle, Algorithm 1, {n} iterations on 2 of the 63 pairs "
+                                          f"(2x256x256) in {el:.1f} s, single thread"}
     return line
 
 
 # --------------------------------------------------------------------- oracle timing
-def oracle_sample_rate(p0, p1, budget_s: float, n_pairs: int = 2):
-    """Pixel-iterations/s of the FP64 oracle's Algorithm 1 on the first
-    ``n_pairs`` pairs of the batch, run until ``budget_s`` seconds pass."""
+def oracle_prox_rate(p0, p1, budget_s: float, n_pairs: int = 2):
     from oracle import prox as P
     a0 = p0[:n_pairs].astype(np.float64)
     a1 = p1[:n_pairs].astype(np.float64)
@@ -249,41 +392,73 @@ def oracle_sample_rate(p0, p1, budget_s: float, n_pairs: int = 2):
     return a0.size * n / el, n, el
 
 
-def cpu_baseline(p0, p1, budget_s: float) -> dict:
-    rate, n, el = oracle_sample_rate(p0, p1, budget_s)
+def oracle_rpca_step_times(Y, n_inner: int, n_steps: int, budget_s: float | None = None):
+    """Seconds per outer iteration of the FP64 oracle's Algorithm 3 on Y, after
+    one untimed first iteration (whose SVT input is zero)."""
+    from oracle import rpca as R
+    T, H, W = Y.shape
+    prm = R.RpcaParams(lam=RPCA_KW["lam"], gamma=RPCA_KW["lam"] * np.sqrt(max(H * W, T)), kappa=RPCA_KW["kappa"],
+                       mu=RPCA_KW["mu"], rho=RPCA_KW["rho"], n_inner=n_inner)
+    Yd = Y.astype(np.float64)
+    st = R.zero_state(T, H, W)
+    st, _, _ = R.outer_iteration(st, Yd, prm)
+    times = []
+    t_start = time.perf_counter()
+    while len(times) < n_steps:
+        t0 = time.perf_counter()
+        st, _, _ = R.outer_iteration(st, Yd, prm)
+        times.append(time.perf_counter() - t0)
+        if budget_s is not None and time.perf_counter() - t_start >= budget_s:
+            break
+    return times
+
+
+def cpu_baseline_rpca(Y, n_inner: int, budget_s: float) -> dict:
+    T, H, W = Y.shape
+    times = oracle_rpca_step_times(Y, n_inner, n_steps=1000, budget_s=budget_s)
+    rate = (T - 1) * H * W * n_inner * len(times) / sum(times)
     return {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"FP64 NumPy oracle, Algorithm 1, {n} iterations on 2 of the 63 pairs "
-                      f"(2x256x256) in {el:.1f} s, single thread"}
+            "sample": f"FP64 NumPy oracle, {len(times)} full Algorithm 3 outer iteration(s) on the 64-frame "
+                      f"256x256 video ({sum(times):.1f} s, after one untimed first iteration), single thread"}
 
 
 def run_reference(args, rank, world):
+    """The oracle as the reference arm: for ``rpca`` each step is one
+    Algorithm 3 outer iteration on a 64 x 64 crop of the 64-frame video (a
+    bounded sample of the same workload)."""
     if rank != 0:
         return None
-    p0, p1 = prox_inputs(0)
-    from oracle import prox as P
-    a0 = p0[:2].astype(np.float64)
-    a1 = p1[:2].astype(np.float64)
-    prm = P.default_steps(256, 256, P.ProxParams(mu=PROX_KW["mu"], rho=PROX_KW["rho"]))
-    st = P.zero_state(a0, a1, "prox")
-    per_step = []
-    for k in range(args.warmup + args.steps):
-        t0 = time.perf_counter()
-        for _ in range(ITERS_PER_STEP):
-            st = P.alg1_iteration(st, a0, a1, prm)
-        el = time.perf_counter() - t0
-        if k >= args.warmup:
-            per_step.append(el)
-    tot = sum(per_step)
-    units = 2 * 256 * 256 * ITERS_PER_STEP * args.steps
+    if args.workload == "prox":
+        p0, p1 = prox_inputs(0)
+        from oracle import prox as P
+        a0, a1 = p0[:2].astype(np.float64), p1[:2].astype(np.float64)
+        prm = P.default_steps(256, 256, P.ProxParams(mu=PROX_KW["mu"], rho=PROX_KW["rho"]))
+        st = P.zero_state(a0, a1, "prox")
+        per = []
+        for k in range(args.warmup + args.steps):
+            t0 = time.perf_counter()
+            for _ in range(PROX_ITERS_PER_STEP):
+                st = P.alg1_iteration(st, a0, a1, prm)
+            if k >= args.warmup:
+                per.append(time.perf_counter() - t0)
+        units = a0.size * PROX_ITERS_PER_STEP * args.steps
+        sample = f"{PROX_ITERS_PER_STEP} Algorithm 1 iterations on 2 of the 63 256x256 pairs per step"
+        workload = "prox_63_pairs_256x256"
+    else:
+        Y = rpca_inputs(0)[:, 96:160, 96:160].copy()
+        T, H, W = Y.shape
+        per = oracle_rpca_step_times(Y, args.n_inner, n_steps=args.warmup + args.steps)[args.warmup:]
+        units = (T - 1) * H * W * args.n_inner * args.steps
+        sample = "one Algorithm 3 outer iteration per step on the central 64x64 crop of the 64-frame video"
+        workload = "rpca_uotdf_T64_256x256 (oracle on a 64x64 crop)"
+    tot = sum(per)
     value = units / tot
     return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": {"workload": "prox_63_pairs_256x256 (64-frame 256x256 blob video, Algorithm 1)",
-                       "iters_per_step": ITERS_PER_STEP, "sample": "2 of 63 pairs"},
+            "config": {"workload": workload, "sample": sample, "n_inner": args.n_inner},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"FP64 NumPy oracle, {ITERS_PER_STEP} Algorithm 1 iterations on 2 of the 63 "
-                                       "256x256 pairs per step, single thread"},
+                             "sample": "FP64 NumPy oracle, single thread: " + sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
@@ -293,12 +468,12 @@ def main():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["prox"], default="prox")
-    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--workload", choices=["rpca", "prox"], default="rpca")
+    ap.add_argument("--n-inner", type=int, default=1)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
-    if args.warmup < 3:
-        args.warmup = 3
+    args.warmup = max(args.warmup, 3)
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
@@ -309,7 +484,8 @@ def main():
             import torch
             torch.cuda.set_device(local_rank)
             torch.distributed.init_process_group("nccl")
-        line = run_ours(args, rank, world, local_rank)
+        run = run_ours_rpca if args.workload == "rpca" else run_ours_prox
+        line = run(args, rank, world, local_rank)
         if world > 1:
             import torch
             torch.distributed.destroy_process_group()

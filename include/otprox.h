@@ -199,6 +199,7 @@ typedef struct {
   int32_t check_every;    /* outer iterations between residual checks (>= 1)     */
   int32_t svt_max_sweeps; /* Jacobi sweeps cap of the T x T eigensolver           */
   int32_t prox_kernel;    /* OT_KERNEL_* of the inner Algorithm 1                 */
+  int32_t use_graph;      /* 1: replay warm outer iterations as a CUDA graph     */
 } ot_rpca_params;
 
 typedef struct {
@@ -229,7 +230,7 @@ typedef struct {
 
 /* Defaults: lambda 0.02, gamma lambda sqrt(max(N,T)), kappa 0.005, mu 3,
  * rho 1, n_inner 1, tol 1e-5, max_iter 5000, check_every 1,
- * svt_max_sweeps 30, prox_kernel AUTO; T = 2, H = W = 1. */
+ * svt_max_sweeps 30, prox_kernel AUTO, use_graph 1; T = 2, H = W = 1. */
 void ot_rpca_default_params(ot_rpca_params* p);
 /* Validate, allocate and zero the state (Algorithm 3 line 2). */
 int ot_rpca_create(const ot_rpca_params* params, void* cuda_stream, ot_rpca_t* out);
@@ -242,6 +243,12 @@ int ot_rpca_iterate_checked(ot_rpca_t h, int32_t n_outer, ot_rpca_result* res);
 /* Iterate until both residuals <= tol or max_iter.  Returns OT_OK,
  * OT_ENOTCONV (state still valid) or OT_ENONFINITE.  Sync. */
 int ot_rpca_solve(ot_rpca_t h, ot_rpca_result* res);
+/* One outer iteration (as ot_rpca_step(h, 1)) with CUDA events recorded on
+ * the handle's stream between its phases; phase_ms[0..5] receives the device
+ * time of: 0 lines 4-9 (fused pass), 1 Gram matrix, 2 T x T eigensolver,
+ * 3 SVT apply, 4 the n_inner Algorithm 1 iterations, 5 lines 12-15.  Sync. */
+int ot_rpca_step_profiled(ot_rpca_t h, double* phase_ms);
+
 /* Copy one variable (OT_RPCA_*) out, dense.  Sync. */
 int ot_rpca_get(ot_rpca_t h, int32_t var, float* out);
 /* Zero the state (keeps Y). */

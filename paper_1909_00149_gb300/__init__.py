@@ -185,6 +185,8 @@ def rpca_default_params(**kw) -> "_abi.ot_rpca_params":
         k = "lambda_" if k in ("lam", "lambda") else k
         if k == "prox_kernel":
             v = KERNELS[v] if isinstance(v, str) else v
+        elif k == "use_graph":
+            v = int(bool(v))
         if not hasattr(p, k):
             raise TypeError(f"unknown parameter {k!r}")
         setattr(p, k, v)
@@ -233,6 +235,12 @@ class Rpca:
         r = _abi.ot_rpca_result()
         check(_lib.ot_rpca_solve(self.h, ctypes.byref(r)), "ot_rpca_solve", ok=(OT_OK, OT_ENOTCONV))
         return r.as_dict()
+
+    def step_profiled(self) -> list:
+        """One outer iteration; device ms of its six phases (see the C header)."""
+        ms = (ctypes.c_double * 6)()
+        check(_lib.ot_rpca_step_profiled(self.h, ms), "ot_rpca_step_profiled")
+        return list(ms)
 
     def reset(self):
         check(_lib.ot_rpca_reset(self.h), "ot_rpca_reset")

@@ -50,7 +50,7 @@ class ot_rpca_params(ctypes.Structure):
                 ("lambda_", ctypes.c_double), ("gamma", ctypes.c_double), ("kappa", ctypes.c_double),
                 ("mu", ctypes.c_double), ("rho", ctypes.c_double), ("n_inner", ctypes.c_int32),
                 ("tol", ctypes.c_double), ("max_iter", ctypes.c_int32), ("check_every", ctypes.c_int32),
-                ("svt_max_sweeps", ctypes.c_int32), ("prox_kernel", ctypes.c_int32)]
+                ("svt_max_sweeps", ctypes.c_int32), ("prox_kernel", ctypes.c_int32), ("use_graph", ctypes.c_int32)]
 
 
 class ot_rpca_result(ctypes.Structure):
@@ -90,6 +90,7 @@ PROTOTYPES = [
     ("ot_rpca_iterate_checked", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ot_rpca_result)]),
     ("ot_rpca_solve", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ot_rpca_result)]),
     ("ot_rpca_get", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]),
+    ("ot_rpca_step_profiled", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
     ("ot_rpca_reset", ctypes.c_int, [ctypes.c_void_p]),
     ("ot_rpca_get_params", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ot_rpca_params)]),
     ("ot_rpca_destroy", ctypes.c_int, [ctypes.c_void_p]),

@@ -132,6 +132,7 @@ cudaError_t rpca_launch_sumsq(const RpcaGeom& g, const float* Y, double* partial
 
 // ----------------------------------------------------------------- SVT
 int svt_padded_T(int T);                       // 16, 32, 64 or 128
+float svt_tolerance(int T);                    // Jacobi stopping tolerance
 int svt_gram_blocks(long long N);
 int svt_apply_blocks(long long N, int T, int* gy);
 cudaError_t svt_prepare();

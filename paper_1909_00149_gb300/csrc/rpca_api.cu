@@ -50,6 +50,13 @@ struct ot_rpca {
   double* hsums;             // pinned: [kNumSums] sums, then sweeps (as int) and sigma
   double y_norm;
   int have_input;
+  // line 10 (SVT) and line 11 (prox) are independent given lines 4-9: the
+  // SVT runs on a side stream while the prox runs on the handle's stream
+  cudaStream_t side;
+  cudaEvent_t ev_fork, ev_join;
+  // one warm outer iteration (with its residual sums) as a graph, by the
+  // ping-pong parity of the inner prox state
+  cudaGraphExec_t graph[2];
 };
 
 extern "C" {
@@ -70,10 +77,16 @@ void ot_rpca_default_params(ot_rpca_params* p) {
   p->check_every = 1;
   p->svt_max_sweeps = 30;
   p->prox_kernel = OT_KERNEL_AUTO;
+  p->use_graph = 1;
 }
 
 int ot_rpca_destroy(ot_rpca_t h) {
   if (!h) return OT_OK;
+  for (int k = 0; k < 2; ++k)
+    if (h->graph[k]) cudaGraphExecDestroy(h->graph[k]);
+  if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+  if (h->ev_join) cudaEventDestroy(h->ev_join);
+  if (h->side) cudaStreamDestroy(h->side);
   if (h->prox) ot_prox_destroy(h->prox);
   if (h->slab) cudaFree(h->slab);
   if (h->gram_partials) cudaFree(h->gram_partials);
@@ -176,6 +189,9 @@ int ot_rpca_create(const ot_rpca_params* params, void* cuda_stream, ot_rpca_t* o
     e = cudaMallocHost(&h->hsums, (kNumSums + 2 + 128) * sizeof(double));
   }
   if (e == cudaSuccess) e = svt_prepare();
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->slab, 0, (8 * nframe + 4 * npair) * sizeof(float), h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) {
@@ -227,16 +243,23 @@ static int enqueue_outer(ot_rpca* h, bool sums) {
   const long long plane = h->G.plane;
   const long long N = plane;   // rows of the N x T matrix: one frame plane (padding columns are zero)
   OT_CUDA(rpca_launch_pre(h->G, h->C, h->P, h->partials, h->stream), "rpca pre");
-  OT_CUDA(svt_launch_gram(h->P.LD, plane, N, h->prm.T, h->gram_partials, h->Gm, h->stream), "svt gram");
-  OT_CUDA(svt_launch_eig(h->Gm, h->prm.T, h->warm, (float)(h->prm.gamma / h->prm.rho), h->prm.svt_max_sweeps, 1e-6f,
-                         h->V, h->Wm, h->sig, h->sweeps, h->stream),
+  // fork: line 10 on the side stream
+  OT_CUDA(cudaEventRecord(h->ev_fork, h->stream), "fork");
+  OT_CUDA(cudaStreamWaitEvent(h->side, h->ev_fork, 0), "fork wait");
+  OT_CUDA(svt_launch_gram(h->P.LD, plane, N, h->prm.T, h->gram_partials, h->Gm, h->side), "svt gram");
+  OT_CUDA(svt_launch_eig(h->Gm, h->prm.T, h->warm, (float)(h->prm.gamma / h->prm.rho), h->prm.svt_max_sweeps, svt_tolerance(h->prm.T),
+                         h->V, h->Wm, h->sig, h->sweeps, h->side),
           "svt eig");
   h->warm = 1;
   OT_CUDA(svt_launch_apply(h->P.LD, plane, N, h->prm.T, h->Wm, h->P.Tm, plane, true,
-                           h->partials + (size_t)h->nb_rpca * kNumSums, h->stream),
+                           h->partials + (size_t)h->nb_rpca * kNumSums, h->side),
           "svt apply");
+  OT_CUDA(cudaEventRecord(h->ev_join, h->side), "join");
+  // line 11 on the handle's stream, concurrently
   int rc = ot_prox_step(h->prox, h->prm.n_inner);
   if (rc != OT_OK) return rc;
+  // join before lines 12-15
+  OT_CUDA(cudaStreamWaitEvent(h->stream, h->ev_join, 0), "join wait");
   OT_CUDA(rpca_launch_post(h->G, h->P, h->partials + (size_t)(h->nb_rpca + h->nb_apply) * kNumSums, h->stream),
           "rpca post");
   if (sums) {
@@ -252,6 +275,35 @@ static int enqueue_outer(ot_rpca* h, bool sums) {
     OT_CUDA(cudaMemcpyAsync(h->prox->herr, h->prox->derr, sizeof(int), cudaMemcpyDeviceToHost, h->stream),
             "rpca error flag copy");
   }
+  return OT_OK;
+}
+
+// One outer iteration: replayed from a CUDA graph once the eigensolver is
+// warm (the graph bakes in the warm flag and the prox buffers of one
+// ping-pong parity), eager otherwise.  Graph replays always finalise the
+// residual sums (a few microseconds).
+static int run_outer(ot_rpca* h, bool sums) {
+  const bool can_graph = h->prm.use_graph && h->stream != nullptr && h->warm;
+  if (!can_graph) return enqueue_outer(h, sums);
+  ot_prox* px = h->prox;
+  const int par = px->cur;
+  if (!h->graph[par]) {
+    cudaGraph_t g = nullptr;
+    OT_CUDA(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal), "rpca graph capture");
+    const int rc = enqueue_outer(h, true);
+    const cudaError_t e2 = cudaStreamEndCapture(h->stream, &g);
+    px->cur = par;   // capture enqueued nothing: undo the parity bookkeeping
+    if (rc != OT_OK) {
+      if (g) cudaGraphDestroy(g);
+      return rc;
+    }
+    if (e2 != cudaSuccess) return cuda_fail(e2, "rpca graph capture end");
+    const cudaError_t e3 = cudaGraphInstantiate(&h->graph[par], g, 0);
+    cudaGraphDestroy(g);
+    if (e3 != cudaSuccess) return cuda_fail(e3, "rpca graph instantiate");
+  }
+  OT_CUDA(cudaGraphLaunch(h->graph[par], h->stream), "rpca graph launch");
+  px->cur = px->resident ? par : (par ^ (h->prm.n_inner & 1));
   return OT_OK;
 }
 
@@ -280,7 +332,7 @@ int ot_rpca_step(ot_rpca_t h, int32_t n_outer) {
   if (!h->have_input) return fail(OT_EINVAL, "ot_rpca_step: no input (call ot_rpca_set_input)");
   if (n_outer < 0) return fail(OT_EINVAL, "ot_rpca_step: n_outer must be >= 0");
   for (int k = 0; k < n_outer; ++k) {
-    const int rc = enqueue_outer(h, false);
+    const int rc = run_outer(h, false);
     if (rc != OT_OK) return rc;
   }
   return OT_OK;
@@ -291,7 +343,7 @@ int ot_rpca_iterate_checked(ot_rpca_t h, int32_t n_outer, ot_rpca_result* res) {
   if (!h->have_input) return fail(OT_EINVAL, "ot_rpca_iterate_checked: no input (call ot_rpca_set_input)");
   if (n_outer < 1) return fail(OT_EINVAL, "ot_rpca_iterate_checked: n_outer must be >= 1");
   for (int k = 0; k < n_outer; ++k) {
-    const int rc = enqueue_outer(h, k == n_outer - 1);
+    const int rc = run_outer(h, k == n_outer - 1);
     if (rc != OT_OK) return rc;
   }
   OT_CUDA(cudaStreamSynchronize(h->stream), "ot_rpca_iterate_checked: sync");
@@ -339,6 +391,50 @@ int ot_rpca_solve(ot_rpca_t h, ot_rpca_result* res) {
          r.res_pri, r.res_dual);
   if (status == OT_ENONFINITE) fail(OT_ENONFINITE, "ot_rpca_solve: non-finite values");
   return status;
+}
+
+int ot_rpca_step_profiled(ot_rpca_t h, double* phase_ms) {
+  if (!h || !phase_ms) return fail(OT_EINVAL, "ot_rpca_step_profiled: NULL argument");
+  if (!h->have_input) return fail(OT_EINVAL, "ot_rpca_step_profiled: no input (call ot_rpca_set_input)");
+  cudaEvent_t ev[7] = {};
+  cudaError_t e = cudaSuccess;
+  for (int k = 0; k < 7 && e == cudaSuccess; ++k) e = cudaEventCreate(&ev[k]);
+  const long long plane = h->G.plane;
+  int rc = OT_OK;
+  if (e == cudaSuccess) e = cudaEventRecord(ev[0], h->stream);
+  if (e == cudaSuccess) e = rpca_launch_pre(h->G, h->C, h->P, h->partials, h->stream);
+  if (e == cudaSuccess) e = cudaEventRecord(ev[1], h->stream);
+  if (e == cudaSuccess) e = svt_launch_gram(h->P.LD, plane, plane, h->prm.T, h->gram_partials, h->Gm, h->stream);
+  if (e == cudaSuccess) e = cudaEventRecord(ev[2], h->stream);
+  if (e == cudaSuccess)
+    e = svt_launch_eig(h->Gm, h->prm.T, h->warm, (float)(h->prm.gamma / h->prm.rho), h->prm.svt_max_sweeps, svt_tolerance(h->prm.T),
+                       h->V, h->Wm, h->sig, h->sweeps, h->stream);
+  if (e == cudaSuccess) {
+    h->warm = 1;
+    e = cudaEventRecord(ev[3], h->stream);
+  }
+  if (e == cudaSuccess)
+    e = svt_launch_apply(h->P.LD, plane, plane, h->prm.T, h->Wm, h->P.Tm, plane, true,
+                         h->partials + (size_t)h->nb_rpca * kNumSums, h->stream);
+  if (e == cudaSuccess) e = cudaEventRecord(ev[4], h->stream);
+  if (e == cudaSuccess) {
+    rc = ot_prox_step(h->prox, h->prm.n_inner);
+    if (rc == OT_OK) e = cudaEventRecord(ev[5], h->stream);
+  }
+  if (e == cudaSuccess && rc == OT_OK)
+    e = rpca_launch_post(h->G, h->P, h->partials + (size_t)(h->nb_rpca + h->nb_apply) * kNumSums, h->stream);
+  if (e == cudaSuccess && rc == OT_OK) e = cudaEventRecord(ev[6], h->stream);
+  if (e == cudaSuccess && rc == OT_OK) e = cudaEventSynchronize(ev[6]);
+  for (int k = 0; k < 6 && e == cudaSuccess && rc == OT_OK; ++k) {
+    float ms = 0.f;
+    e = cudaEventElapsedTime(&ms, ev[k], ev[k + 1]);
+    phase_ms[k] = ms;
+  }
+  for (int k = 0; k < 7; ++k)
+    if (ev[k]) cudaEventDestroy(ev[k]);
+  if (rc != OT_OK) return rc;
+  if (e != cudaSuccess) return cuda_fail(e, "ot_rpca_step_profiled");
+  return OT_OK;
 }
 
 int ot_rpca_get(ot_rpca_t h, int32_t var, float* out) {
@@ -391,7 +487,7 @@ int ot_svt(const float* X, float* Y, int64_t N, int32_t T, double theta, void* c
   float* sig = Wm + (size_t)TP * TP;
   int* sweeps = reinterpret_cast<int*>(sig + (size_t)TP * TP);
   cudaError_t e = svt_launch_gram(X, N, N, T, part, Gm, st);
-  if (e == cudaSuccess) e = svt_launch_eig(Gm, T, 0, (float)theta, 60, 1e-6f, V, Wm, sig, sweeps, st);
+  if (e == cudaSuccess) e = svt_launch_eig(Gm, T, 0, (float)theta, 60, svt_tolerance(T), V, Wm, sig, sweeps, st);
   if (e == cudaSuccess) e = svt_launch_apply(X, N, N, T, Wm, Y, N, false, nullptr, st);
   cudaError_t e2 = cudaFreeAsync(ws, st);
   if (e != cudaSuccess) return cuda_fail(e, "ot_svt");

@@ -23,55 +23,128 @@ namespace otp {
 namespace {
 
 constexpr int kGramChunk = 128;      // pixels staged per step
+constexpr int kGramThreads = 256;
 
-// Per-CTA partial Gram over a strided set of pixel chunks.  Thread (ty, tx)
-// of a (Tp/4) x (Tp/4) block owns the 4 x 4 output tile rows 4ty.., cols 4tx..
+// Per-CTA partial Gram over a strided set of pixel chunks.  The chunk is
+// staged pixel-major (sx[pixel][t]).  Every thread owns an 8 x 8 tile of the
+// TP x TP output; the (TP/8)^2 threads covering the output form a group, and
+// the 256 / (TP/8)^2 groups split the chunk's pixels.  Two float4 reads per
+// operand per pixel feed 64 FMAs.  The groups are summed in shared memory at
+// the end and the CTA's total is written in FP64.
 template <int TP>
-__global__ void __launch_bounds__((TP / 4) * (TP / 4))
+constexpr int gram_groups() { return kGramThreads / ((TP / 8) * (TP / 8)); }
+
+template <int TP>
+constexpr size_t gram_smem() {
+  const size_t stage = (size_t)kGramChunk * (TP + 4) * sizeof(float);
+  const size_t red = (size_t)gram_groups<TP>() * TP * TP * sizeof(float);
+  return stage > red ? stage : red;
+}
+
+template <int TP>
+__global__ void __launch_bounds__(kGramThreads)
 gram_partial_kernel(const float* __restrict__ X, long long ld, long long N, int T, double* __restrict__ partials) {
-  constexpr int NT = (TP / 4) * (TP / 4);
-  __shared__ __align__(16) float sx[TP][kGramChunk];
+  constexpr int R = 8;
+  constexpr int TPG = (TP / 8) * (TP / 8);        // threads per group
+  constexpr int NG = gram_groups<TP>();
+  constexpr int PPG = kGramChunk / NG;            // pixels per group and chunk
+  constexpr int LDS = TP + 4;                     // padded pixel row
+  extern __shared__ __align__(16) float sx[];
   const int tid = threadIdx.x;
-  const int ty = tid / (TP / 4), tx = tid % (TP / 4);
-  float acc[4][4] = {};
+  const int grp = tid / TPG, gt = tid % TPG;
+  const int ty = gt / (TP / 8), tx = gt % (TP / 8);
+  float acc[R][R];
+#pragma unroll
+  for (int r = 0; r < R; ++r)
+#pragma unroll
+    for (int c = 0; c < R; ++c) acc[r][c] = 0.f;
   const long long nchunks = (N + kGramChunk - 1) / kGramChunk;
   for (long long ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
     const long long i0 = ch * kGramChunk;
-    for (int e = tid; e < TP * kGramChunk; e += NT) {
-      const int t = e / kGramChunk, i = e % kGramChunk;
-      const long long gi = i0 + i;
-      sx[t][i] = (t < T && gi < N) ? __ldg(X + (long long)t * ld + gi) : 0.f;
+    for (int e = tid; e < TP * kGramChunk; e += kGramThreads) {
+      const int t = e / kGramChunk, p = e % kGramChunk;
+      const long long gi = i0 + p;
+      sx[p * LDS + t] = (t < T && gi < N) ? __ldg(X + (long long)t * ld + gi) : 0.f;
     }
     __syncthreads();
-#pragma unroll 4
-    for (int i = 0; i < kGramChunk; i += 4) {
-      float4 a[4], b[4];
+    const float* base = sx + grp * PPG * LDS;
+#pragma unroll 2
+    for (int p = 0; p < PPG; ++p) {
+      float a[R], b[R];
 #pragma unroll
-      for (int r = 0; r < 4; ++r) a[r] = *reinterpret_cast<const float4*>(&sx[4 * ty + r][i]);
+      for (int r = 0; r < R; r += 4) {
+        const float4 va = *reinterpret_cast<const float4*>(base + p * LDS + R * ty + r);
+        const float4 vb = *reinterpret_cast<const float4*>(base + p * LDS + R * tx + r);
+        a[r] = va.x; a[r + 1] = va.y; a[r + 2] = va.z; a[r + 3] = va.w;
+        b[r] = vb.x; b[r + 1] = vb.y; b[r + 2] = vb.z; b[r + 3] = vb.w;
+      }
 #pragma unroll
-      for (int c = 0; c < 4; ++c) b[c] = *reinterpret_cast<const float4*>(&sx[4 * tx + c][i]);
+      for (int r = 0; r < R; ++r)
 #pragma unroll
-      for (int r = 0; r < 4; ++r)
-#pragma unroll
-        for (int c = 0; c < 4; ++c)
-          acc[r][c] = fmaf(a[r].x, b[c].x, fmaf(a[r].y, b[c].y, fmaf(a[r].z, b[c].z, fmaf(a[r].w, b[c].w, acc[r][c]))));
+        for (int c = 0; c < R; ++c) acc[r][c] = fmaf(a[r], b[c], acc[r][c]);
     }
     __syncthreads();
   }
+  // sum the groups through shared memory (reusing the staging buffer)
+  float* red = sx;   // [NG][TP][TP]
+#pragma unroll
+  for (int r = 0; r < R; ++r)
+#pragma unroll
+    for (int c = 0; c < R; ++c) red[((size_t)grp * TP + R * ty + r) * TP + R * tx + c] = acc[r][c];
+  __syncthreads();
   double* out = partials + (size_t)blockIdx.x * TP * TP;
-#pragma unroll
-  for (int r = 0; r < 4; ++r)
-#pragma unroll
-    for (int c = 0; c < 4; ++c) out[(4 * ty + r) * TP + 4 * tx + c] = (double)acc[r][c];
+  for (int e = tid; e < TP * TP; e += kGramThreads) {
+    double v = 0.0;
+    for (int g = 0; g < NG; ++g) v += (double)red[(size_t)g * TP * TP + e];
+    out[e] = v;
+  }
 }
 
-// G[e] = sum over CTAs of partials[b][e], fixed order, FP64.
-__global__ void gram_reduce_kernel(const double* __restrict__ partials, int nparts, int n, double* __restrict__ G) {
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= n) return;
-  double s = 0.0;
-  for (int b = 0; b < nparts; ++b) s += partials[(size_t)b * n + e];
-  G[e] = s;
+// G[e] = sum over CTAs of partials[b][e] in FP64, fixed order: a block owns
+// 32 consecutive entries (one per lane); its 8 warps take every 8th partial
+// and are summed in warp order.
+__global__ void __launch_bounds__(256) gram_reduce_kernel(const double* __restrict__ partials, int nparts, int n,
+                                                          double* __restrict__ G) {
+  __shared__ double s[8][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int e = blockIdx.x * 32 + lane;
+  double v = 0.0;
+  if (e < n)
+    for (int b = warp; b < nparts; b += 8) v += partials[(size_t)b * n + e];
+  s[warp][lane] = v;
+  __syncthreads();
+  if (warp == 0 && e < n) {
+    double t = 0.0;
+    for (int w = 0; w < 8; ++w) t += s[w][lane];
+    G[e] = t;
+  }
+}
+
+// C = op(A) * diag(d) * B for TP x TP shared matrices (leading dimension
+// LDA).  Threads take 4 x 4 output blocks in turn.  transA: use A^T.
+template <int TP, int LDA>
+__device__ __forceinline__ void small_gemm(const float* A, const float* B, float* C, bool transA, const float* diag) {
+  constexpr int NB = TP / 4;            // 4 x 4 blocks per side
+  for (int blk = threadIdx.x; blk < NB * NB; blk += blockDim.x) {
+    const int by = blk / NB, bx = blk % NB;
+    float acc[4][4] = {};
+    for (int k = 0; k < TP; ++k) {
+      float a[4], b[4];
+      const float dk = diag ? diag[k] : 1.f;
+#pragma unroll
+      for (int r = 0; r < 4; ++r) a[r] = transA ? A[k * LDA + 4 * by + r] : A[(4 * by + r) * LDA + k];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) b[c] = dk * B[k * LDA + 4 * bx + c];
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[r][c] = fmaf(a[r], b[c], acc[r][c]);
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) C[(4 * by + r) * LDA + 4 * bx + c] = acc[r][c];
+  }
 }
 
 // One-CTA cyclic Jacobi on the symmetric G (TP x TP, zero beyond T), then
@@ -79,44 +152,69 @@ __global__ void gram_reduce_kernel(const double* __restrict__ partials, int npar
 // sigma_i = sqrt(max(lambda_i, 0)).  V_io: warm-start eigenvectors in (when
 // warm) and the new ones out.  sig_out: sigma_i (diagnostics), sweeps_out:
 // sweeps used.
+// Round-robin ordering: each round rotates the TP/2 disjoint pairs of a
+// precomputed schedule.  Phase 1: warp k forms the rotation J_k of pair k
+// from its 2 x 2 diagonal block.  Phase 2: each thread owns 2 x 2 blocks
+// (pair kb rows x pair kc columns) and applies both rotations at once,
+// B <- J_kb^T B J_kc, and rotates two rows of V.  The rotation need only be
+// orthogonal (c^2 + s^2 = 1 to rounding), not correctly rounded, so the
+// approximate reciprocal and reciprocal square root are used.
+constexpr int kJacobiThreads = 1024;
+
+__device__ __forceinline__ void jacobi_rotation(float app, float aqq, float apq, float& c, float& s, float& t) {
+  c = 1.f;
+  s = 0.f;
+  t = 0.f;
+  if (apq != 0.f) {
+    float tau = (aqq - app) * __fdividef(0.5f, apq);
+    tau = fminf(fmaxf(tau, -1e18f), 1e18f);
+    const float h2 = fmaf(tau, tau, 1.f);
+    const float h = h2 * rsqrtf(h2);                      // sqrt(1 + tau^2)
+    t = copysignf(__fdividef(1.f, fabsf(tau) + h), tau);
+    c = rsqrtf(fmaf(t, t, 1.f));
+    s = t * c;
+  }
+}
+
 template <int TP>
-__global__ void __launch_bounds__(1024)
+__global__ void __launch_bounds__(kJacobiThreads)
 jacobi_svt_kernel(const double* __restrict__ G, int warm, float theta, int max_sweeps, float tol,
                   float* __restrict__ V_io, float* __restrict__ Wm, float* __restrict__ sig_out,
                   int* __restrict__ sweeps_out) {
   constexpr int LDA = TP + 1;
+  constexpr int NP = TP / 2;
+  constexpr int NW = kJacobiThreads / 32;
   extern __shared__ float sm[];
   float* A = sm;                 // [TP][LDA]
   float* V = A + TP * LDA;       // [TP][LDA]
   float* Tmp = V + TP * LDA;     // [TP][LDA]
-  float* cs = Tmp + TP * LDA;    // [TP/2] c, [TP/2] s
-  int* pq = reinterpret_cast<int*>(cs + TP);   // [TP/2] p, [TP/2] q
-  __shared__ float red[32];
-  __shared__ float s_off, s_diag;
-  const int tid = threadIdx.x, nt = blockDim.x;
+  float* f = Tmp + TP * LDA;     // [TP]
+  __shared__ float s_c[NP], s_s[NP], s_t[NP];
+  __shared__ unsigned char s_sched[(TP - 1) * NP * 2];   // (p, q) of pair k in round r
+  __shared__ float red[2][NW];
+  __shared__ int s_go;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
-  for (int e = tid; e < TP * TP; e += nt) {
+  for (int e = tid; e < (TP - 1) * NP; e += kJacobiThreads) {
+    const int r = e / NP, k = e % NP;
+    int p = (r + k) % (TP - 1);
+    int q = k == 0 ? TP - 1 : (r - k + TP - 1) % (TP - 1);
+    if (p > q) { const int t = p; p = q; q = t; }
+    s_sched[2 * e] = (unsigned char)p;
+    s_sched[2 * e + 1] = (unsigned char)q;
+  }
+  for (int e = tid; e < TP * TP; e += kJacobiThreads) {
     const int i = e / TP, j = e % TP;
     A[i * LDA + j] = (float)G[e];
     V[i * LDA + j] = warm ? V_io[e] : (i == j ? 1.f : 0.f);
   }
   __syncthreads();
   if (warm) {   // A <- V^T G V
-    for (int e = tid; e < TP * TP; e += nt) {
-      const int i = e / TP, j = e % TP;
-      float s = 0.f;
-      for (int k = 0; k < TP; ++k) s = fmaf(A[i * LDA + k], V[k * LDA + j], s);
-      Tmp[i * LDA + j] = s;
-    }
+    small_gemm<TP, LDA>(A, V, Tmp, false, nullptr);   // Tmp = G V
     __syncthreads();
-    for (int e = tid; e < TP * TP; e += nt) {
-      const int i = e / TP, j = e % TP;
-      float s = 0.f;
-      for (int k = 0; k < TP; ++k) s = fmaf(V[k * LDA + i], Tmp[k * LDA + j], s);
-      A[i * LDA + j] = s;
-    }
+    small_gemm<TP, LDA>(V, Tmp, A, true, nullptr);    // A = V^T Tmp
     __syncthreads();
-    for (int e = tid; e < TP * TP; e += nt) {   // symmetrise the rounding
+    for (int e = tid; e < TP * TP; e += kJacobiThreads) {   // symmetrise the rounding
       const int i = e / TP, j = e % TP;
       if (i < j) {
         const float m = 0.5f * (A[i * LDA + j] + A[j * LDA + i]);
@@ -131,163 +229,225 @@ jacobi_svt_kernel(const double* __restrict__ G, int warm, float theta, int max_s
   for (; sweep < max_sweeps; ++sweep) {
     // convergence: off-diagonal mass vs diagonal mass
     float off = 0.f, dg = 0.f;
-    for (int e = tid; e < TP * TP; e += nt) {
+    for (int e = tid; e < TP * TP; e += kJacobiThreads) {
       const int i = e / TP, j = e % TP;
       const float v = A[i * LDA + j];
-      if (i == j) dg += v * v; else off += v * v;
+      if (i == j) dg = fmaf(v, v, dg); else off = fmaf(v, v, off);
     }
+#pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       off += __shfl_down_sync(0xffffffffu, off, o);
       dg += __shfl_down_sync(0xffffffffu, dg, o);
     }
-    if ((tid & 31) == 0) red[tid >> 5] = off;
-    __syncthreads();
-    if (tid == 0) {
-      float s = 0.f;
-      for (int w = 0; w < nt / 32; ++w) s += red[w];
-      s_off = s;
+    if (lane == 0) {
+      red[0][warp] = off;
+      red[1][warp] = dg;
     }
     __syncthreads();
-    if ((tid & 31) == 0) red[tid >> 5] = dg;
-    __syncthreads();
     if (tid == 0) {
-      float s = 0.f;
-      for (int w = 0; w < nt / 32; ++w) s += red[w];
-      s_diag = s;
+      float so = 0.f, sd = 0.f;
+      for (int w = 0; w < NW; ++w) {
+        so += red[0][w];
+        sd += red[1][w];
+      }
+      s_go = so > tol * tol * sd;
     }
     __syncthreads();
-    if (!(s_off > tol * tol * s_diag)) break;
+    if (!s_go) break;
 
     for (int r = 0; r < TP - 1; ++r) {
-      // round-robin pairing of 0..TP-1 (TP-1 fixed)
-      if (tid < TP / 2) {
-        const int k = tid;
-        int p = (r + k) % (TP - 1);
-        int q = k == 0 ? TP - 1 : (r - k + TP - 1) % (TP - 1);
-        if (p > q) { const int t = p; p = q; q = t; }
-        const float app = A[p * LDA + p], aqq = A[q * LDA + q], apq = A[p * LDA + q];
-        float c = 1.f, s = 0.f;
-        if (apq != 0.f && fabsf(apq) > 1e-30f * sqrtf(fabsf(app * aqq))) {
-          const float tau = (aqq - app) / (2.f * apq);
-          const float t = copysignf(1.f, tau) / (fabsf(tau) + sqrtf(1.f + tau * tau));
-          c = 1.f / sqrtf(1.f + t * t);
-          s = t * c;
+      const unsigned char* sch = s_sched + 2 * r * NP;
+      // phase 1: rotations
+      for (int k = warp; k < NP; k += NW) {
+        const int p = sch[2 * k], q = sch[2 * k + 1];
+        float c, sn, tn;
+        jacobi_rotation(A[p * LDA + p], A[q * LDA + q], A[p * LDA + q], c, sn, tn);
+        if (lane == 0) {
+          s_c[k] = c;
+          s_s[k] = sn;
+          s_t[k] = tn;
         }
-        cs[k] = c;
-        cs[TP / 2 + k] = s;
-        pq[k] = p;
-        pq[TP / 2 + k] = q;
       }
       __syncthreads();
-      // rows p, q of A  (A <- J^T A)
-      for (int e = tid; e < (TP / 2) * TP; e += nt) {
-        const int k = e / TP, j = e % TP;
-        const int p = pq[k], q = pq[TP / 2 + k];
-        const float c = cs[k], s = cs[TP / 2 + k];
-        const float ap = A[p * LDA + j], aq = A[q * LDA + j];
-        A[p * LDA + j] = c * ap - s * aq;
-        A[q * LDA + j] = s * ap + c * aq;
+      // phase 2: 2 x 2 blocks of A, and rows of V
+      for (int e = tid; e < NP * NP; e += kJacobiThreads) {
+        const int kb = e / NP, kc = e % NP;
+        const int p = sch[2 * kb], q = sch[2 * kb + 1], pc = sch[2 * kc], qc = sch[2 * kc + 1];
+        const float c = s_c[kb], sn = s_s[kb], c2 = s_c[kc], s2 = s_s[kc];
+        const float a00 = A[p * LDA + pc], a01 = A[p * LDA + qc], a10 = A[q * LDA + pc], a11 = A[q * LDA + qc];
+        if (kb == kc) {
+          // the pair's own block: the rotation zeroes a_pq exactly and moves
+          // -/+ t a_pq onto the diagonal (the accurate classical update)
+          const float tn = s_t[kb];
+          A[p * LDA + p] = a00 - tn * a01;
+          A[q * LDA + q] = a11 + tn * a01;
+          A[p * LDA + q] = 0.f;
+          A[q * LDA + p] = 0.f;
+          continue;
+        }
+        // rows: J^T B
+        const float r00 = c * a00 - sn * a10, r01 = c * a01 - sn * a11;
+        const float r10 = sn * a00 + c * a10, r11 = sn * a01 + c * a11;
+        // columns: (J^T B) J'
+        A[p * LDA + pc] = c2 * r00 - s2 * r01;
+        A[p * LDA + qc] = s2 * r00 + c2 * r01;
+        A[q * LDA + pc] = c2 * r10 - s2 * r11;
+        A[q * LDA + qc] = s2 * r10 + c2 * r11;
       }
-      __syncthreads();
-      // columns p, q of A and V  (A <- A J, V <- V J)
-      for (int e = tid; e < (TP / 2) * TP; e += nt) {
+      for (int e = tid; e < NP * TP; e += kJacobiThreads) {
         const int k = e / TP, i = e % TP;
-        const int p = pq[k], q = pq[TP / 2 + k];
-        const float c = cs[k], s = cs[TP / 2 + k];
-        const float ap = A[i * LDA + p], aq = A[i * LDA + q];
-        A[i * LDA + p] = c * ap - s * aq;
-        A[i * LDA + q] = s * ap + c * aq;
+        const int p = sch[2 * k], q = sch[2 * k + 1];
+        const float c = s_c[k], sn = s_s[k];
         const float vp = V[i * LDA + p], vq = V[i * LDA + q];
-        V[i * LDA + p] = c * vp - s * vq;
-        V[i * LDA + q] = s * vp + c * vq;
+        V[i * LDA + p] = c * vp - sn * vq;
+        V[i * LDA + q] = sn * vp + c * vq;
       }
       __syncthreads();
     }
   }
-  // f_i into cs-sized scratch (reuse Tmp row 0)
-  float* f = Tmp;
-  for (int i = tid; i < TP; i += nt) {
+  // f_i, then Wm = V diag(f) V^T
+  for (int i = tid; i < TP; i += kJacobiThreads) {
     const float lam = A[i * LDA + i];
     const float sg = sqrtf(fmaxf(lam, 0.f));
     f[i] = (sg > theta) ? (sg - theta) / sg : 0.f;
     sig_out[i] = sg;
   }
+  // Tmp <- V^T (small_gemm reads B row-major)
+  for (int e = tid; e < TP * TP; e += kJacobiThreads) {
+    const int i = e / TP, j = e % TP;
+    Tmp[i * LDA + j] = V[j * LDA + i];
+  }
   __syncthreads();
-  for (int e = tid; e < TP * TP; e += nt) {
-    const int s = e / TP, t = e % TP;
-    float w = 0.f;
-    for (int i = 0; i < TP; ++i) w = fmaf(V[s * LDA + i] * f[i], V[t * LDA + i], w);
-    Wm[e] = w;
-    V_io[e] = V[s * LDA + t];
+  small_gemm<TP, LDA>(V, Tmp, A, false, f);    // A = V diag(f) V^T
+  __syncthreads();
+  for (int e = tid; e < TP * TP; e += kJacobiThreads) {
+    const int i = e / TP, j = e % TP;
+    Wm[e] = A[i * LDA + j];
+    V_io[e] = V[i * LDA + j];
   }
   if (tid == 0) *sweeps_out = sweep;
 }
 
-// Y[:, t] = sum_s Wm[s][t] X[:, s] for t in [t0, t0 + 64); optional
-// accumulation of ||Y - Y_old||^2 (dual residual of Algorithm 3) into
-// partials[block][1].  One thread per row (pixel).
+// Y[:, t] = sum_s Wm[s][t] X[:, s]: an (N x TP) x (TP x 64) product per
+// block column t0..t0+63.  A CTA computes 128 rows (pixels) x 64 outputs with
+// 256 threads, each 4 pixels x 8 outputs; X and Wm are staged in shared
+// memory.  Optionally accumulates ||Y - Y_old||^2 (the dual residual term of
+// Algorithm 3) into slot 1 of partials[block].
+constexpr int kApplyRows = 128;
+
 template <int TP>
 __global__ void __launch_bounds__(256)
 svt_apply_kernel(const float* __restrict__ X, long long ld, long long N, int T, const float* __restrict__ Wm,
-                 float* __restrict__ Y, long long ldy, int reduce, double* __restrict__ partials) {
+                 float* __restrict__ Y, long long ldy, int reduce, int vec, double* __restrict__ partials) {
   constexpr int TB = 64;
-  __shared__ __align__(16) float sW[TP][TB];
+  extern __shared__ __align__(16) float sm_apply[];
+  float (*sW)[TB] = reinterpret_cast<float (*)[TB]>(sm_apply);                       // [TP][TB]
+  float (*sx)[kApplyRows] = reinterpret_cast<float (*)[kApplyRows]>(sm_apply + TP * TB);   // [TP][rows]
+  const int tid = threadIdx.x;
   const int t0 = blockIdx.y * TB;
-  for (int e = threadIdx.x; e < TP * TB; e += blockDim.x) {
+  const int tp = tid & 31;          // pixel group: rows 4tp .. 4tp+3
+  const int tt = tid >> 5;          // output group: cols 8tt .. 8tt+7
+  for (int e = tid; e < TP * TB; e += 256) {
     const int s = e / TB, t = e % TB;
     sW[s][t] = (t0 + t < TP) ? Wm[s * TP + t0 + t] : 0.f;
   }
-  __syncthreads();
   float acc[kNumSums] = {};
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
-    float y[TB];
-#pragma unroll
-    for (int t = 0; t < TB; ++t) y[t] = 0.f;
-    for (int s = 0; s < T; ++s) {
-      const float x = __ldg(X + (long long)s * ld + i);
-#pragma unroll
-      for (int t = 0; t < TB; t += 4) {
-        const float4 w = *reinterpret_cast<const float4*>(&sW[s][t]);
-        y[t] = fmaf(w.x, x, y[t]);
-        y[t + 1] = fmaf(w.y, x, y[t + 1]);
-        y[t + 2] = fmaf(w.z, x, y[t + 2]);
-        y[t + 3] = fmaf(w.w, x, y[t + 3]);
-      }
-    }
-#pragma unroll
-    for (int t = 0; t < TB; ++t) {
-      if (t0 + t < T) {
-        float* dst = Y + (long long)(t0 + t) * ldy + i;
-        if (reduce) {
-          const float d = y[t] - *dst;
-          acc[1] = fmaf(d, d, acc[1]);
+  const long long nblk = (N + kApplyRows - 1) / kApplyRows;
+  for (long long blk = blockIdx.x; blk < nblk; blk += gridDim.x) {
+    const long long i0 = blk * kApplyRows;
+    __syncthreads();
+    for (int e = tid; e < TP * (kApplyRows / 4); e += 256) {
+      const int s = e / (kApplyRows / 4), q = e % (kApplyRows / 4);
+      const long long gi = i0 + 4 * q;
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (s < T) {
+        const float* src = X + (long long)s * ld + gi;
+        if (vec && gi + 3 < N) {
+          v = __ldg(reinterpret_cast<const float4*>(src));
+        } else {
+          if (gi < N) v.x = __ldg(src);
+          if (gi + 1 < N) v.y = __ldg(src + 1);
+          if (gi + 2 < N) v.z = __ldg(src + 2);
+          if (gi + 3 < N) v.w = __ldg(src + 3);
         }
-        *dst = y[t];
+      }
+      *reinterpret_cast<float4*>(&sx[s][4 * q]) = v;
+    }
+    __syncthreads();
+    float y[4][8];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 8; ++b) y[a][b] = 0.f;
+#pragma unroll 4
+    for (int s = 0; s < TP; ++s) {
+      const float4 x4 = *reinterpret_cast<const float4*>(&sx[s][4 * tp]);
+      const float4 w0 = *reinterpret_cast<const float4*>(&sW[s][8 * tt]);
+      const float4 w1 = *reinterpret_cast<const float4*>(&sW[s][8 * tt + 4]);
+      const float xv[4] = {x4.x, x4.y, x4.z, x4.w};
+      const float wv[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 8; ++b) y[a][b] = fmaf(wv[b], xv[a], y[a][b]);
+    }
+    const long long gi = i0 + 4 * tp;
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+      const int t = t0 + 8 * tt + b;
+      if (t >= T) continue;
+      float* dst = Y + (long long)t * ldy + gi;
+      if (vec && gi + 3 < N) {
+        const float4 nv = make_float4(y[0][b], y[1][b], y[2][b], y[3][b]);
+        if (reduce) {
+          const float4 ov = *reinterpret_cast<const float4*>(dst);
+          const float d0 = nv.x - ov.x, d1 = nv.y - ov.y, d2 = nv.z - ov.z, d3 = nv.w - ov.w;
+          acc[1] += d0 * d0 + d1 * d1 + d2 * d2 + d3 * d3;
+        }
+        *reinterpret_cast<float4*>(dst) = nv;
+      } else {
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+          if (gi + a < N) {
+            if (reduce) {
+              const float d = y[a][b] - dst[a];
+              acc[1] = fmaf(d, d, acc[1]);
+            }
+            dst[a] = y[a][b];
+          }
+        }
       }
     }
   }
-  if (reduce) {
-    block_sums_to<256>(acc, partials + ((size_t)blockIdx.y * gridDim.x + blockIdx.x) * kNumSums);
-  }
+  if (reduce) block_sums_to<256>(acc, partials + ((size_t)blockIdx.y * gridDim.x + blockIdx.x) * kNumSums);
+}
+
+template <int TP>
+constexpr size_t apply_smem() {
+  return (size_t)TP * (64 + kApplyRows) * sizeof(float);
 }
 
 template <int TP>
 size_t jacobi_smem() {
-  return (size_t)(3 * TP * (TP + 1) + TP) * sizeof(float) + TP * sizeof(int);
+  return (size_t)(3 * TP * (TP + 1) + TP) * sizeof(float);
 }
 
 }  // namespace
+
+// Relative off-diagonal Frobenius norm at which the FP32 Jacobi stops:
+// 8 u sqrt(TP), about where FP32 rounding of the rotations leaves it.
+float svt_tolerance(int T) { return 8.f * 5.96e-8f * sqrtf((float)svt_padded_T(T)); }
 
 int svt_padded_T(int T) { return T <= 16 ? 16 : (T <= 32 ? 32 : (T <= 64 ? 64 : 128)); }
 
 int svt_gram_blocks(long long N) {
   const long long nch = (N + kGramChunk - 1) / kGramChunk;
-  return (int)(nch < 152 ? nch : 152);
+  return (int)(nch < 152 * 2 ? nch : 152 * 2);
 }
 
 int svt_apply_blocks(long long N, int T, int* gy) {
   *gy = (svt_padded_T(T) + 63) / 64;
-  const long long nb = (N + 255) / 256;
+  const long long nb = (N + kApplyRows - 1) / kApplyRows;
   return (int)(nb < 152 * 8 ? nb : 152 * 8);
 }
 
@@ -296,6 +456,18 @@ cudaError_t svt_prepare() {
                                        (int)jacobi_smem<128>());
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(jacobi_svt_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)jacobi_smem<64>());
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(gram_partial_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gram_smem<128>());
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(gram_partial_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gram_smem<64>());
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(gram_partial_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gram_smem<32>());
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(gram_partial_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gram_smem<16>());
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(svt_apply_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)apply_smem<128>());
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(svt_apply_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)apply_smem<64>());
   return e;
 }
 
@@ -305,15 +477,15 @@ cudaError_t svt_launch_gram(const float* X, long long ld, long long N, int T, do
   const int TP = svt_padded_T(T);
   const int nb = svt_gram_blocks(N);
   switch (TP) {
-    case 16: gram_partial_kernel<16><<<nb, 16, 0, st>>>(X, ld, N, T, partials); break;
-    case 32: gram_partial_kernel<32><<<nb, 64, 0, st>>>(X, ld, N, T, partials); break;
-    case 64: gram_partial_kernel<64><<<nb, 256, 0, st>>>(X, ld, N, T, partials); break;
-    default: gram_partial_kernel<128><<<nb, 1024, 0, st>>>(X, ld, N, T, partials); break;
+    case 16: gram_partial_kernel<16><<<nb, kGramThreads, gram_smem<16>(), st>>>(X, ld, N, T, partials); break;
+    case 32: gram_partial_kernel<32><<<nb, kGramThreads, gram_smem<32>(), st>>>(X, ld, N, T, partials); break;
+    case 64: gram_partial_kernel<64><<<nb, kGramThreads, gram_smem<64>(), st>>>(X, ld, N, T, partials); break;
+    default: gram_partial_kernel<128><<<nb, kGramThreads, gram_smem<128>(), st>>>(X, ld, N, T, partials); break;
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const int n = TP * TP;
-  gram_reduce_kernel<<<(n + 255) / 256, 256, 0, st>>>(partials, nb, n, G);
+  gram_reduce_kernel<<<(n + 31) / 32, 256, 0, st>>>(partials, nb, n, G);
   return cudaGetLastError();
 }
 
@@ -321,10 +493,10 @@ cudaError_t svt_launch_eig(const double* G, int T, int warm, float theta, int ma
                            float* Wm, float* sig, int* sweeps, cudaStream_t st) {
   const int TP = svt_padded_T(T);
   switch (TP) {
-    case 16: jacobi_svt_kernel<16><<<1, 256, jacobi_smem<16>(), st>>>(G, warm, theta, max_sweeps, tol, V_io, Wm, sig, sweeps); break;
-    case 32: jacobi_svt_kernel<32><<<1, 512, jacobi_smem<32>(), st>>>(G, warm, theta, max_sweeps, tol, V_io, Wm, sig, sweeps); break;
-    case 64: jacobi_svt_kernel<64><<<1, 1024, jacobi_smem<64>(), st>>>(G, warm, theta, max_sweeps, tol, V_io, Wm, sig, sweeps); break;
-    default: jacobi_svt_kernel<128><<<1, 1024, jacobi_smem<128>(), st>>>(G, warm, theta, max_sweeps, tol, V_io, Wm, sig, sweeps); break;
+    case 16: jacobi_svt_kernel<16><<<1, kJacobiThreads, jacobi_smem<16>(), st>>>(G, warm, theta, max_sweeps, tol, V_io, Wm, sig, sweeps); break;
+    case 32: jacobi_svt_kernel<32><<<1, kJacobiThreads, jacobi_smem<32>(), st>>>(G, warm, theta, max_sweeps, tol, V_io, Wm, sig, sweeps); break;
+    case 64: jacobi_svt_kernel<64><<<1, kJacobiThreads, jacobi_smem<64>(), st>>>(G, warm, theta, max_sweeps, tol, V_io, Wm, sig, sweeps); break;
+    default: jacobi_svt_kernel<128><<<1, kJacobiThreads, jacobi_smem<128>(), st>>>(G, warm, theta, max_sweeps, tol, V_io, Wm, sig, sweeps); break;
   }
   return cudaGetLastError();
 }
@@ -335,11 +507,13 @@ cudaError_t svt_launch_apply(const float* X, long long ld, long long N, int T, c
   int gy = 1;
   const int nb = svt_apply_blocks(N, T, &gy);
   const dim3 grid(nb, gy);
+  const int vec = ((ld % 4) == 0 && (ldy % 4) == 0 && (reinterpret_cast<uintptr_t>(X) % 16) == 0 &&
+                   (reinterpret_cast<uintptr_t>(Y) % 16) == 0) ? 1 : 0;
   switch (TP) {
-    case 16: svt_apply_kernel<16><<<grid, 256, 0, st>>>(X, ld, N, T, Wm, Y, ldy, reduce, partials); break;
-    case 32: svt_apply_kernel<32><<<grid, 256, 0, st>>>(X, ld, N, T, Wm, Y, ldy, reduce, partials); break;
-    case 64: svt_apply_kernel<64><<<grid, 256, 0, st>>>(X, ld, N, T, Wm, Y, ldy, reduce, partials); break;
-    default: svt_apply_kernel<128><<<grid, 256, 0, st>>>(X, ld, N, T, Wm, Y, ldy, reduce, partials); break;
+    case 16: svt_apply_kernel<16><<<grid, 256, apply_smem<16>(), st>>>(X, ld, N, T, Wm, Y, ldy, reduce, vec, partials); break;
+    case 32: svt_apply_kernel<32><<<grid, 256, apply_smem<32>(), st>>>(X, ld, N, T, Wm, Y, ldy, reduce, vec, partials); break;
+    case 64: svt_apply_kernel<64><<<grid, 256, apply_smem<64>(), st>>>(X, ld, N, T, Wm, Y, ldy, reduce, vec, partials); break;
+    default: svt_apply_kernel<128><<<grid, 256, apply_smem<128>(), st>>>(X, ld, N, T, Wm, Y, ldy, reduce, vec, partials); break;
   }
   return cudaGetLastError();
 }

@@ -197,3 +197,20 @@ def test_rpca_rejects_bad_parameters(lib):
     for kw in (dict(T=1, H=4, W=4), dict(T=200, H=4, W=4), dict(T=4, H=4, W=4, n_inner=0)):
         with pytest.raises(lib.OtError):
             lib.Rpca(**kw)
+
+
+def test_rpca_graph_replay_matches_eager(lib):
+    """Warm outer iterations replayed from a CUDA graph (on a non-default
+    stream) give the same iterates as eager launches, bit for bit."""
+    Y, _, _ = rpca_video(rng_for(1, 60), T=8, H=40, W=36, n_blobs=2)
+    out = []
+    for use_graph in (0, 1):
+        stream = torch.cuda.Stream()
+        with torch.cuda.stream(stream):
+            with lib.Rpca(8, 40, 36, stream=stream, use_graph=use_graph, **RP) as rp:
+                rp.set_input(Y)
+                for _ in range(7):
+                    rp.iterate_checked(1)
+                out.append({k: rp.get(k).cpu() for k in ("S", "L", "T", "D", "Z", "W", "a")})
+    for k in out[0]:
+        assert torch.equal(out[0][k], out[1][k]), k
