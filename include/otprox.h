@@ -71,6 +71,22 @@ extern "C" {
 #define OT_KERNEL_TILED    1
 #define OT_KERNEL_RESIDENT 2
 #define OT_KERNEL_TMA      3
+/* Solver of eq. (Prox_UOT):
+ *  ALG1       -- Algorithm 1, the paper's primal-dual iteration (Sec. III-B);
+ *  PROJECTION -- ADMM with an exact projection onto {K z = k0} through the
+ *                DCT-II Neumann solve (K K^T = D D* + n_id I).  Not the
+ *                paper's algorithm; the same minimiser.  Its state: M, x, r
+ *                are the ADMM iterate z, and a is beta times the last
+ *                projection multiplier (the dual of K z = k0 at a fixed point). */
+#define OT_ALG_ALG1        0
+#define OT_ALG_PROJECTION  1
+
+/* Arithmetic of the dense DCT contractions (the Neumann solve below):
+ *  FP32       -- FP32 CUDA-core GEMMs;
+ *  SPLIT_BF16 -- tcgen05 tensor-core GEMMs on a 3-term BF16 split
+ *                (a_hi b_hi + a_hi b_lo + a_lo b_hi, FP32 accumulation). */
+#define OT_PREC_FP32       0
+#define OT_PREC_SPLIT_BF16 1
 
 typedef struct ot_prox* ot_prox_t;
 
@@ -91,6 +107,9 @@ typedef struct {
   int32_t check_every;    /* iterations between stopping tests (>= 1)            */
   int32_t kernel;         /* OT_KERNEL_*                                         */
   int32_t use_graph;      /* 1: replay each check interval as a CUDA graph       */
+  int32_t algorithm;      /* OT_ALG_*                                            */
+  int32_t precision;      /* OT_PREC_* of the DCT solves (projection form)       */
+  double  beta;           /* ADMM penalty of the projection form (> 0)           */
 } ot_prox_params;
 
 typedef struct {
@@ -106,7 +125,8 @@ typedef struct {
 
 /* Fill *p with the defaults: mode PROX, iso, unbalanced, p = 1, mu = 3,
  * rho = 0.01, default steps, tol = 1e-5, max_iter = 100000,
- * check_every = 10, kernel AUTO, use_graph = 1.  B, H, W are set to 1. */
+ * check_every = 10, kernel AUTO, use_graph = 1, algorithm ALG1,
+ * precision FP32, beta = 1.  B, H, W are set to 1. */
 void ot_prox_default_params(ot_prox_params* p);
 
 /* lambda_max(D D*) = 4 sin^2(pi (H-1) / 2H) + 4 sin^2(pi (W-1) / 2W): the
@@ -263,6 +283,17 @@ int ot_rpca_destroy(ot_rpca_t h);
  * with cudaMallocAsync on the stream and returned before the call ends.
  * Async. */
 int ot_svt(const float* X, float* Y, int64_t N, int32_t T, double theta, void* cuda_stream);
+
+/* ------------------------------------------------------ Neumann solve */
+/* Y = (D D* + c I)^{-1} X for B independent H x W images, where D D* is the
+ * grid Laplacian with zero-flux (Neumann) boundary of Theorem 1's proof; for
+ * c = 0 the pseudo-inverse (the constant mode is dropped).  Solved by the
+ * orthonormal DCT-II, which diagonalises D D* (eigenvalues
+ * 4 sin^2(pi k / 2H) + 4 sin^2(pi l / 2W)); each transform is one batched
+ * GEMM.  X, Y: DEVICE pointers, dense [B][H][W] float32; they may alias.
+ * precision: OT_PREC_*.  Allocates its tables per call.  Sync. */
+int ot_neumann_solve(const float* X, float* Y, int32_t B, int32_t H, int32_t W, double c, int32_t precision,
+                     void* cuda_stream);
 
 /* ot_prox_evaluate for a state the caller holds, without allocating.
  * The paper has no counterpart: this is a convenience for callers that

@@ -91,6 +91,10 @@ def default_params(**kw) -> ot_prox_params:
             v = NORMS[v] if isinstance(v, str) else v
         elif k == "kernel":
             v = KERNELS[v] if isinstance(v, str) else v
+        elif k == "algorithm":
+            v = _abi.ALGORITHMS[v] if isinstance(v, str) else v
+        elif k == "precision":
+            v = _abi.PRECISIONS[v] if isinstance(v, str) else v
         elif k in ("balanced", "use_graph"):
             v = int(bool(v))
         if not hasattr(p, k):
@@ -255,6 +259,17 @@ class Rpca:
         return out
 
 
+def neumann_solve(X, c: float, precision="fp32", out=None, stream=None):
+    """(D D* + c I)^{-1} X for X [B, H, W] float32 CUDA (DCT-II)."""
+    import torch
+    B, H, W = X.shape
+    Y = torch.empty_like(X) if out is None else out
+    prec = _abi.PRECISIONS[precision] if isinstance(precision, str) else precision
+    check(_lib.ot_neumann_solve(X.data_ptr(), Y.data_ptr(), B, H, W, float(c), prec, _stream_handle(stream)),
+          "ot_neumann_solve")
+    return Y
+
+
 def svt(X, theta: float, stream=None):
     """shrink*_theta of the N x T matrix whose T columns are X[t] (X: [T, ...]
     float32 CUDA tensor).  Returns a tensor of the same shape."""
@@ -266,4 +281,4 @@ def svt(X, theta: float, stream=None):
     return Y
 
 
-__all__ = ["Rpca", "svt", "rpca_default_params", "OtProx", "OtError", "default_params", "check", "LIB_PATH", "ot_prox_params", "ot_prox_result"]
+__all__ = ["Rpca", "svt", "neumann_solve", "rpca_default_params", "OtProx", "OtError", "default_params", "check", "LIB_PATH", "ot_prox_params", "ot_prox_result"]

@@ -20,6 +20,8 @@ STATUS_NAMES = {0: "OT_OK", -1: "OT_EINVAL", -2: "OT_ENOMEM", -3: "OT_ECUDA", -4
 MODES = {"prox": 0, "fixed_first": 1, "eval": 2}
 NORMS = {"iso": 0, "aniso": 1}
 KERNELS = {"auto": 0, "tiled": 1, "resident": 2, "tma": 3}
+PRECISIONS = {"fp32": 0, "split_bf16": 1}
+ALGORITHMS = {"alg1": 0, "projection": 1}
 
 c_float_p = ctypes.POINTER(ctypes.c_float)
 c_double_p = ctypes.POINTER(ctypes.c_double)
@@ -32,7 +34,8 @@ class ot_prox_params(ctypes.Structure):
                 ("mu", ctypes.c_double), ("rho", ctypes.c_double),
                 ("tau1", ctypes.c_double), ("tau2", ctypes.c_double), ("tol", ctypes.c_double),
                 ("max_iter", ctypes.c_int32), ("check_every", ctypes.c_int32),
-                ("kernel", ctypes.c_int32), ("use_graph", ctypes.c_int32)]
+                ("kernel", ctypes.c_int32), ("use_graph", ctypes.c_int32),
+                ("algorithm", ctypes.c_int32), ("precision", ctypes.c_int32), ("beta", ctypes.c_double)]
 
 
 class ot_prox_result(ctypes.Structure):
@@ -96,6 +99,8 @@ PROTOTYPES = [
     ("ot_rpca_destroy", ctypes.c_int, [ctypes.c_void_p]),
     ("ot_svt", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_double,
                               ctypes.c_void_p]),
+    ("ot_neumann_solve", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
+                                         ctypes.c_int32, ctypes.c_double, ctypes.c_int32, ctypes.c_void_p]),
     ("ot_prox_evaluate_noalloc", ctypes.c_int, [ctypes.POINTER(ot_prox_params)] + [ctypes.c_void_p] * 8 +
      [ctypes.POINTER(ot_prox_result), ctypes.c_void_p]),
 ]

@@ -63,6 +63,9 @@ void ot_prox_default_params(ot_prox_params* p) {
   p->check_every = 10;
   p->kernel = OT_KERNEL_AUTO;
   p->use_graph = 1;
+  p->algorithm = OT_ALG_ALG1;
+  p->precision = OT_PREC_FP32;
+  p->beta = 1.0;
 }
 
 double ot_lambda_max(int32_t H, int32_t W) {
@@ -103,7 +106,23 @@ static StatePtrs state_ptrs(ot_prox* h, int parity) {
 
 // Enqueue n iterations starting from ping-pong `parity`; the last one
 // reduces (and the sums are finalised into dsums) when `reduce`.
+static cudaError_t enqueue_admm(ot_prox* h, int n, bool reduce) {
+  const int nb = admm_num_blocks(h->G);
+  cudaError_t e = cudaSuccess;
+  for (int k = 0; k < n && e == cudaSuccess; ++k) {
+    const bool red = reduce && (k == n - 1);
+    e = admm_launch_z(h->G, h->AC, h->AP, red, h->partials, h->stream);
+    if (e == cudaSuccess) e = admm_launch_rhs(h->G, h->AC, h->AP, red, h->partials + (size_t)nb * kNumSums, h->stream);
+    if (e == cudaSuccess) e = dct_plan_solve(h->dct, h->AP.k, h->G.Wp, h->AP.y, h->G.Wp, h->stream);
+    if (e == cudaSuccess)
+      e = admm_launch_w(h->G, h->AC, h->AP, red, h->partials + (size_t)2 * nb * kNumSums, h->stream);
+  }
+  if (e == cudaSuccess && reduce && n > 0) e = launch_finalize_sums(h->partials, 3 * nb, h->dsums, h->stream);
+  return e;
+}
+
 static cudaError_t enqueue_iterations(ot_prox* h, int parity, int n, bool reduce) {
+  if (h->admm) return enqueue_admm(h, n, reduce);
   const int mode = h->prm.mode;
   const bool bal = h->prm.balanced != 0;
   cudaError_t e = cudaSuccess;
@@ -129,7 +148,9 @@ static cudaError_t enqueue_iterations(ot_prox* h, int parity, int n, bool reduce
   return e;
 }
 
-static int parity_after(const ot_prox* h, int parity, int n) { return h->resident ? parity : (parity ^ (n & 1)); }
+static int parity_after(const ot_prox* h, int parity, int n) {
+  return (h->resident || h->admm) ? parity : (parity ^ (n & 1));
+}
 
 // One check interval: n iterations, reduction, copy of the sums to the host.
 static int run_check_interval(ot_prox* h, int n) {
@@ -246,6 +267,12 @@ int ot_prox_create(const ot_prox_params* params, void* cuda_stream, ot_prox_t* o
   if (p.max_iter < 0) return fail(OT_EINVAL, "ot_prox_create: max_iter must be >= 0");
   if (p.check_every < 1) return fail(OT_EINVAL, "ot_prox_create: check_every must be >= 1");
   if (p.kernel < 0 || p.kernel > 3) return fail(OT_EINVAL, "ot_prox_create: unknown kernel %d", p.kernel);
+  if (p.algorithm != OT_ALG_ALG1 && p.algorithm != OT_ALG_PROJECTION)
+    return fail(OT_EINVAL, "ot_prox_create: unknown algorithm %d", p.algorithm);
+  if (p.precision != OT_PREC_FP32 && p.precision != OT_PREC_SPLIT_BF16)
+    return fail(OT_EINVAL, "ot_prox_create: unknown precision %d", p.precision);
+  if (p.algorithm == OT_ALG_PROJECTION && (!(p.beta > 0) || !isfinite(p.beta)))
+    return fail(OT_EINVAL, "ot_prox_create: beta must be > 0");
   if (!isfinite(p.tau1) || !isfinite(p.tau2)) return fail(OT_EINVAL, "ot_prox_create: steps must be finite");
   // Theorem 1: tau1 tau2 < 1 / (lambda_max + n_id)
   const double L = ot_lambda_max(p.H, p.W) + (double)ot_n_identity_blocks(p.mode, p.balanced);
@@ -282,6 +309,7 @@ int ot_prox_create(const ot_prox_params* params, void* cuda_stream, ot_prox_t* o
   } else if (p.kernel == OT_KERNEL_TMA) {
     tma = true;
   }
+  if (p.algorithm == OT_ALG_PROJECTION) resident = tma = false;
 
   ot_prox* h = (ot_prox*)calloc(1, sizeof(ot_prox));
   if (!h) return fail(OT_ENOMEM, "ot_prox_create: host allocation failed");
@@ -291,6 +319,7 @@ int ot_prox_create(const ot_prox_params* params, void* cuda_stream, ot_prox_t* o
   h->plane_elems = plane_elems;
   h->resident = resident;
   h->tma = tma;
+  h->admm = p.algorithm == OT_ALG_PROJECTION;
   const float t1 = (float)p.tau1;
   h->C.tau1 = t1;
   h->C.tau2 = (float)p.tau2;
@@ -323,7 +352,8 @@ int ot_prox_create(const ot_prox_params* params, void* cuda_stream, ot_prox_t* o
   if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
     n_sm = 152;
   h->tma_grid = (int)(ctas < (double)n_sm ? ctas : n_sm);
-  const int n_parts = (int)(ctas > (double)G.B ? ctas : G.B);
+  int n_parts = (int)(ctas > (double)G.B ? ctas : G.B);
+  if (h->admm && 3 * admm_num_blocks(G) > n_parts) n_parts = 3 * admm_num_blocks(G);
   const int n_cert = cert_num_blocks(G);
   const int np = n_parts > n_cert ? n_parts : n_cert;
   const size_t ws_bytes = (size_t)np * kNumSums * sizeof(double) + (size_t)n_cert * 4 * sizeof(double) +
@@ -341,7 +371,46 @@ int ot_prox_create(const ot_prox_params* params, void* cuda_stream, ot_prox_t* o
     ot_prox_destroy(h);
     return cuda_fail(e, "ot_prox_create: workspace allocation");
   }
-  if (resident) e = prepare_prox_resident(p.mode, p.balanced != 0, G);
+  if (h->admm && e == cudaSuccess) {
+    e = cudaMalloc(&h->admm_slab, plane_elems * 10 * sizeof(float));
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->admm_slab, 0, plane_elems * 10 * sizeof(float), h->stream);
+    if (e == cudaSuccess) {
+      AdmmPlanes& P = h->AP;
+      P.z[0] = h->Mx[0];
+      P.z[1] = h->My[0];
+      P.z[2] = h->x0;
+      P.z[3] = h->x1;
+      P.z[4] = h->r;
+      for (int k = 0; k < 5; ++k) {
+        P.w[k] = h->admm_slab + (size_t)k * plane_elems;
+        P.u[k] = h->admm_slab + (size_t)(5 + k) * plane_elems;
+      }
+      P.k = h->Mx[1];      // unused by the projection form otherwise
+      P.y = h->My[1];
+      P.a = h->a[0];
+      P.p0 = h->p0;
+      P.p1 = h->p1;
+      AdmmCoeffs& C = h->AC;
+      C.beta = (float)p.beta;
+      C.inv_beta = (float)(1.0 / p.beta);
+      C.rb = (float)(p.rho * p.beta);
+      C.inv_1rb = (float)(1.0 / (1.0 + p.rho * p.beta));
+      C.mu_over_beta = (float)(p.mu / p.beta);
+      C.r2 = (float)(1.0 / (1.0 + 2.0 * p.mu / p.beta));
+      C.iso = p.norm == OT_NORM_ISO;
+      C.pexp = p.p_exp;
+      C.free0 = p.mode == OT_MODE_PROX;
+      C.free1 = p.mode != OT_MODE_EVAL;
+      C.balanced = p.balanced;
+      h->n_id = ot_n_identity_blocks(p.mode, p.balanced);
+      const int rc = dct_plan_create(p.B, p.H, p.W, (double)h->n_id, p.precision, &h->dct);
+      if (rc != OT_OK) {
+        ot_prox_destroy(h);
+        return rc;
+      }
+    }
+  }
+  if (resident && e == cudaSuccess) e = prepare_prox_resident(p.mode, p.balanced != 0, G);
   if (tma && e == cudaSuccess) {
     e = prepare_prox_tma(p.mode, p.balanced != 0);
     int bw, bh;
@@ -393,6 +462,8 @@ int ot_prox_reset(ot_prox_t h) {
   if (!h) return fail(OT_EINVAL, "ot_prox_reset: NULL handle");
   // everything but the inputs p0, p1 (the last two planes)
   OT_CUDA(cudaMemsetAsync(h->slab, 0, h->plane_elems * 9 * sizeof(float), h->stream), "ot_prox_reset");
+  if (h->admm)
+    OT_CUDA(cudaMemsetAsync(h->admm_slab, 0, h->plane_elems * 10 * sizeof(float), h->stream), "ot_prox_reset");
   h->cur = 0;
   return OT_OK;
 }
@@ -528,12 +599,21 @@ int ot_prox_set_state(ot_prox_t h, const float* Mx, const float* My, const float
     OT_CUDA(cudaMemset2DAsync(h->My[c] + (h->G.W - 1), (size_t)h->G.Wp * fb, 0, fb, (size_t)h->G.B * h->G.H,
                               h->stream),
             "ot_prox_set_state: zeroing My[:,W-1]");
+  if (h->admm) {   // projection form: restart the splitting at w = z, u = 0
+    for (int k = 0; k < 5; ++k)
+      OT_CUDA(cudaMemcpyAsync(h->AP.w[k], h->AP.z[k], h->plane_elems * sizeof(float), cudaMemcpyDeviceToDevice,
+                              h->stream),
+              "ot_prox_set_state: w = z");
+    OT_CUDA(cudaMemsetAsync(h->AP.u[0], 0, h->plane_elems * 5 * sizeof(float), h->stream), "ot_prox_set_state: u = 0");
+  }
   return OT_OK;
 }
 
 int ot_prox_destroy(ot_prox_t h) {
   if (!h) return OT_OK;
   destroy_graphs(h);
+  if (h->dct) dct_plan_destroy(h->dct);
+  if (h->admm_slab) cudaFree(h->admm_slab);
   if (h->slab) cudaFree(h->slab);
   if (h->partials) cudaFree(h->partials);
   if (h->hsums) cudaFreeHost(h->hsums);

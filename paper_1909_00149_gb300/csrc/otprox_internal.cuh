@@ -110,6 +110,39 @@ cudaError_t launch_evaluate(const Geometry& g, const CertCoeffs& cc, const float
                             double* sums_out, double* cert_partials, double* cert_out,
                             cudaStream_t st);
 
+// ----------------------------------------------------------------- projection form
+struct AdmmCoeffs {
+  float beta, inv_beta;      // ADMM penalty and 1/beta (flux threshold)
+  float rb, inv_1rb;         // rho * beta and 1 / (1 + rho * beta) (x-step)
+  float mu_over_beta;        // r threshold (p = 1)
+  float r2;                  // 1 / (1 + 2 mu / beta)  (p = 2)
+  int iso, pexp, free0, free1, balanced;
+};
+// z, w, u: 5 planes each (Mx, My, x0, x1, r; frozen x and balanced r unused)
+struct AdmmPlanes {
+  float* z[5];
+  float* w[5];
+  float* u[5];
+  float* k;      // K(z + u) - k0
+  float* y;      // (K K^T)^{-1} k
+  float* a;      // beta y
+  const float* p0;
+  const float* p1;
+};
+int admm_num_blocks(const Geometry& g);
+cudaError_t admm_launch_z(const Geometry& g, const AdmmCoeffs& c, const AdmmPlanes& P, bool reduce, double* partials,
+                          cudaStream_t st);
+cudaError_t admm_launch_rhs(const Geometry& g, const AdmmCoeffs& c, const AdmmPlanes& P, bool reduce,
+                            double* partials, cudaStream_t st);
+cudaError_t admm_launch_w(const Geometry& g, const AdmmCoeffs& c, const AdmmPlanes& P, bool reduce, double* partials,
+                          cudaStream_t st);
+
+// DCT-II Neumann solve (dct_solve.cu)
+struct DctPlan;
+int dct_plan_create(int B, int H, int W, double c, int precision, DctPlan** out);
+void dct_plan_destroy(DctPlan* p);
+cudaError_t dct_plan_solve(DctPlan* p, const float* X, long long x_ld, float* Y, long long y_ld, cudaStream_t st);
+
 // ----------------------------------------------------------------- RPCA
 struct RpcaGeom {
   int T, H, W, Wp;

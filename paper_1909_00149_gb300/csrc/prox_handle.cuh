@@ -38,4 +38,11 @@ struct ot_prox {
   double* hsums;             // pinned host mirror
   cudaGraphExec_t graph[2];  // one check interval, by starting parity
   int graph_n;
+  // projection form (algorithm OT_ALG_PROJECTION)
+  bool admm;
+  float* admm_slab;          // z[5], w[5], u[5], k, y
+  otp::AdmmPlanes AP;
+  otp::AdmmCoeffs AC;
+  otp::DctPlan* dct;
+  int n_id;                  // identity blocks of K: the Laplacian shift c
 };
