@@ -26,6 +26,7 @@
 
 #include "../../include/otprox.h"
 #include "otprox_internal.cuh"
+#include "dct_plan.cuh"
 
 namespace otp {
 namespace {
@@ -88,20 +89,6 @@ gemm_f32_kernel(const float* __restrict__ A, int lda, const float* __restrict__ 
 
 }  // namespace
 
-// ------------------------------------------------------------------ plan
-struct DctPlan {
-  int B, H, W;
-  double c;
-  int precision;
-  // FP32 transform matrices (row-major n x n): C and C^T for each axis
-  float *CH, *CHt, *CW, *CWt;
-  float* inv_lam;     // [W][H]: 1 / (lam_W[l] + lam_H[k] + c), 0 for a zero mode
-  float* work;        // [B][max(H,W)]^2 scratch
-  void* tc;           // tensor-core plan (split BF16), or null
-};
-
-namespace {
-
 std::vector<double> dct_matrix(int n) {
   std::vector<double> C((size_t)n * n);
   const double pi = 3.14159265358979323846;
@@ -122,6 +109,8 @@ std::vector<double> path_laplacian_eigs(int n) {
   return lam;
 }
 
+namespace {
+
 cudaError_t upload(float** dst, const std::vector<float>& v) {
   cudaError_t e = cudaMalloc(dst, v.size() * sizeof(float));
   if (e == cudaSuccess) e = cudaMemcpy(*dst, v.data(), v.size() * sizeof(float), cudaMemcpyHostToDevice);
@@ -129,10 +118,6 @@ cudaError_t upload(float** dst, const std::vector<float>& v) {
 }
 
 }  // namespace
-
-int dct_tc_create(DctPlan* p);                 // dct_tcgen05.cu
-void dct_tc_destroy(DctPlan* p);
-cudaError_t dct_tc_solve(DctPlan* p, const float* X, long long x_ld, float* Y, long long y_ld, cudaStream_t st);
 
 void dct_plan_destroy(DctPlan* p) {
   if (!p) return;
@@ -191,6 +176,10 @@ int dct_plan_create(int B, int H, int W, double c, int precision, DctPlan** out)
   return OT_OK;
 }
 
+void dct_plan_set_error_flag(DctPlan* p, int* derr) {
+  if (p && derr) p->err = derr;
+}
+
 // Y = (D D* + c I)^{-1} X for B problems; X, Y device [B][H][*] with row
 // pitch x_ld / y_ld floats (problem stride H * ld).  X and Y may alias.
 cudaError_t dct_plan_solve(DctPlan* p, const float* X, long long x_ld, float* Y, long long y_ld, cudaStream_t st) {
@@ -243,7 +232,10 @@ extern "C" int ot_neumann_solve(const float* X, float* Y, int32_t B, int32_t H, 
   // X is read by G1 before Y is first written (G2), so X and Y may alias.
   cudaError_t e = dct_plan_solve(p, X, W, Y, W, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  int flag = 0;
+  if (e == cudaSuccess && p->err) e = cudaMemcpy(&flag, p->err, sizeof(int), cudaMemcpyDeviceToHost);
   dct_plan_destroy(p);
   if (e != cudaSuccess) return cuda_fail(e, "ot_neumann_solve");
+  if (flag) return fail(OT_ETIMEOUT, "ot_neumann_solve: a bounded device wait expired in a tensor-core GEMM");
   return OT_OK;
 }

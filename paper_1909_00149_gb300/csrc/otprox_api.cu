@@ -408,6 +408,7 @@ int ot_prox_create(const ot_prox_params* params, void* cuda_stream, ot_prox_t* o
         ot_prox_destroy(h);
         return rc;
       }
+      dct_plan_set_error_flag(h->dct, h->derr);
     }
   }
   if (resident && e == cudaSuccess) e = prepare_prox_resident(p.mode, p.balanced != 0, G);

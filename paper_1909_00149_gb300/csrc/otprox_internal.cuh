@@ -142,6 +142,8 @@ struct DctPlan;
 int dct_plan_create(int B, int H, int W, double c, int precision, DctPlan** out);
 void dct_plan_destroy(DctPlan* p);
 cudaError_t dct_plan_solve(DctPlan* p, const float* X, long long x_ld, float* Y, long long y_ld, cudaStream_t st);
+// Route the tensor-core kernels' timeout flag to the owner's device flag.
+void dct_plan_set_error_flag(DctPlan* p, int* derr);
 
 // ----------------------------------------------------------------- RPCA
 struct RpcaGeom {
