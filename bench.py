@@ -66,13 +66,14 @@ def measured_peaks() -> dict:
     return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0, "source": "fallback"}
 
 
-def jacobi_flops(T: int, sweeps: int) -> float:
-    """FP32 flops of one SVT eigensolve: per sweep (TP-1) rounds, each
-    rotating all TP^2 entries of A twice (rows, columns) and TP^2 of V at ~3
-    flops per entry; plus the three TP^3 products (warm start, final
-    V diag V^T)."""
+def jacobi_flops(T: int, rounds: int) -> float:
+    """FP32 flops of one SVT eigensolve: per Jacobi round, the TP/2 plane
+    rotations update the TP(TP+1)/2 stored entries of the symmetric A on both
+    sides (2 rotations x 3 flops per entry) and the TP^2 entries of V (3
+    flops per entry), about 6 TP^2; plus the three TP^3 products (warm start
+    and V diag(f) V^T)."""
     TP = 16 if T <= 16 else 32 if T <= 32 else 64 if T <= 64 else 128
-    return sweeps * (TP - 1) * 9.0 * TP * TP + 3 * 2.0 * TP ** 3
+    return rounds * 6.0 * TP * TP + 3 * 2.0 * TP ** 3
 
 
 def source_hash(name: str) -> str:
@@ -252,7 +253,7 @@ def run_ours_rpca(args, rank, world, local_rank):
     else:
         # the T x T eigensolver is one CTA by design: its ceiling is one SM's
         # FP32 FMA rate (128 lanes x 2 flop x max SM clock)
-        flops = jacobi_flops(T, res["svt_sweeps"])
+        flops = jacobi_flops(T, res["svt_rounds"])
         sm_peak = 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e9
         roof = {"bound": "alu", "achieved": flops / (phase_ms[dom] / 1e3) / 1e9, "peak": sm_peak,
                 "unit": "GFLOP/s", "traffic": None, "algorithmic_flops_per_launch": flops,
@@ -274,7 +275,7 @@ def run_ours_rpca(args, rank, world, local_rank):
                          ((12 * T + 15 * P) * H * W * 4 / 1e6, sum(pbytes) / 1e6)},
         "roofline": roof,
         "phases": phases,
-        "last_residuals": {"res_pri": res["res_pri"], "res_dual": res["res_dual"], "svt_sweeps": res["svt_sweeps"],
+        "last_residuals": {"res_pri": res["res_pri"], "res_dual": res["res_dual"], "svt_rounds": res["svt_rounds"],
                            "svt_rank": res["svt_rank"]},
         "e2e": {"value": units / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": T * H * W * 4,
                 "d2h_bytes_per_step": 8 * 8 + 4 + 4 * 64 + 4},

@@ -227,7 +227,7 @@ typedef struct {
   int32_t status;         /* OT_OK / OT_ENOTCONV / OT_ENONFINITE                  */
   double  res_pri;        /* ||(X-S-L, L-T, z-s_t, w-s_{t+1})|| / ||Y||           */
   double  res_dual;       /* rho ||(dX, dT, dz, dw)|| / ||Y||                     */
-  int32_t svt_sweeps;     /* Jacobi sweeps of the last SVT                        */
+  int32_t svt_rounds;     /* Jacobi rounds of the last SVT (T_pad - 1 per sweep)  */
   int32_t svt_rank;       /* singular values above gamma/rho in the last SVT     */
 } ot_rpca_result;
 

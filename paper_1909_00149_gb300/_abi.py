@@ -58,7 +58,7 @@ class ot_rpca_params(ctypes.Structure):
 
 class ot_rpca_result(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int32), ("status", ctypes.c_int32), ("res_pri", ctypes.c_double),
-                ("res_dual", ctypes.c_double), ("svt_sweeps", ctypes.c_int32), ("svt_rank", ctypes.c_int32)]
+                ("res_dual", ctypes.c_double), ("svt_rounds", ctypes.c_int32), ("svt_rank", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}

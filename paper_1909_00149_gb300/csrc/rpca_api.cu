@@ -312,7 +312,7 @@ static void fill_rpca_result(const ot_rpca* h, ot_rpca_result* r) {
   const double ny = fmax(h->y_norm, 1e-30);
   r->res_pri = sqrt(s[2] + s[3] + s[4] + s[5]) / ny;
   r->res_dual = h->prm.rho * sqrt(s[0] + s[1] + s[6] + s[7]) / ny;
-  r->svt_sweeps = *reinterpret_cast<const int*>(h->hsums + kNumSums);
+  r->svt_rounds = *reinterpret_cast<const int*>(h->hsums + kNumSums);
   const float* sig = reinterpret_cast<const float*>(h->hsums + kNumSums + 2);
   int rank = 0;
   for (int i = 0; i < h->prm.T; ++i) rank += sig[i] > (float)(h->prm.gamma / h->prm.rho);

@@ -151,7 +151,7 @@ __device__ __forceinline__ void small_gemm(const float* A, const float* B, float
 // Wm = V diag(f) V^T with f_i = max(sigma_i - theta, 0) / sigma_i,
 // sigma_i = sqrt(max(lambda_i, 0)).  V_io: warm-start eigenvectors in (when
 // warm) and the new ones out.  sig_out: sigma_i (diagnostics), sweeps_out:
-// sweeps used.
+// Jacobi rounds used (TP - 1 per sweep).
 // Round-robin ordering: each round rotates the TP/2 disjoint pairs of a
 // precomputed schedule.  Phase 1: warp k forms the rotation J_k of pair k
 // from its 2 x 2 diagonal block.  Phase 2: each thread owns 2 x 2 blocks
@@ -325,7 +325,398 @@ jacobi_svt_kernel(const double* __restrict__ G, int warm, float theta, int max_s
     Wm[e] = A[i * LDA + j];
     V_io[e] = V[i * LDA + j];
   }
-  if (tid == 0) *sweeps_out = sweep;
+  if (tid == 0) *sweeps_out = sweep * (TP - 1);   // rounds
+}
+
+// The same eigensolve for TP <= 64, pipelined with fixed addressing.
+// Pairing by the circle method: slots top k = k and bottom k = TP/2 + k form
+// pair k; between rounds slot 0 stays and the other TP - 1 slots advance one
+// step along the ring top 1 -> ... -> top TP/2-1 -> bottom TP/2-1 -> ... ->
+// bottom 0 -> top 1, so each index meets every other once per sweep of TP - 1
+// rounds.  A is stored in slot order (A_slot[s][s'] = A[index at s][index at
+// s']), upper triangle, double-buffered: a round reads the pair blocks of the
+// current buffer and writes the rotated entries straight to their shifted
+// slots in the other, so every shared-memory address a thread touches is the
+// same in every round.  The rows of V live in registers in slot order: thread
+// (row i, segment g) holds the kJregM pairs g*kJregM..., rotates them in place
+// and passes one value to each ring neighbour segment by a warp shuffle.
+// One barrier per round: while warps 1.. apply the rotations of round r,
+// lane k of warp 0 forms the rotation of round r + 1's pair k from the three
+// entries that round r produces for it (recomputed with the same operations,
+// so they are bit-identical to the stored ones).
+//
+// Stopping.  Only Wm = F(A) = V f(Lambda) V^T is needed, f(lam) =
+// max(1 - theta / sqrt(lam), 0).  Writing A = D + E (E off-diagonal), the
+// first-order change of F is dd_ij e_ij with dd_ij the divided difference of
+// f between lam_i and lam_j, so rotations inside the subspace that f maps to
+// zero do not change Wm.  Every kJregCheck rounds the solver stops when
+// either the plain test ||E||_F <= tol ||diag||_2 holds, or the weighted one
+// sqrt(sum_ij (dd_ij e_ij)^2) <= tol max_i f_i, where dd_ij is bounded by the
+// largest slope of f on [min(lam_i, lam_j) - eps, max(lam_i, lam_j) + eps],
+// eps = ||E||_F (by Weyl's inequality every eigenvalue lies within eps of the
+// diagonal, so a pair whose interval stays below theta^2 cannot contribute).
+constexpr int kJregThreads = 512;
+constexpr int kJregCheck = 16;  // rounds between stopping tests
+constexpr int kJregM = 4;       // pairs per register segment of a V row
+
+__host__ __device__ constexpr int upper_idx(int i, int j, int ld) { return i < j ? i * ld + j : j * ld + i; }
+
+// slot that the value at slot s moves to between rounds, and its inverse
+template <int NP>
+__device__ __forceinline__ int ring_next(int s) {
+  return s == 0 ? 0 : s < NP - 1 ? s + 1 : s == NP - 1 ? 2 * NP - 1 : s == NP ? 1 : s - 1;
+}
+template <int NP>
+__device__ __forceinline__ int ring_prev(int s) {
+  return s == 0 ? 0 : s == 1 ? NP : s < NP ? s - 1 : s == 2 * NP - 1 ? NP - 1 : s + 1;
+}
+
+// c x - s y and s x + c y with a fixed operation order (no contraction
+// choices), so that two threads computing the same entry agree bit for bit
+__device__ __forceinline__ float rot_lo(float c, float s, float x, float y) { return fmaf(c, x, __fmul_rn(-s, y)); }
+__device__ __forceinline__ float rot_hi(float c, float s, float x, float y) { return fmaf(s, x, __fmul_rn(c, y)); }
+
+template <int TP>
+constexpr size_t jreg_smem() {
+  return (size_t)(4 * TP * (TP + 1) + TP) * sizeof(float);
+}
+
+template <int TP>
+__global__ void __launch_bounds__(kJregThreads, 1)
+jacobi_reg_kernel(const double* __restrict__ G, int warm, float theta, int max_sweeps, float tol,
+                  float* __restrict__ V_io, float* __restrict__ Wm, float* __restrict__ sig_out,
+                  int* __restrict__ rounds_out) {
+  constexpr int LDA = TP + 1;
+  constexpr int NP = TP / 2;
+  constexpr int S = NP / kJregM;           // register segments per V row
+  constexpr int NOFF = NP * (NP - 1) / 2;  // off-diagonal pair blocks kb < kc
+  constexpr int NB = NOFF + NP;
+  constexpr int NAPP = kJregThreads - 32;  // block-applying threads (warps 1..)
+  constexpr int NBT = (NB + NAPP - 1) / NAPP;
+  constexpr int R = TP - 1;                // rounds per sweep
+  constexpr int NW = kJregThreads / 32;
+  static_assert(NP <= 32, "one rotation per lane of warp 0");
+  static_assert(S >= 2 && S <= 32 && (S & (S - 1)) == 0, "segments must be a power of two within a warp");
+  static_assert((TP * S) % 32 == 0 && TP * S <= kJregThreads, "V rows must fill whole warps");
+  static_assert(NBT <= 2, "at most two pair blocks per thread");
+  extern __shared__ float sm[];
+  // sm: two slot-ordered copies of A (upper triangle, ping-pong), then V, Tmp, f
+  float* V = sm + 2 * TP * LDA;           // [TP][LDA]
+  float* Tmp = V + TP * LDA;              // [TP][LDA]
+  float* f = Tmp + TP * LDA;              // [TP]
+  __shared__ float s_rot[2][3][NP];       // (c, s, t) of each pair, by round parity
+  __shared__ unsigned char s_pl[R][TP];   // index held by each slot at round r
+  __shared__ float s_slope[TP];
+  __shared__ unsigned char s_act[TP];
+  __shared__ float red[2][NW];
+  __shared__ int s_go;
+  __shared__ float s_eps;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+
+  for (int e = tid; e < R * TP; e += kJregThreads) {
+    const int r = e / TP, slot = e % TP;
+    int pl = 0;
+    if (slot != 0) {
+      const int ring = slot < NP ? slot - 1 : TP - 2 - (slot - NP);
+      const int j = ((ring - r) % R + R) % R;       // ring position this slot's index started from
+      pl = j <= NP - 2 ? j + 1 : NP + TP - 2 - j;
+    }
+    s_pl[r][slot] = (unsigned char)pl;
+  }
+  // applier threads: their pair blocks (read offsets in the current buffer,
+  // write offsets at the shifted slots in the next); kind 0 none, 1 off-diagonal, 2 own pair
+  int rd[NBT][4], wr[NBT][4], bkb[NBT], bkc[NBT], kind[NBT];
+#pragma unroll
+  for (int u = 0; u < NBT; ++u) {
+    const int e = tid - 32 + u * NAPP;
+    kind[u] = 0;
+    bkb[u] = bkc[u] = 0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) rd[u][q] = wr[u][q] = 0;
+    if (warp > 0 && e < NB) {
+      int kb, kc;
+      if (e < NOFF) {
+        int rem = e;
+        kb = 0;
+        while (rem >= NP - 1 - kb) { rem -= NP - 1 - kb; ++kb; }
+        kc = kb + 1 + rem;
+        kind[u] = 1;
+      } else {
+        kb = kc = e - NOFF;
+        kind[u] = 2;
+      }
+      bkb[u] = kb;
+      bkc[u] = kc;
+      const int rs[2] = {kb, NP + kb};
+      const int cs[2] = {kc, NP + kc};
+      if (kind[u] == 1) {
+#pragma unroll
+        for (int a = 0; a < 2; ++a)
+#pragma unroll
+          for (int b = 0; b < 2; ++b) {
+            rd[u][2 * a + b] = upper_idx(rs[a], cs[b], LDA);
+            wr[u][2 * a + b] = upper_idx(ring_next<NP>(rs[a]), ring_next<NP>(cs[b]), LDA);
+          }
+      } else {
+        rd[u][0] = rs[0] * LDA + rs[0];
+        rd[u][1] = rs[1] * LDA + rs[1];
+        rd[u][2] = upper_idx(rs[0], rs[1], LDA);
+        const int n0 = ring_next<NP>(rs[0]), n1 = ring_next<NP>(rs[1]);
+        wr[u][0] = n0 * LDA + n0;
+        wr[u][1] = n1 * LDA + n1;
+        wr[u][2] = upper_idx(n0, n1, LDA);
+      }
+    }
+  }
+  // rotation lanes (warp 0, lane k < NP): where next round's pair k comes from.
+  // Its top is now at slot P, its bottom at slot Q, in pairs kP != kQ.
+  int pP = 0, pQ = 0, pPdg = 0, pQdg = 0, pPpq = 0, pQpq = 0, pB[4] = {0, 0, 0, 0};
+  int pkP = 0, pkQ = 0, pkb = 0, pkc = 0;
+  bool pPbot = false, pQbot = false, pa = false, pb = false;
+  if (warp == 0 && lane < NP) {
+    const int P = ring_prev<NP>(lane), Q = ring_prev<NP>(NP + lane);
+    pP = P;
+    pQ = Q;
+    pPbot = P >= NP;
+    pQbot = Q >= NP;
+    pkP = pPbot ? P - NP : P;
+    pkQ = pQbot ? Q - NP : Q;
+    pPdg = P * LDA + P;
+    pQdg = Q * LDA + Q;
+    pPpq = pkP * LDA + NP + pkP;
+    pQpq = pkQ * LDA + NP + pkQ;
+    pkb = pkP < pkQ ? pkP : pkQ;
+    pkc = pkP < pkQ ? pkQ : pkP;
+    pa = pkP < pkQ ? pPbot : pQbot;         // row slot (in pair kb) is a bottom slot
+    pb = pkP < pkQ ? pQbot : pPbot;         // column slot (in pair kc) is a bottom slot
+    pB[0] = upper_idx(pkb, pkc, LDA);
+    pB[1] = upper_idx(pkb, NP + pkc, LDA);
+    pB[2] = upper_idx(NP + pkb, pkc, LDA);
+    pB[3] = upper_idx(NP + pkb, NP + pkc, LDA);
+  }
+  (void)pP;
+  (void)pQ;
+
+  float* A = sm;
+  for (int e = tid; e < TP * TP; e += kJregThreads) {
+    const int i = e / TP, j = e % TP;
+    A[i * LDA + j] = (float)G[e];
+    V[i * LDA + j] = warm ? V_io[e] : (i == j ? 1.f : 0.f);
+  }
+  __syncthreads();
+  if (warm) {   // A <- V^T G V
+    small_gemm<TP, LDA>(A, V, Tmp, false, nullptr);
+    __syncthreads();
+    small_gemm<TP, LDA>(V, Tmp, A, true, nullptr);
+    __syncthreads();
+  }
+  for (int e = tid; e < TP * TP; e += kJregThreads) {   // symmetric part into the upper triangle
+    const int i = e / TP, j = e % TP;
+    if (i < j) A[i * LDA + j] = 0.5f * (A[i * LDA + j] + A[j * LDA + i]);
+  }
+  const bool vown = tid < TP * S;          // warp-uniform
+  const int vi = tid / S, vg = tid % S;
+  float vt[kJregM], vb[kJregM];
+  if (vown) {
+#pragma unroll
+    for (int j = 0; j < kJregM; ++j) {
+      vt[j] = V[vi * LDA + vg * kJregM + j];
+      vb[j] = V[vi * LDA + NP + vg * kJregM + j];
+    }
+  }
+  __syncthreads();
+  if (tid < NP) {   // rotations of the first round
+    float c, sn, tn;
+    jacobi_rotation(A[tid * LDA + tid], A[(NP + tid) * LDA + NP + tid], A[tid * LDA + NP + tid], c, sn, tn);
+    s_rot[0][0][tid] = c;
+    s_rot[0][1][tid] = sn;
+    s_rot[0][2][tid] = tn;
+  }
+  __syncthreads();
+
+  const float th2 = theta * theta;
+  const int max_rounds = max_sweeps * R;
+  int done = 0, r = 0, cur = 0;    // rounds done; round within the sweep; current buffer
+  for (;; ++done, r = (r + 1 == R) ? 0 : r + 1) {
+    A = sm + cur * (TP * LDA);
+    if (done % kJregCheck == 0 || done == max_rounds) {
+      float off = 0.f, dg = 0.f;
+      for (int e = tid; e < TP * TP; e += kJregThreads) {
+        const int i = e / TP, j = e % TP;
+        const float v = A[i * LDA + j];
+        if (i == j) dg = fmaf(v, v, dg);
+        else if (i < j) off = fmaf(2.f * v, v, off);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        off += __shfl_down_sync(0xffffffffu, off, o);
+        dg += __shfl_down_sync(0xffffffffu, dg, o);
+      }
+      if (lane == 0) {
+        red[0][warp] = off;
+        red[1][warp] = dg;
+      }
+      __syncthreads();
+      if (tid == 0) {
+        float so = 0.f, sd = 0.f;
+        for (int w = 0; w < NW; ++w) {
+          so += red[0][w];
+          sd += red[1][w];
+        }
+        s_go = so > tol * tol * sd;
+        s_eps = sqrtf(so);
+      }
+      __syncthreads();
+      if (s_go && theta > 0.f) {   // the weighted test
+        const float eps = s_eps;
+        float fmax = 0.f;
+        if (tid < TP) {
+          const float li = A[tid * LDA + tid];
+          const float x = fmaxf(li - eps, th2);
+          s_slope[tid] = theta * 0.5f / (x * sqrtf(x));   // largest slope of f on [li - eps, inf)
+          s_act[tid] = li + eps > th2;
+          const float sg = sqrtf(fmaxf(li, 0.f));
+          fmax = sg > theta ? (sg - theta) / sg : 0.f;
+        }
+        __syncthreads();
+        float wsum = 0.f;
+        for (int e = tid; e < TP * TP; e += kJregThreads) {
+          const int i = e / TP, j = e % TP;
+          if (i < j && (s_act[i] | s_act[j])) {
+            const float t = A[i * LDA + j] * fmaxf(s_slope[i], s_slope[j]);
+            wsum = fmaf(2.f * t, t, wsum);
+          }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          wsum += __shfl_down_sync(0xffffffffu, wsum, o);
+          fmax = fmaxf(fmax, __shfl_down_sync(0xffffffffu, fmax, o));
+        }
+        if (lane == 0) {
+          red[0][warp] = wsum;
+          red[1][warp] = fmax;
+        }
+        __syncthreads();
+        if (tid == 0) {
+          float sw = 0.f, fm = 0.f;
+          for (int w = 0; w < NW; ++w) {
+            sw += red[0][w];
+            fm = fmaxf(fm, red[1][w]);
+          }
+          if (sw <= tol * tol * fm * fm) s_go = 0;
+        }
+        __syncthreads();
+      }
+      if (!s_go || done == max_rounds) break;
+    }
+    const float* rc = &s_rot[done & 1][0][0];
+    float* rn = &s_rot[(done + 1) & 1][0][0];
+    float* An = sm + (cur ^ 1) * (TP * LDA);
+    if (warp == 0) {
+      if (lane < NP) {
+        // the three entries of next round's pair, as this round leaves them
+        const float tP = rc[2 * NP + pkP], tQ = rc[2 * NP + pkQ];
+        const float aPP = A[pPdg], aQQ = A[pQdg], aPpq = A[pPpq], aQpq = A[pQpq];
+        const float app = pPbot ? fmaf(tP, aPpq, aPP) : fmaf(-tP, aPpq, aPP);
+        const float aqq = pQbot ? fmaf(tQ, aQpq, aQQ) : fmaf(-tQ, aQpq, aQQ);
+        const float c = rc[pkb], sn = rc[NP + pkb], c2 = rc[pkc], s2 = rc[NP + pkc];
+        const float a00 = A[pB[0]], a01 = A[pB[1]], a10 = A[pB[2]], a11 = A[pB[3]];
+        const float r0 = pa ? rot_hi(c, sn, a00, a10) : rot_lo(c, sn, a00, a10);
+        const float r1 = pa ? rot_hi(c, sn, a01, a11) : rot_lo(c, sn, a01, a11);
+        const float apq = pb ? rot_hi(c2, s2, r0, r1) : rot_lo(c2, s2, r0, r1);
+        float cn, snn, tnn;
+        jacobi_rotation(app, aqq, apq, cn, snn, tnn);
+        rn[lane] = cn;
+        rn[NP + lane] = snn;
+        rn[2 * NP + lane] = tnn;
+      }
+    } else {
+#pragma unroll
+      for (int u = 0; u < NBT; ++u) {
+        if (kind[u] == 1) {
+          const float c = rc[bkb[u]], sn = rc[NP + bkb[u]], c2 = rc[bkc[u]], s2 = rc[NP + bkc[u]];
+          const float a00 = A[rd[u][0]], a01 = A[rd[u][1]], a10 = A[rd[u][2]], a11 = A[rd[u][3]];
+          const float r00 = rot_lo(c, sn, a00, a10), r01 = rot_lo(c, sn, a01, a11);
+          const float r10 = rot_hi(c, sn, a00, a10), r11 = rot_hi(c, sn, a01, a11);
+          An[wr[u][0]] = rot_lo(c2, s2, r00, r01);
+          An[wr[u][1]] = rot_hi(c2, s2, r00, r01);
+          An[wr[u][2]] = rot_lo(c2, s2, r10, r11);
+          An[wr[u][3]] = rot_hi(c2, s2, r10, r11);
+        } else if (kind[u] == 2) {
+          // the pair's own block: a_pq is zeroed exactly and -/+ t a_pq moves
+          // onto the diagonal (the accurate classical update)
+          const float apq = A[rd[u][2]], tn = rc[2 * NP + bkb[u]];
+          An[wr[u][0]] = fmaf(-tn, apq, A[rd[u][0]]);
+          An[wr[u][1]] = fmaf(tn, apq, A[rd[u][1]]);
+          An[wr[u][2]] = 0.f;
+        }
+      }
+    }
+    if (vown) {
+#pragma unroll
+      for (int j = 0; j < kJregM; ++j) {
+        const int k = vg * kJregM + j;
+        const float c = rc[k], sn = rc[NP + k];
+        const float vp = vt[j], vq = vb[j];
+        vt[j] = rot_lo(c, sn, vp, vq);
+        vb[j] = rot_hi(c, sn, vp, vq);
+      }
+      // one step along the ring
+      const float recv_top = __shfl_up_sync(0xffffffffu, vt[kJregM - 1], 1, S);
+      const float recv_bot = __shfl_down_sync(0xffffffffu, vb[0], 1, S);
+      float nt[kJregM], nb[kJregM];
+      if (vg == 0) {
+        nt[0] = vt[0];
+        nt[1] = vb[0];
+#pragma unroll
+        for (int j = 2; j < kJregM; ++j) nt[j] = vt[j - 1];
+      } else {
+        nt[0] = recv_top;
+#pragma unroll
+        for (int j = 1; j < kJregM; ++j) nt[j] = vt[j - 1];
+      }
+#pragma unroll
+      for (int j = 0; j < kJregM - 1; ++j) nb[j] = vb[j + 1];
+      nb[kJregM - 1] = (vg == S - 1) ? vt[kJregM - 1] : recv_bot;
+#pragma unroll
+      for (int j = 0; j < kJregM; ++j) {
+        vt[j] = nt[j];
+        vb[j] = nb[j];
+      }
+    }
+    cur ^= 1;
+    __syncthreads();
+  }
+  // slot s holds index s_pl[r][s]
+  const unsigned char* pl = s_pl[r];
+  if (vown) {
+#pragma unroll
+    for (int j = 0; j < kJregM; ++j) {
+      V[vi * LDA + pl[vg * kJregM + j]] = vt[j];
+      V[vi * LDA + pl[NP + vg * kJregM + j]] = vb[j];
+    }
+  }
+  for (int sl = tid; sl < TP; sl += kJregThreads) {
+    const float lam = A[sl * LDA + sl];
+    const float sg = sqrtf(fmaxf(lam, 0.f));
+    f[pl[sl]] = (sg > theta) ? (sg - theta) / sg : 0.f;
+    sig_out[pl[sl]] = sg;
+  }
+  __syncthreads();
+  for (int e = tid; e < TP * TP; e += kJregThreads) {
+    const int i = e / TP, j = e % TP;
+    Tmp[i * LDA + j] = V[j * LDA + i];
+  }
+  __syncthreads();
+  float* Out = sm + (cur ^ 1) * (TP * LDA);
+  small_gemm<TP, LDA>(V, Tmp, Out, false, f);    // V diag(f) V^T
+  __syncthreads();
+  for (int e = tid; e < TP * TP; e += kJregThreads) {
+    const int i = e / TP, j = e % TP;
+    Wm[e] = Out[i * LDA + j];
+    V_io[e] = V[i * LDA + j];
+  }
+  if (tid == 0) *rounds_out = done;
 }
 
 // Y[:, t] = sum_s Wm[s][t] X[:, s]: an (N x TP) x (TP x 64) product per
@@ -455,7 +846,7 @@ cudaError_t svt_prepare() {
   cudaError_t e = cudaFuncSetAttribute(jacobi_svt_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)jacobi_smem<128>());
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(jacobi_svt_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)jacobi_smem<64>());
+    e = cudaFuncSetAttribute(jacobi_reg_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)jreg_smem<64>());
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(gram_partial_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gram_smem<128>());
   if (e == cudaSuccess)
@@ -493,9 +884,9 @@ cudaError_t svt_launch_eig(const double* G, int T, int warm, float theta, int ma
                            float* Wm, float* sig, int* sweeps, cudaStream_t st) {
   const int TP = svt_padded_T(T);
   switch (TP) {
-    case 16: jacobi_svt_kernel<16><<<1, kJacobiThreads, jacobi_smem<16>(), st>>>(G, warm, theta, max_sweeps, tol, V_io, Wm, sig, sweeps); break;
-    case 32: jacobi_svt_kernel<32><<<1, kJacobiThreads, jacobi_smem<32>(), st>>>(G, warm, theta, max_sweeps, tol, V_io, Wm, sig, sweeps); break;
-    case 64: jacobi_svt_kernel<64><<<1, kJacobiThreads, jacobi_smem<64>(), st>>>(G, warm, theta, max_sweeps, tol, V_io, Wm, sig, sweeps); break;
+    case 16: jacobi_reg_kernel<16><<<1, kJregThreads, jreg_smem<16>(), st>>>(G, warm, theta, max_sweeps, tol, V_io, Wm, sig, sweeps); break;
+    case 32: jacobi_reg_kernel<32><<<1, kJregThreads, jreg_smem<32>(), st>>>(G, warm, theta, max_sweeps, tol, V_io, Wm, sig, sweeps); break;
+    case 64: jacobi_reg_kernel<64><<<1, kJregThreads, jreg_smem<64>(), st>>>(G, warm, theta, max_sweeps, tol, V_io, Wm, sig, sweeps); break;
     default: jacobi_svt_kernel<128><<<1, kJacobiThreads, jacobi_smem<128>(), st>>>(G, warm, theta, max_sweeps, tol, V_io, Wm, sig, sweeps); break;
   }
   return cudaGetLastError();
