@@ -281,7 +281,8 @@ int ot_rpca_destroy(ot_rpca_t h);
  * N floats (X + t*N), via the T x T Gram matrix and a Jacobi eigensolver.
  * X, Y: DEVICE pointers, must not alias; 1 <= T <= 128.  Workspace is taken
  * with cudaMallocAsync on the stream and returned before the call ends.
- * Async. */
+ * Synchronises the stream; OT_ETIMEOUT if a bounded wait in the tensor-core
+ * Gram kernel expired. */
 int ot_svt(const float* X, float* Y, int64_t N, int32_t T, double theta, void* cuda_stream);
 
 /* ------------------------------------------------------ Neumann solve */

@@ -246,7 +246,7 @@ static int enqueue_outer(ot_rpca* h, bool sums) {
   // fork: line 10 on the side stream
   OT_CUDA(cudaEventRecord(h->ev_fork, h->stream), "fork");
   OT_CUDA(cudaStreamWaitEvent(h->side, h->ev_fork, 0), "fork wait");
-  OT_CUDA(svt_launch_gram(h->P.LD, plane, N, h->prm.T, h->gram_partials, h->Gm, h->side), "svt gram");
+  OT_CUDA(svt_launch_gram(h->P.LD, plane, N, h->prm.T, h->gram_partials, h->Gm, h->prox->derr, h->side), "svt gram");
   OT_CUDA(svt_launch_eig(h->Gm, h->prm.T, h->warm, (float)(h->prm.gamma / h->prm.rho), h->prm.svt_max_sweeps, svt_tolerance(h->prm.T),
                          h->V, h->Wm, h->sig, h->sweeps, h->side),
           "svt eig");
@@ -404,7 +404,7 @@ int ot_rpca_step_profiled(ot_rpca_t h, double* phase_ms) {
   if (e == cudaSuccess) e = cudaEventRecord(ev[0], h->stream);
   if (e == cudaSuccess) e = rpca_launch_pre(h->G, h->C, h->P, h->partials, h->stream);
   if (e == cudaSuccess) e = cudaEventRecord(ev[1], h->stream);
-  if (e == cudaSuccess) e = svt_launch_gram(h->P.LD, plane, plane, h->prm.T, h->gram_partials, h->Gm, h->stream);
+  if (e == cudaSuccess) e = svt_launch_gram(h->P.LD, plane, plane, h->prm.T, h->gram_partials, h->Gm, h->prox->derr, h->stream);
   if (e == cudaSuccess) e = cudaEventRecord(ev[2], h->stream);
   if (e == cudaSuccess)
     e = svt_launch_eig(h->Gm, h->prm.T, h->warm, (float)(h->prm.gamma / h->prm.rho), h->prm.svt_max_sweeps, svt_tolerance(h->prm.T),
@@ -476,7 +476,7 @@ int ot_svt(const float* X, float* Y, int64_t N, int32_t T, double theta, void* c
   const int TP = svt_padded_T(T);
   const int ng = svt_gram_blocks(N);
   const size_t bytes = (size_t)ng * TP * TP * sizeof(double) + (size_t)TP * TP * sizeof(double) +
-                       (size_t)3 * TP * TP * sizeof(float) + 64;
+                       (size_t)3 * TP * TP * sizeof(float) + 64 + 16;
   OT_CUDA(svt_prepare(), "ot_svt: prepare");
   void* ws = nullptr;
   OT_CUDA(cudaMallocAsync(&ws, bytes, st), "ot_svt: cudaMallocAsync");
@@ -486,12 +486,18 @@ int ot_svt(const float* X, float* Y, int64_t N, int32_t T, double theta, void* c
   float* Wm = V + (size_t)TP * TP;
   float* sig = Wm + (size_t)TP * TP;
   int* sweeps = reinterpret_cast<int*>(sig + (size_t)TP * TP);
-  cudaError_t e = svt_launch_gram(X, N, N, T, part, Gm, st);
+  int* derr = sweeps + 4;
+  int herr = 0;
+  cudaError_t e = cudaMemsetAsync(derr, 0, sizeof(int), st);
+  if (e == cudaSuccess) e = svt_launch_gram(X, N, N, T, part, Gm, derr, st);
   if (e == cudaSuccess) e = svt_launch_eig(Gm, T, 0, (float)theta, 60, svt_tolerance(T), V, Wm, sig, sweeps, st);
   if (e == cudaSuccess) e = svt_launch_apply(X, N, N, T, Wm, Y, N, false, nullptr, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, derr, sizeof(int), cudaMemcpyDeviceToHost, st);
   cudaError_t e2 = cudaFreeAsync(ws, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_fail(e, "ot_svt");
   if (e2 != cudaSuccess) return cuda_fail(e2, "ot_svt: cudaFreeAsync");
+  if (herr) return fail(OT_ETIMEOUT, "ot_svt: a bounded device wait expired in the Gram kernel");
   return OT_OK;
 }
 

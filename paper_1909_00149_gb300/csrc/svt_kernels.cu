@@ -831,9 +831,15 @@ float svt_tolerance(int T) { return 8.f * 5.96e-8f * sqrtf((float)svt_padded_T(T
 
 int svt_padded_T(int T) { return T <= 16 ? 16 : (T <= 32 ? 32 : (T <= 64 ? 64 : 128)); }
 
-int svt_gram_blocks(long long N) {
+static int gram_simt_blocks(long long N) {
   const long long nch = (N + kGramChunk - 1) / kGramChunk;
   return (int)(nch < 152 * 2 ? nch : 152 * 2);
+}
+
+// Partial-Gram slots to allocate: enough for either Gram kernel.
+int svt_gram_blocks(long long N) {
+  const int a = gram_simt_blocks(N), b = svt_gram_tc_blocks(N);
+  return a > b ? a : b;
 }
 
 int svt_apply_blocks(long long N, int T, int* gy) {
@@ -863,10 +869,19 @@ cudaError_t svt_prepare() {
 }
 
 // partials: >= svt_gram_blocks(N) * TP * TP doubles; G: TP * TP doubles.
-cudaError_t svt_launch_gram(const float* X, long long ld, long long N, int T, double* partials, double* G,
+// With an error flag (err != NULL) and T > 16 the tensor-core kernel runs
+// (gram_tcgen05.cu); it sets *err if a bounded wait expires.
+cudaError_t svt_launch_gram(const float* X, long long ld, long long N, int T, double* partials, double* G, int* err,
                             cudaStream_t st) {
   const int TP = svt_padded_T(T);
-  const int nb = svt_gram_blocks(N);
+  const int n = TP * TP;
+  if (err && TP >= 32 && (ld * 4) % 16 == 0 && (reinterpret_cast<uintptr_t>(X) & 15) == 0) {
+    cudaError_t e = svt_launch_gram_tc(X, ld, N, T, partials, err, st);
+    if (e != cudaSuccess) return e;
+    gram_reduce_kernel<<<(n + 31) / 32, 256, 0, st>>>(partials, svt_gram_tc_blocks(N), n, G);
+    return cudaGetLastError();
+  }
+  const int nb = gram_simt_blocks(N);
   switch (TP) {
     case 16: gram_partial_kernel<16><<<nb, kGramThreads, gram_smem<16>(), st>>>(X, ld, N, T, partials); break;
     case 32: gram_partial_kernel<32><<<nb, kGramThreads, gram_smem<32>(), st>>>(X, ld, N, T, partials); break;
@@ -875,7 +890,6 @@ cudaError_t svt_launch_gram(const float* X, long long ld, long long N, int T, do
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  const int n = TP * TP;
   gram_reduce_kernel<<<(n + 31) / 32, 256, 0, st>>>(partials, nb, n, G);
   return cudaGetLastError();
 }
