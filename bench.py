@@ -247,7 +247,7 @@ def run_ours_rpca(args, rank, world, local_rank):
     launches = 1 if dom != 4 else args.n_inner
     if pbytes[dom] > 0:
         roof = {"bound": "hbm", "achieved": pbytes[dom] / (phase_ms[dom] / 1e3) / 1e9, "peak": peaks["hbm_gbs"],
-                "unit": "GB/s", "traffic": ncu_traffic(kname, "step"),
+                "unit": "GB/s", "traffic": ncu_traffic(kname, kname),
                 "algorithmic_bytes_per_launch": pbytes[dom] / launches,
                 "peak_source": peaks["source"] + " copy bandwidth (of measured)"}
     else:

@@ -506,42 +506,38 @@ prox_resident_kernel(const Geometry G, const IterCoeffs C, float* __restrict__ g
 
 // ===================================================================== K3
 // Fixed-order FP64 sum of per-CTA partials (deterministic: no atomics).
+// partials[p][k], p < n, k < NQ (NQ a power of two).  One CTA of 1024
+// threads reads the n * NQ values coalesced: thread t always meets quantity
+// k = t % NQ and sums every 1024th value; lanes with equal k are then
+// combined by shuffles, the 32 warp results in shared memory by warp 0.
+// Quantities whose bit is set in max_mask are reduced by max instead of sum.
+constexpr int kFinThreads = 1024;
+
 template <int NQ>
-__global__ void __launch_bounds__(256) finalize_kernel(const double* __restrict__ partials, int n,
-                                                       unsigned max_mask, double* __restrict__ out) {
-  __shared__ double red[8][NQ];
+__global__ void __launch_bounds__(kFinThreads) finalize_kernel(const double* __restrict__ partials, int n,
+                                                               unsigned max_mask, double* __restrict__ out) {
+  static_assert(NQ >= 1 && NQ <= 32 && (NQ & (NQ - 1)) == 0, "NQ must be a power of two <= 32");
+  __shared__ double red[kFinThreads / 32][NQ];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  double v[NQ];
-#pragma unroll
-  for (int k = 0; k < NQ; ++k) v[k] = 0.0;
-  for (int p = tid; p < n; p += 256) {
-#pragma unroll
-    for (int k = 0; k < NQ; ++k) {
-      const double x = partials[(size_t)p * NQ + k];
-      v[k] = ((max_mask >> k) & 1u) ? fmax(v[k], x) : v[k] + x;
-    }
+  const int k = tid & (NQ - 1);
+  const bool is_max = (max_mask >> k) & 1u;
+  const long long total = (long long)n * NQ;
+  double v = 0.0;
+  for (long long e = tid; e < total; e += kFinThreads) {
+    const double x = __ldg(partials + e);
+    v = is_max ? fmax(v, x) : v + x;
   }
 #pragma unroll
-  for (int k = 0; k < NQ; ++k) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const double y = __shfl_down_sync(0xffffffffu, v[k], o);
-      v[k] = ((max_mask >> k) & 1u) ? fmax(v[k], y) : v[k] + y;
-    }
-    if (lane == 0) red[warp][k] = v[k];
+  for (int o = 16; o >= NQ; o >>= 1) {
+    const double y = __shfl_down_sync(0xffffffffu, v, o);
+    v = is_max ? fmax(v, y) : v + y;
   }
+  if (lane < NQ) red[warp][lane] = v;
   __syncthreads();
-  if (warp == 0) {
-#pragma unroll
-    for (int k = 0; k < NQ; ++k) {
-      double t = lane < 8 ? red[lane][k] : 0.0;
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        const double y = __shfl_down_sync(0xffffffffu, t, o);
-        t = ((max_mask >> k) & 1u) ? fmax(t, y) : t + y;
-      }
-      if (lane == 0) out[k] = t;
-    }
+  if (warp == 0 && lane < NQ) {
+    double t = red[0][lane];
+    for (int w = 1; w < kFinThreads / 32; ++w) t = is_max ? fmax(t, red[w][lane]) : t + red[w][lane];
+    out[lane] = t;
   }
 }
 
@@ -760,7 +756,7 @@ cudaError_t prepare_prox_resident(int mode, bool balanced, const Geometry& g) {
 }
 
 cudaError_t launch_finalize_sums(const double* partials, int n, double* out, cudaStream_t st) {
-  finalize_kernel<kNumSums><<<1, 256, 0, st>>>(partials, n, 0u, out);
+  finalize_kernel<kNumSums><<<1, kFinThreads, 0, st>>>(partials, n, 0u, out);
   return cudaGetLastError();
 }
 
@@ -780,10 +776,10 @@ cudaError_t launch_evaluate(const Geometry& g, const CertCoeffs& cc, const float
   eval_pass1_kernel<<<nb, kCertThreads, 0, st>>>(g, cc, Mx, My, a, x0, x1, r, p0, p1, partials, cert_partials);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  finalize_kernel<kNumSums><<<1, 256, 0, st>>>(partials, nb, 0u, sums_out);
-  finalize_kernel<kCertQ><<<1, 256, 0, st>>>(cert_partials, nb, 1u, cert_out);
+  finalize_kernel<kNumSums><<<1, kFinThreads, 0, st>>>(partials, nb, 0u, sums_out);
+  finalize_kernel<kCertQ><<<1, kFinThreads, 0, st>>>(cert_partials, nb, 1u, cert_out);
   eval_pass2_kernel<<<nb, kCertThreads, 0, st>>>(g, cc, Mx, My, a, x0, x1, p0, p1, cert_out, cert_partials);
-  finalize_kernel<kCertQ><<<1, 256, 0, st>>>(cert_partials, nb, 1u, cert_out);
+  finalize_kernel<kCertQ><<<1, kFinThreads, 0, st>>>(cert_partials, nb, 1u, cert_out);
   return cudaGetLastError();
 }
 
