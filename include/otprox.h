@@ -276,6 +276,70 @@ int ot_rpca_reset(ot_rpca_t h);
 int ot_rpca_get_params(ot_rpca_t h, ot_rpca_params* out);
 int ot_rpca_destroy(ot_rpca_t h);
 
+/* ------------------------------------------------------------------------
+ * UOT-DF / BPDN+UOT-DF (Algorithm 2, Sec. IV-A.1), Phi = I, for B
+ * independent frames [B][H][W]:
+ *   min_{s >= 0} 1/2 ||y - s||^2 + lambda ||s||_1 + kappa V_mu(s, s0)
+ * (eq. UOT-DF for lambda = 0, eq. BPDN+UOT-DF for lambda > 0), s0 the
+ * prediction of the current state.  ADMM with the splitting s = x = z of
+ * Sec. IV-A.1; line 6 runs n_inner warm-started Algorithm 1 iterations in
+ * the fixed-first form (eq. Prox_UOT_specialcase, prox weight kappa/rho).
+ * Readings of the printed algorithm: the s-update minimises both augmented
+ * terms, s = max((x + a + z + b)/2 - lambda/(2 rho), 0); stopping uses the
+ * primal and dual residuals ||(x - s, z - s)|| and rho ||(dx, dz)|| relative
+ * to ||y||, both <= tol. */
+typedef struct ot_uotdf* ot_uotdf_t;
+
+typedef struct {
+  int32_t B, H, W;        /* independent frames, rows, columns                   */
+  double  kappa;          /* OT weight > 0                                        */
+  double  mu;             /* growth/decay penalty of V_mu > 0                     */
+  double  rho;            /* ADMM penalty > 0                                     */
+  double  lambda;         /* sparsity weight >= 0 (0: UOT-DF)                     */
+  int32_t n_inner;        /* Algorithm 1 iterations per ADMM iteration (>= 1)    */
+  int32_t norm;           /* OT_NORM_* of the flux                                */
+  int32_t p_exp;          /* 1 or 2: exponent of the source term                  */
+  double  tol;            /* tolerance on both relative residuals                 */
+  int32_t max_iter;       /* iteration cap of ot_uotdf_solve                      */
+  int32_t check_every;    /* iterations between residual checks (>= 1)           */
+  int32_t prox_kernel;    /* OT_KERNEL_* of the inner Algorithm 1                 */
+} ot_uotdf_params;
+
+typedef struct {
+  int32_t iters;          /* ADMM iterations run by this call                     */
+  int32_t status;         /* OT_OK / OT_ENOTCONV / OT_ENONFINITE                  */
+  double  res_pri;        /* ||(x - s, z - s)|| / ||y||                            */
+  double  res_dual;       /* rho ||(dx, dz)|| / ||y||                              */
+} ot_uotdf_result;
+
+/* Variables readable with ot_uotdf_get, each [B][H][W]. */
+#define OT_UOTDF_S 0
+#define OT_UOTDF_X 1
+#define OT_UOTDF_Z 2
+#define OT_UOTDF_A 3
+#define OT_UOTDF_B 4
+
+/* Defaults: kappa 0.5, mu 3, rho 1, lambda 0, n_inner 1, iso, p_exp 1,
+ * tol 1e-5, max_iter 20000, check_every 10, prox_kernel AUTO; B = H = W = 1. */
+void ot_uotdf_default_params(ot_uotdf_params* p);
+/* All state zero (Algorithm 2 line 2).  OT_EINVAL on a bad parameter. */
+int ot_uotdf_create(const ot_uotdf_params* params, void* cuda_stream, ot_uotdf_t* out);
+/* y: measurements, s0: prediction; [B][H][W] float32, host or device.
+ * Synchronises; OT_ENONFINITE if y is not finite. */
+int ot_uotdf_set_input(ot_uotdf_t h, const float* y, const float* s0);
+/* n ADMM iterations, stream-ordered, no stopping test. */
+int ot_uotdf_step(ot_uotdf_t h, int32_t n);
+/* n iterations, the last one with the residual sums; synchronises. */
+int ot_uotdf_iterate_checked(ot_uotdf_t h, int32_t n, ot_uotdf_result* res);
+/* Iterate to the stopping rule (checked every check_every iterations). */
+int ot_uotdf_solve(ot_uotdf_t h, ot_uotdf_result* res);
+/* Copy variable var (OT_UOTDF_*) to out [B][H][W]; synchronises. */
+int ot_uotdf_get(ot_uotdf_t h, int32_t var, float* out);
+/* Zero the state (keeps y and s0). */
+int ot_uotdf_reset(ot_uotdf_t h);
+int ot_uotdf_get_params(ot_uotdf_t h, ot_uotdf_params* out);
+int ot_uotdf_destroy(ot_uotdf_t h);
+
 /* Singular-value thresholding shrink*_theta(X) = U max(Sigma - theta, 0) V^T
  * (Sec. IV-B.1, Algorithm 3 line 10) of an N x T matrix stored as T columns of
  * N floats (X + t*N), via the T x T Gram matrix and a Jacobi eigensolver.

@@ -259,6 +259,76 @@ class Rpca:
         return out
 
 
+def uotdf_default_params(**kw) -> "_abi.ot_uotdf_params":
+    p = _abi.ot_uotdf_params()
+    _lib.ot_uotdf_default_params(ctypes.byref(p))
+    for k, v in kw.items():
+        k = "lambda_" if k in ("lam", "lambda") else k
+        if k == "prox_kernel":
+            v = KERNELS[v] if isinstance(v, str) else v
+        elif k == "norm":
+            v = NORMS[v] if isinstance(v, str) else v
+        if not hasattr(p, k):
+            raise TypeError(f"unknown parameter {k!r}")
+        setattr(p, k, v)
+    return p
+
+
+class Uotdf:
+    """UOT-DF / BPDN+UOT-DF (Algorithm 2, Phi = I) on B independent H x W frames."""
+
+    def __init__(self, B: int, H: int, W: int, stream=None, **params):
+        self.B, self.H, self.W = int(B), int(H), int(W)
+        p = uotdf_default_params(B=self.B, H=self.H, W=self.W, **params)
+        h = ctypes.c_void_p()
+        self._stream = _stream_handle(stream)
+        check(_lib.ot_uotdf_create(ctypes.byref(p), self._stream, ctypes.byref(h)), "ot_uotdf_create")
+        self.h = h
+        self.params = _abi.ot_uotdf_params()
+        check(_lib.ot_uotdf_get_params(self.h, ctypes.byref(self.params)), "ot_uotdf_get_params")
+
+    def close(self):
+        if getattr(self, "h", None):
+            _lib.ot_uotdf_destroy(self.h)
+            self.h = None
+
+    __del__ = close
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def set_input(self, y, s0):
+        A = _Arrays(self.B * self.H * self.W)
+        check(_lib.ot_uotdf_set_input(self.h, A.ptr(y), A.ptr(s0)), "ot_uotdf_set_input")
+
+    def step(self, n: int):
+        check(_lib.ot_uotdf_step(self.h, int(n)), "ot_uotdf_step")
+
+    def iterate_checked(self, n: int = 1) -> dict:
+        r = _abi.ot_uotdf_result()
+        check(_lib.ot_uotdf_iterate_checked(self.h, int(n), ctypes.byref(r)), "ot_uotdf_iterate_checked")
+        return r.as_dict()
+
+    def solve(self) -> dict:
+        r = _abi.ot_uotdf_result()
+        check(_lib.ot_uotdf_solve(self.h, ctypes.byref(r)), "ot_uotdf_solve", ok=(OT_OK, OT_ENOTCONV))
+        return r.as_dict()
+
+    def reset(self):
+        check(_lib.ot_uotdf_reset(self.h), "ot_uotdf_reset")
+
+    def get(self, name: str, device=None):
+        import torch
+        dev = torch.device("cuda") if device is None else torch.device(device)
+        out = torch.empty((self.B, self.H, self.W), dtype=torch.float32, device=dev)
+        A = _Arrays(out.numel())
+        check(_lib.ot_uotdf_get(self.h, _abi.UOTDF_VARS[name], A.ptr(out, True)), "ot_uotdf_get")
+        return out
+
+
 def neumann_solve(X, c: float, precision="fp32", out=None, stream=None):
     """(D D* + c I)^{-1} X for X [B, H, W] float32 CUDA (DCT-II)."""
     import torch
@@ -281,4 +351,4 @@ def svt(X, theta: float, stream=None):
     return Y
 
 
-__all__ = ["Rpca", "svt", "neumann_solve", "rpca_default_params", "OtProx", "OtError", "default_params", "check", "LIB_PATH", "ot_prox_params", "ot_prox_result"]
+__all__ = ["Uotdf", "uotdf_default_params", "Rpca", "svt", "neumann_solve", "rpca_default_params", "OtProx", "OtError", "default_params", "check", "LIB_PATH", "ot_prox_params", "ot_prox_result"]

@@ -64,6 +64,24 @@ class ot_rpca_result(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class ot_uotdf_params(ctypes.Structure):
+    _fields_ = [("B", ctypes.c_int32), ("H", ctypes.c_int32), ("W", ctypes.c_int32),
+                ("kappa", ctypes.c_double), ("mu", ctypes.c_double), ("rho", ctypes.c_double),
+                ("lambda_", ctypes.c_double), ("n_inner", ctypes.c_int32), ("norm", ctypes.c_int32),
+                ("p_exp", ctypes.c_int32), ("tol", ctypes.c_double), ("max_iter", ctypes.c_int32),
+                ("check_every", ctypes.c_int32), ("prox_kernel", ctypes.c_int32)]
+
+
+class ot_uotdf_result(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int32), ("status", ctypes.c_int32), ("res_pri", ctypes.c_double),
+                ("res_dual", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+UOTDF_VARS = {"s": 0, "x": 1, "z": 2, "a": 3, "b": 4}
+
 RPCA_VARS = {"S": 0, "L": 1, "X": 2, "T": 3, "A": 4, "D": 5, "B": 6, "C": 7, "Z": 8, "W": 9,
              "Mx": 10, "My": 11, "r": 12, "a": 13}
 RPCA_PAIR_VARS = {"B", "C", "Z", "W", "Mx", "My", "r", "a"}
@@ -97,6 +115,17 @@ PROTOTYPES = [
     ("ot_rpca_reset", ctypes.c_int, [ctypes.c_void_p]),
     ("ot_rpca_get_params", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ot_rpca_params)]),
     ("ot_rpca_destroy", ctypes.c_int, [ctypes.c_void_p]),
+    ("ot_uotdf_default_params", None, [ctypes.POINTER(ot_uotdf_params)]),
+    ("ot_uotdf_create", ctypes.c_int, [ctypes.POINTER(ot_uotdf_params), ctypes.c_void_p,
+                                       ctypes.POINTER(ctypes.c_void_p)]),
+    ("ot_uotdf_set_input", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    ("ot_uotdf_step", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
+    ("ot_uotdf_iterate_checked", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ot_uotdf_result)]),
+    ("ot_uotdf_solve", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ot_uotdf_result)]),
+    ("ot_uotdf_get", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]),
+    ("ot_uotdf_reset", ctypes.c_int, [ctypes.c_void_p]),
+    ("ot_uotdf_get_params", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ot_uotdf_params)]),
+    ("ot_uotdf_destroy", ctypes.c_int, [ctypes.c_void_p]),
     ("ot_svt", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_double,
                               ctypes.c_void_p]),
     ("ot_neumann_solve", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
