@@ -157,6 +157,7 @@ struct RpcaCoeffs {
 // [T-1][H][Wp] (z = prox x0, w = prox x1, Bz, Cw, p0, p1, zprev, wprev).
 struct RpcaPlanes {
   float *X, *L, *A, *Tm, *D, *Y, *S, *LD;
+  float* Tn;                // the SVT output of this outer iteration (Tm holds the previous one)
   float *z, *w, *Bz, *Cw, *p0, *p1, *zprev, *wprev;
 };
 int rpca_num_blocks(const RpcaGeom& g);
@@ -180,7 +181,11 @@ cudaError_t svt_launch_gram_tc(const float* X, long long ld, long long N, int T,
 cudaError_t svt_launch_eig(const double* G, int T, int warm, float theta, int max_sweeps, float tol, float* V_io,
                            float* Wm, float* sig, int* sweeps, cudaStream_t st);
 cudaError_t svt_launch_apply(const float* X, long long ld, long long N, int T, const float* Wm, float* Y,
-                             long long ldy, bool reduce, double* partials, cudaStream_t st);
+                             long long ldy, bool reduce, double* partials, int* err, cudaStream_t st);
+// tensor-core apply (svt_tcgen05.cu); T_pad = 32 or 64
+int svt_apply_tc_blocks(long long N);
+cudaError_t svt_launch_apply_tc(const float* X, long long ld, long long N, int T, const float* Wm, float* Y,
+                                long long ldy, int* err, cudaStream_t st);
 
 int fail(int code, const char* fmt, ...);
 int cuda_fail(cudaError_t e, const char* what);

@@ -55,8 +55,9 @@ struct ot_rpca {
   cudaStream_t side;
   cudaEvent_t ev_fork, ev_join;
   // one warm outer iteration (with its residual sums) as a graph, by the
-  // ping-pong parity of the inner prox state
-  cudaGraphExec_t graph[2];
+  // ping-pong parity of the inner prox state and of the SVT output planes
+  cudaGraphExec_t graph[2][2];
+  int tpar;                  // flips when Tm and Tn swap
 };
 
 extern "C" {
@@ -83,7 +84,8 @@ void ot_rpca_default_params(ot_rpca_params* p) {
 int ot_rpca_destroy(ot_rpca_t h) {
   if (!h) return OT_OK;
   for (int k = 0; k < 2; ++k)
-    if (h->graph[k]) cudaGraphExecDestroy(h->graph[k]);
+    for (int j = 0; j < 2; ++j)
+      if (h->graph[k][j]) cudaGraphExecDestroy(h->graph[k][j]);
   if (h->ev_fork) cudaEventDestroy(h->ev_fork);
   if (h->ev_join) cudaEventDestroy(h->ev_join);
   if (h->side) cudaStreamDestroy(h->side);
@@ -144,7 +146,7 @@ int ot_rpca_create(const ot_rpca_params* params, void* cuda_stream, ot_rpca_t* o
 
   const size_t plane = (size_t)h->G.plane;
   const size_t nframe = (size_t)p.T * plane, npair = (size_t)(p.T - 1) * plane;
-  cudaError_t e = cudaMalloc(&h->slab, (8 * nframe + 4 * npair) * sizeof(float));
+  cudaError_t e = cudaMalloc(&h->slab, (9 * nframe + 4 * npair) * sizeof(float));
   if (e != cudaSuccess) {
     ot_rpca_destroy(h);
     return cuda_fail(e, "ot_rpca_create: cudaMalloc(state)");
@@ -163,6 +165,7 @@ int ot_rpca_create(const ot_rpca_params* params, void* cuda_stream, ot_rpca_t* o
   P.Cw = q; q += npair;
   P.zprev = q; q += npair;
   P.wprev = q; q += npair;
+  P.Tn = q; q += nframe;
   P.z = h->prox->x0;
   P.w = h->prox->x1;
   P.p0 = h->prox->p0;
@@ -192,7 +195,7 @@ int ot_rpca_create(const ot_rpca_params* params, void* cuda_stream, ot_rpca_t* o
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming);
-  if (e == cudaSuccess) e = cudaMemsetAsync(h->slab, 0, (8 * nframe + 4 * npair) * sizeof(float), h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->slab, 0, (9 * nframe + 4 * npair) * sizeof(float), h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) {
     ot_rpca_destroy(h);
@@ -212,8 +215,11 @@ int ot_rpca_reset(ot_rpca_t h) {
   if (!h) return fail(OT_EINVAL, "ot_rpca_reset: NULL handle");
   const size_t plane = (size_t)h->G.plane;
   const size_t nframe = (size_t)h->prm.T * plane, npair = (size_t)(h->prm.T - 1) * plane;
-  // every plane but Y
-  OT_CUDA(cudaMemsetAsync(h->P.X, 0, 5 * nframe * sizeof(float), h->stream), "ot_rpca_reset");
+  // every plane but Y (X L A Tm D are adjacent, as are S LD and the pair planes; Tm, Tn may have swapped)
+  OT_CUDA(cudaMemsetAsync(h->P.X, 0, 3 * nframe * sizeof(float), h->stream), "ot_rpca_reset");
+  OT_CUDA(cudaMemsetAsync(h->P.D, 0, nframe * sizeof(float), h->stream), "ot_rpca_reset");
+  OT_CUDA(cudaMemsetAsync(h->P.Tm, 0, nframe * sizeof(float), h->stream), "ot_rpca_reset");
+  OT_CUDA(cudaMemsetAsync(h->P.Tn, 0, nframe * sizeof(float), h->stream), "ot_rpca_reset");
   OT_CUDA(cudaMemsetAsync(h->P.S, 0, (2 * nframe + 4 * npair) * sizeof(float), h->stream), "ot_rpca_reset");
   h->warm = 0;
   return ot_prox_reset(h->prox);
@@ -251,8 +257,8 @@ static int enqueue_outer(ot_rpca* h, bool sums) {
                          h->V, h->Wm, h->sig, h->sweeps, h->side),
           "svt eig");
   h->warm = 1;
-  OT_CUDA(svt_launch_apply(h->P.LD, plane, N, h->prm.T, h->Wm, h->P.Tm, plane, true,
-                           h->partials + (size_t)h->nb_rpca * kNumSums, h->side),
+  OT_CUDA(svt_launch_apply(h->P.LD, plane, N, h->prm.T, h->Wm, h->P.Tn, plane, false, nullptr, h->prox->derr,
+                           h->side),
           "svt apply");
   OT_CUDA(cudaEventRecord(h->ev_join, h->side), "join");
   // line 11 on the handle's stream, concurrently
@@ -260,10 +266,9 @@ static int enqueue_outer(ot_rpca* h, bool sums) {
   if (rc != OT_OK) return rc;
   // join before lines 12-15
   OT_CUDA(cudaStreamWaitEvent(h->stream, h->ev_join, 0), "join wait");
-  OT_CUDA(rpca_launch_post(h->G, h->P, h->partials + (size_t)(h->nb_rpca + h->nb_apply) * kNumSums, h->stream),
-          "rpca post");
+  OT_CUDA(rpca_launch_post(h->G, h->P, h->partials + (size_t)h->nb_rpca * kNumSums, h->stream), "rpca post");
   if (sums) {
-    OT_CUDA(launch_finalize_sums(h->partials, 2 * h->nb_rpca + h->nb_apply, h->dsums, h->stream), "rpca finalize");
+    OT_CUDA(launch_finalize_sums(h->partials, 2 * h->nb_rpca, h->dsums, h->stream), "rpca finalize");
     OT_CUDA(cudaMemcpyAsync(h->hsums, h->dsums, kNumSums * sizeof(double), cudaMemcpyDeviceToHost, h->stream),
             "rpca sums copy");
     OT_CUDA(cudaMemcpyAsync(reinterpret_cast<int*>(h->hsums + kNumSums), h->sweeps, sizeof(int),
@@ -282,12 +287,25 @@ static int enqueue_outer(ot_rpca* h, bool sums) {
 // warm (the graph bakes in the warm flag and the prox buffers of one
 // ping-pong parity), eager otherwise.  Graph replays always finalise the
 // residual sums (a few microseconds).
+// The SVT output just written (Tn) becomes the previous one (Tm) for the next
+// outer iteration.
+static void swap_svt_planes(ot_rpca* h) {
+  float* t = h->P.Tm;
+  h->P.Tm = h->P.Tn;
+  h->P.Tn = t;
+  h->tpar ^= 1;
+}
+
 static int run_outer(ot_rpca* h, bool sums) {
   const bool can_graph = h->prm.use_graph && h->stream != nullptr && h->warm;
-  if (!can_graph) return enqueue_outer(h, sums);
+  if (!can_graph) {
+    const int rc = enqueue_outer(h, sums);
+    if (rc == OT_OK) swap_svt_planes(h);
+    return rc;
+  }
   ot_prox* px = h->prox;
-  const int par = px->cur;
-  if (!h->graph[par]) {
+  const int par = px->cur, tp = h->tpar;
+  if (!h->graph[par][tp]) {
     cudaGraph_t g = nullptr;
     OT_CUDA(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal), "rpca graph capture");
     const int rc = enqueue_outer(h, true);
@@ -298,12 +316,13 @@ static int run_outer(ot_rpca* h, bool sums) {
       return rc;
     }
     if (e2 != cudaSuccess) return cuda_fail(e2, "rpca graph capture end");
-    const cudaError_t e3 = cudaGraphInstantiate(&h->graph[par], g, 0);
+    const cudaError_t e3 = cudaGraphInstantiate(&h->graph[par][tp], g, 0);
     cudaGraphDestroy(g);
     if (e3 != cudaSuccess) return cuda_fail(e3, "rpca graph instantiate");
   }
-  OT_CUDA(cudaGraphLaunch(h->graph[par], h->stream), "rpca graph launch");
+  OT_CUDA(cudaGraphLaunch(h->graph[par][tp], h->stream), "rpca graph launch");
   px->cur = px->resident ? par : (par ^ (h->prm.n_inner & 1));
+  swap_svt_planes(h);
   return OT_OK;
 }
 
@@ -414,16 +433,19 @@ int ot_rpca_step_profiled(ot_rpca_t h, double* phase_ms) {
     e = cudaEventRecord(ev[3], h->stream);
   }
   if (e == cudaSuccess)
-    e = svt_launch_apply(h->P.LD, plane, plane, h->prm.T, h->Wm, h->P.Tm, plane, true,
-                         h->partials + (size_t)h->nb_rpca * kNumSums, h->stream);
+    e = svt_launch_apply(h->P.LD, plane, plane, h->prm.T, h->Wm, h->P.Tn, plane, false, nullptr, h->prox->derr,
+                         h->stream);
   if (e == cudaSuccess) e = cudaEventRecord(ev[4], h->stream);
   if (e == cudaSuccess) {
     rc = ot_prox_step(h->prox, h->prm.n_inner);
     if (rc == OT_OK) e = cudaEventRecord(ev[5], h->stream);
   }
   if (e == cudaSuccess && rc == OT_OK)
-    e = rpca_launch_post(h->G, h->P, h->partials + (size_t)(h->nb_rpca + h->nb_apply) * kNumSums, h->stream);
-  if (e == cudaSuccess && rc == OT_OK) e = cudaEventRecord(ev[6], h->stream);
+    e = rpca_launch_post(h->G, h->P, h->partials + (size_t)h->nb_rpca * kNumSums, h->stream);
+  if (e == cudaSuccess && rc == OT_OK) {
+    swap_svt_planes(h);
+    e = cudaEventRecord(ev[6], h->stream);
+  }
   if (e == cudaSuccess && rc == OT_OK) e = cudaEventSynchronize(ev[6]);
   for (int k = 0; k < 6 && e == cudaSuccess && rc == OT_OK; ++k) {
     float ms = 0.f;
@@ -491,7 +513,7 @@ int ot_svt(const float* X, float* Y, int64_t N, int32_t T, double theta, void* c
   cudaError_t e = cudaMemsetAsync(derr, 0, sizeof(int), st);
   if (e == cudaSuccess) e = svt_launch_gram(X, N, N, T, part, Gm, derr, st);
   if (e == cudaSuccess) e = svt_launch_eig(Gm, T, 0, (float)theta, 60, svt_tolerance(T), V, Wm, sig, sweeps, st);
-  if (e == cudaSuccess) e = svt_launch_apply(X, N, N, T, Wm, Y, N, false, nullptr, st);
+  if (e == cudaSuccess) e = svt_launch_apply(X, N, N, T, Wm, Y, N, false, nullptr, derr, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, derr, sizeof(int), cudaMemcpyDeviceToHost, st);
   cudaError_t e2 = cudaFreeAsync(ws, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);

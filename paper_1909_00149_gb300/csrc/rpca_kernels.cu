@@ -10,13 +10,14 @@
 //   LD  = L + D                                   (the SVT input, line 10)
 //   p0_t = s_t - b_t,  p1_t = s_{t+1} - c_{t+1}   (the prox centres, line 11)
 // and keeps z, w of this iteration for the dual residual.
-// post (lines 12-15):
-//   A += X - S - L,  D += L - Tm,  b_t += z_t - s_t,  c_{t+1} += w_{t+1} - s_{t+1}
+// post (lines 12-15), with Tn the SVT output of this iteration and Tm the
+// previous one:
+//   A += X - S - L,  D += L - Tn,  b_t += z_t - s_t,  c_{t+1} += w_{t+1} - s_{t+1}
 // with the ADMM residual sums.  Readings (see the oracle): the sign of the
 // A-update follows the augmented Lagrangian; the x-update keeps rho; S >= 0.
 //
-// Partial-sum slots (kNumSums per block): 0 ||dX||^2, 1 ||dTm||^2 (the SVT
-// apply), 2 ||X-S-L||^2, 3 ||L-Tm||^2, 4 ||z-s_t||^2, 5 ||w-s_{t+1}||^2,
+// Partial-sum slots (kNumSums per block): 0 ||dX||^2, 1 ||Tn - Tm||^2,
+// 2 ||X-S-L||^2, 3 ||L-Tn||^2, 4 ||z-s_t||^2, 5 ||w-s_{t+1}||^2,
 // 6 ||dz||^2, 7 ||dw||^2.
 #include <cuda_runtime.h>
 #include <math.h>
@@ -94,14 +95,16 @@ rpca_post_kernel(const RpcaGeom g, const RpcaPlanes P, double* __restrict__ part
     const long long o = 4 * q;
     const long long op = o - (long long)t * g.plane;
     const bool hz = t < g.T - 1, hw = t > 0;
-    const float4 x = ldg4(P.X + o), s = ldg4(P.S + o), l = ldg4(P.L + o), tm = ldg4(P.Tm + o);
+    const float4 x = ldg4(P.X + o), s = ldg4(P.S + o), l = ldg4(P.L + o), tn = ldg4(P.Tn + o), tm = ldg4(P.Tm + o);
     float4 a = ldg4(P.A + o), d = ldg4(P.D + o);
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
       const float r1 = f4c(x, e) - f4c(s, e) - f4c(l, e);
-      const float r2 = f4c(l, e) - f4c(tm, e);
+      const float r2 = f4c(l, e) - f4c(tn, e);
+      const float dt = f4c(tn, e) - f4c(tm, e);
       f4(a, e) += r1;
       f4(d, e) += r2;
+      acc[1] = fmaf(dt, dt, acc[1]);
       acc[2] = fmaf(r1, r1, acc[2]);
       acc[3] = fmaf(r2, r2, acc[3]);
     }

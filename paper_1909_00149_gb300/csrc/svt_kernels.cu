@@ -906,11 +906,17 @@ cudaError_t svt_launch_eig(const double* G, int T, int warm, float theta, int ma
   return cudaGetLastError();
 }
 
+// With an error flag (err != NULL), no residual sum, T_pad = 32 or 64 and a
+// TMA-compatible X the tensor-core kernel runs (svt_tcgen05.cu); it sets
+// *err if a bounded wait expires.  partials (when reduce):
+// svt_apply_blocks(N, T) * gy slots, ||Y - Y_old||^2 in slot 1.
 cudaError_t svt_launch_apply(const float* X, long long ld, long long N, int T, const float* Wm, float* Y,
-                             long long ldy, bool reduce, double* partials, cudaStream_t st) {
+                             long long ldy, bool reduce, double* partials, int* err, cudaStream_t st) {
   const int TP = svt_padded_T(T);
   int gy = 1;
   const int nb = svt_apply_blocks(N, T, &gy);
+  if (err && !reduce && (TP == 32 || TP == 64) && ld % 4 == 0 && (reinterpret_cast<uintptr_t>(X) & 15) == 0)
+    return svt_launch_apply_tc(X, ld, N, T, Wm, Y, ldy, err, st);
   const dim3 grid(nb, gy);
   const int vec = ((ld % 4) == 0 && (ldy % 4) == 0 && (reinterpret_cast<uintptr_t>(X) % 16) == 0 &&
                    (reinterpret_cast<uintptr_t>(Y) % 16) == 0) ? 1 : 0;

@@ -29,7 +29,8 @@ def svt_bound(X, theta):
     return max(1e-5, 8 * U32 * (s[0] / max(theta, 1e-30) + np.sqrt(X.shape[1])))
 
 
-@pytest.mark.parametrize("N,T,rank", [(3000, 8, 2), (4096, 33, 3), (20000, 64, 3), (5000, 100, 4), (999, 5, 1)])
+@pytest.mark.parametrize("N,T,rank", [(3000, 8, 2), (4096, 33, 3), (20000, 64, 3), (5000, 100, 4), (999, 5, 1),
+                                      (2048, 32, 2), (65536, 64, 3), (4100, 40, 3)])
 def test_svt_matches_oracle(lib, N, T, rank):
     rng = np.random.default_rng(N + T)
     U = rng.uniform(0, 1, (N, rank))
@@ -128,7 +129,7 @@ def test_rpca_elementwise_and_prox_parity(lib, T, H, W, k):
     assert abs(res["res_dual"] - dual) <= 1e-4 * dual + 1e-9
 
 
-@pytest.mark.parametrize("T,H,W", [(6, 24, 28), (9, 33, 17)])
+@pytest.mark.parametrize("T,H,W", [(6, 24, 28), (9, 33, 17), (40, 16, 20), (24, 20, 13)])
 @pytest.mark.parametrize("k", [1, 5, 30])
 def test_rpca_trajectory_parity(lib, T, H, W, k):
     """Full Algorithm 3 with the paper's gamma = lambda sqrt(max(N, T)).  The
