@@ -43,6 +43,16 @@ using namespace otp;
 
 
 
+// Leave k SMs free of the persistent TMA iteration kernel (one CTA per SM),
+// so that a one-CTA kernel on another stream can run beside it.
+void prox_reserve_sms(ot_prox* h, int k) {
+  int n_sm = 0, dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    n_sm = 152;
+  const int cap = n_sm - k > 1 ? n_sm - k : 1;
+  if (h->tma_grid > cap) h->tma_grid = cap;
+}
+
 extern "C" {
 
 const char* ot_last_error(void) { return g_err.c_str(); }

@@ -46,3 +46,6 @@ struct ot_prox {
   otp::DctPlan* dct;
   int n_id;                  // identity blocks of K: the Laplacian shift c
 };
+
+// Cap the persistent TMA kernel's grid at (SMs - k) CTAs (otprox_api.cu).
+void prox_reserve_sms(ot_prox* h, int k);

@@ -3,9 +3,11 @@
 //
 // One outer iteration, in stream order:
 //   rpca_pre      lines 4-9 fused; builds L + D and the prox centres
-//   gram / eig / apply   line 10: Tm = shrink*_{gamma/rho}(L + D)
-//   ot_prox_step  line 11: n_inner warm-started Algorithm 1 iterations on
-//                 the T-1 frame pairs with weight kappa/rho
+//   gram          line 10, first pass: G = (L + D)^T (L + D)
+//   eig | prox    the one-CTA T x T eigensolver on a side stream, beside
+//                 line 11 (n_inner warm-started Algorithm 1 iterations on
+//                 the T-1 frame pairs with weight kappa/rho) on all other SMs
+//   apply         line 10, second pass: Tn = (L + D) Wm
 //   rpca_post     lines 12-15 and the ADMM residual sums
 // then, on check iterations, one fixed-order FP64 finalize and a 64-byte copy
 // to the host.
@@ -143,6 +145,8 @@ int ot_rpca_create(const ot_rpca_params* params, void* cuda_stream, ot_rpca_t* o
     ot_rpca_destroy(h);
     return rc;
   }
+  // one SM stays free for the one-CTA eigensolver, which runs beside line 11
+  prox_reserve_sms(h->prox, 1);
 
   const size_t plane = (size_t)h->G.plane;
   const size_t nframe = (size_t)p.T * plane, npair = (size_t)(p.T - 1) * plane;
@@ -249,23 +253,25 @@ static int enqueue_outer(ot_rpca* h, bool sums) {
   const long long plane = h->G.plane;
   const long long N = plane;   // rows of the N x T matrix: one frame plane (padding columns are zero)
   OT_CUDA(rpca_launch_pre(h->G, h->C, h->P, h->partials, h->stream), "rpca pre");
-  // fork: line 10 on the side stream
+  // line 10: the Gram pass uses every SM
+  OT_CUDA(svt_launch_gram(h->P.LD, plane, N, h->prm.T, h->gram_partials, h->Gm, h->prox->derr, h->stream), "svt gram");
+  // fork: the one-CTA T x T eigensolver on the side stream, on the SM that
+  // the persistent prox kernel leaves free
   OT_CUDA(cudaEventRecord(h->ev_fork, h->stream), "fork");
   OT_CUDA(cudaStreamWaitEvent(h->side, h->ev_fork, 0), "fork wait");
-  OT_CUDA(svt_launch_gram(h->P.LD, plane, N, h->prm.T, h->gram_partials, h->Gm, h->prox->derr, h->side), "svt gram");
   OT_CUDA(svt_launch_eig(h->Gm, h->prm.T, h->warm, (float)(h->prm.gamma / h->prm.rho), h->prm.svt_max_sweeps, svt_tolerance(h->prm.T),
                          h->V, h->Wm, h->sig, h->sweeps, h->side),
           "svt eig");
   h->warm = 1;
-  OT_CUDA(svt_launch_apply(h->P.LD, plane, N, h->prm.T, h->Wm, h->P.Tn, plane, false, nullptr, h->prox->derr,
-                           h->side),
-          "svt apply");
   OT_CUDA(cudaEventRecord(h->ev_join, h->side), "join");
   // line 11 on the handle's stream, concurrently
   int rc = ot_prox_step(h->prox, h->prm.n_inner);
   if (rc != OT_OK) return rc;
-  // join before lines 12-15
+  // join, then the rest of line 10 and lines 12-15
   OT_CUDA(cudaStreamWaitEvent(h->stream, h->ev_join, 0), "join wait");
+  OT_CUDA(svt_launch_apply(h->P.LD, plane, N, h->prm.T, h->Wm, h->P.Tn, plane, false, nullptr, h->prox->derr,
+                           h->stream),
+          "svt apply");
   OT_CUDA(rpca_launch_post(h->G, h->P, h->partials + (size_t)h->nb_rpca * kNumSums, h->stream), "rpca post");
   if (sums) {
     OT_CUDA(launch_finalize_sums(h->partials, 2 * h->nb_rpca, h->dsums, h->stream), "rpca finalize");

@@ -101,21 +101,35 @@ gram_partial_kernel(const float* __restrict__ X, long long ld, long long N, int 
 }
 
 // G[e] = sum over CTAs of partials[b][e] in FP64, fixed order: a block owns
-// 32 consecutive entries (one per lane); its 8 warps take every 8th partial
-// and are summed in warp order.
-__global__ void __launch_bounds__(256) gram_reduce_kernel(const double* __restrict__ partials, int nparts, int n,
-                                                          double* __restrict__ G) {
-  __shared__ double s[8][32];
+// 32 consecutive entries (one per lane); its 32 warps take every 32nd
+// partial and are summed in warp order.
+constexpr int kRedWarps = 32;
+
+__global__ void __launch_bounds__(32 * kRedWarps) gram_reduce_kernel(const double* __restrict__ partials, int nparts,
+                                                                   int n, double* __restrict__ G) {
+  __shared__ double s[kRedWarps][32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int e = blockIdx.x * 32 + lane;
   double v = 0.0;
-  if (e < n)
-    for (int b = warp; b < nparts; b += 8) v += partials[(size_t)b * n + e];
+  if (e < n) {
+    int b = warp;
+    for (; b + 3 * kRedWarps < nparts; b += 4 * kRedWarps) {   // four loads in flight, summed in order
+      const double x0 = __ldg(partials + (size_t)b * n + e);
+      const double x1 = __ldg(partials + (size_t)(b + kRedWarps) * n + e);
+      const double x2 = __ldg(partials + (size_t)(b + 2 * kRedWarps) * n + e);
+      const double x3 = __ldg(partials + (size_t)(b + 3 * kRedWarps) * n + e);
+      v += x0;
+      v += x1;
+      v += x2;
+      v += x3;
+    }
+    for (; b < nparts; b += kRedWarps) v += __ldg(partials + (size_t)b * n + e);
+  }
   s[warp][lane] = v;
   __syncthreads();
   if (warp == 0 && e < n) {
     double t = 0.0;
-    for (int w = 0; w < 8; ++w) t += s[w][lane];
+    for (int w = 0; w < kRedWarps; ++w) t += s[w][lane];
     G[e] = t;
   }
 }
@@ -498,10 +512,25 @@ jacobi_reg_kernel(const double* __restrict__ G, int warm, float theta, int max_s
   (void)pQ;
 
   float* A = sm;
-  for (int e = tid; e < TP * TP; e += kJregThreads) {
-    const int i = e / TP, j = e % TP;
-    A[i * LDA + j] = (float)G[e];
-    V[i * LDA + j] = warm ? V_io[e] : (i == j ? 1.f : 0.f);
+  {   // all global loads first, so that they are in flight together
+    constexpr int NL = (TP * TP + kJregThreads - 1) / kJregThreads;
+    double g[NL];
+    float v[NL];
+#pragma unroll
+    for (int u = 0; u < NL; ++u) {
+      const int e = tid + u * kJregThreads;
+      g[u] = e < TP * TP ? __ldg(G + e) : 0.0;
+      v[u] = (e < TP * TP && warm) ? V_io[e] : 0.f;
+    }
+#pragma unroll
+    for (int u = 0; u < NL; ++u) {
+      const int e = tid + u * kJregThreads;
+      if (e < TP * TP) {
+        const int i = e / TP, j = e % TP;
+        A[i * LDA + j] = (float)g[u];
+        V[i * LDA + j] = warm ? v[u] : (i == j ? 1.f : 0.f);
+      }
+    }
   }
   __syncthreads();
   if (warm) {   // A <- V^T G V
@@ -878,7 +907,7 @@ cudaError_t svt_launch_gram(const float* X, long long ld, long long N, int T, do
   if (err && TP >= 32 && (ld * 4) % 16 == 0 && (reinterpret_cast<uintptr_t>(X) & 15) == 0) {
     cudaError_t e = svt_launch_gram_tc(X, ld, N, T, partials, err, st);
     if (e != cudaSuccess) return e;
-    gram_reduce_kernel<<<(n + 31) / 32, 256, 0, st>>>(partials, svt_gram_tc_blocks(N), n, G);
+    gram_reduce_kernel<<<(n + 31) / 32, 32 * kRedWarps, 0, st>>>(partials, svt_gram_tc_blocks(N), n, G);
     return cudaGetLastError();
   }
   const int nb = gram_simt_blocks(N);
@@ -890,7 +919,7 @@ cudaError_t svt_launch_gram(const float* X, long long ld, long long N, int T, do
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  gram_reduce_kernel<<<(n + 31) / 32, 256, 0, st>>>(partials, nb, n, G);
+  gram_reduce_kernel<<<(n + 31) / 32, 32 * kRedWarps, 0, st>>>(partials, nb, n, G);
   return cudaGetLastError();
 }
 

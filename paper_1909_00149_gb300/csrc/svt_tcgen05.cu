@@ -12,7 +12,7 @@
 // range in chunks of 64 pixels:
 //   warp 0 (one lane): TMA loads of the FP32 chunk [TP rows][64] into a ring
 //                      of stages,
-//   warps 2-5:         split each chunk into the three BF16 pieces, written
+//   warps 2-9:         split each chunk into the three BF16 pieces, written
 //                      K-major with the 128-byte swizzle the MMA expects,
 //   warp 1 (one lane): issues the MMAs into one FP32 accumulator in tensor
 //                      memory (128 lanes x TP columns),
@@ -36,7 +36,8 @@ namespace {
 using namespace tc;
 
 constexpr int kGK = 64;                  // pixels per chunk: 64 bf16 = one 128-byte swizzled row
-constexpr int kGThreads = 192;
+constexpr int kSplitWarps = 8;           // splitter warps (two per SM sub-partition, to hide latency)
+constexpr int kGThreads = 64 + 32 * kSplitWarps;
 constexpr int kPieceBytes = 128 * 128;   // one BF16 piece, 128 rows (TMEM lanes) x 128 bytes
 constexpr int kSetBytes = 3 * kPieceBytes;
 
@@ -73,10 +74,10 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap xmap, int T, int nchunks, dou
   if (tid == 0) {
     for (int s = 0; s < NS; ++s) {
       bar_init(s_u32(&full[s]), 1);
-      bar_init(s_u32(&freef[s]), 4);
+      bar_init(s_u32(&freef[s]), kSplitWarps);
     }
     for (int b = 0; b < 2; ++b) {
-      bar_init(s_u32(&conv[b]), 4);
+      bar_init(s_u32(&conv[b]), kSplitWarps);
       bar_init(s_u32(&freeb[b]), 1);
     }
     bar_init(s_u32(&done), 1);
@@ -127,7 +128,7 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap xmap, int T, int nchunks, dou
       if (!ok) (void)bar_wait(s_u32(&done), 0);
     }
   } else {
-    // splitters: 128 threads, a task is one row and one 8-pixel group of the chunk
+    // splitters: a task is one row and one 8-pixel group of the chunk
     const int q0 = tid - 64;
     for (int c = 0; c < nc && ok; ++c) {
       const int s = c % NS, b = c & 1;
@@ -136,8 +137,8 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap xmap, int T, int nchunks, dou
       const float* src = reinterpret_cast<const float*>(stages + (size_t)s * SB);
       unsigned char* dst = sets + (size_t)b * kSetBytes;
 #pragma unroll
-      for (int i = 0; i < TP * 8 / 128; ++i) {
-        const int q = q0 + 128 * i;
+      for (int i = 0; i < TP * 8 / (32 * kSplitWarps); ++i) {
+        const int q = q0 + 32 * kSplitWarps * i;
         const int row = q >> 3, g = q & 7;
         const float4 u0 = *reinterpret_cast<const float4*>(src + row * kGK + g * 8);
         const float4 u1 = *reinterpret_cast<const float4*>(src + row * kGK + g * 8 + 4);
@@ -165,10 +166,10 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap xmap, int T, int nchunks, dou
         bar_arrive(s_u32(&freef[s]));
       }
     }
-    // epilogue: warp w reads TMEM lanes 32 (w % 4) ... (tile rows t)
+    // epilogue (warps 2-5): warp w reads TMEM lanes 32 (w % 4) ... (tile rows t)
     const bool fin = ok && bar_wait(s_u32(&done), 0);
     const int quad = warp & 3;
-    if (fin && 32 * quad < TP) {
+    if (fin && warp < 6 && 32 * quad < TP) {
       fence_after_sync();
       const int t = 32 * quad + lane;
       double* out = partials + (size_t)blockIdx.x * TP * TP + (size_t)t * TP;
@@ -218,14 +219,15 @@ cudaError_t launch_gram_tc(const CUtensorMap& m, int T, int nchunks, int grid, d
 // per CTA.  The six products of the Gram give FP32 accuracy.  Per CTA, over
 // its pixel tiles (persistent):
 //   warp 0 (one lane): TMA loads of X tiles [TP frames][128 pixels],
-//   warps 2-5:         transpose + split into the BF16 pieces of B,
+//   warps 2-9:         transpose + split into the BF16 pieces of B,
 //   warp 1 (one lane): 24 MMAs per tile into one of two TMEM accumulators
 //                      (128 lanes x 128 columns each),
-//   warps 6-9:         read the accumulator and store the rows t < T of Y,
+//   warps 10-13:       read the accumulator and store the rows t < T of Y,
 //                      transposed through shared memory so that each store
 //                      instruction writes 128 contiguous bytes of one row.
 constexpr int kAN = 128;                     // pixels per tile (MMA N)
-constexpr int kAThreads = 320;
+constexpr int kAEpi = 2 + kSplitWarps;        // first epilogue warp
+constexpr int kAThreads = 32 * (kAEpi + 4);
 constexpr int kAStages = 2;
 constexpr int kABPiece = kAN * 128;          // one BF16 piece of B: 128 pixel rows x 64 frames
 constexpr int kABSet = 3 * kABPiece;
@@ -267,15 +269,15 @@ apply_tc_kernel(const __grid_constant__ CUtensorMap xmap, const float* __restric
   if (tid == 0) {
     for (int s = 0; s < kAStages; ++s) {
       bar_init(s_u32(&full[s]), 1);
-      bar_init(s_u32(&freef[s]), 4);
+      bar_init(s_u32(&freef[s]), kSplitWarps);
     }
     for (int b = 0; b < 2; ++b) {
-      bar_init(s_u32(&conv[b]), 4);
+      bar_init(s_u32(&conv[b]), kSplitWarps);
       bar_init(s_u32(&freeb[b]), 1);
       bar_init(s_u32(&tfull[b]), 1);
       bar_init(s_u32(&tfree[b]), 4);
     }
-    bar_init(s_u32(&aready), 4);
+    bar_init(s_u32(&aready), kSplitWarps);
     bar_init(s_u32(&drain), 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -335,11 +337,12 @@ apply_tc_kernel(const __grid_constant__ CUtensorMap xmap, const float* __restric
         (void)bar_wait(s_u32(&drain), 0);
       }
     }
-  } else if (warp < 6) {
-    // splitters (128 threads): thread q owns pixel row q of B
+  } else if (warp < kAEpi) {
+    // splitters: thread q owns pixel row q % 128 of B and half of its frame groups
     const int q = tid - 64;
+    const int px = q & (kAN - 1), half = q >> 7;
     // A = Wm (symmetric), once: rows t < TP, frames s < TP, groups of 8 frames
-    for (int task = q; task < TP * (TP / 8); task += 128) {
+    for (int task = q; task < TP * (TP / 8); task += 32 * kSplitWarps) {
       const int row = task / (TP / 8), g = task % (TP / 8);
       float h[8], m[8], l[8];
 #pragma unroll
@@ -362,11 +365,12 @@ apply_tc_kernel(const __grid_constant__ CUtensorMap xmap, const float* __restric
       const float* src = reinterpret_cast<const float*>(stages + (size_t)s * SB);
       unsigned char* dst = bsets + (size_t)b * kABSet;
 #pragma unroll
-      for (int g = 0; g < TP / 8; ++g) {
+      for (int gg = 0; gg < TP / 16; ++gg) {
+        const int g = 2 * gg + half;
         float h[8], m[8], l[8];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) split3(src[(g * 8 + j) * kAN + q], h[j], m[j], l[j]);
-        const uint32_t off = (uint32_t)q * 128 + (uint32_t)((g ^ (q & 7)) << 4);
+        for (int j = 0; j < 8; ++j) split3(src[(g * 8 + j) * kAN + px], h[j], m[j], l[j]);
+        const uint32_t off = (uint32_t)px * 128 + (uint32_t)((g ^ (px & 7)) << 4);
         *reinterpret_cast<uint4*>(dst + off) =
             make_uint4(pack_bf16(h[0], h[1]), pack_bf16(h[2], h[3]), pack_bf16(h[4], h[5]), pack_bf16(h[6], h[7]));
         *reinterpret_cast<uint4*>(dst + kABPiece + off) =
@@ -382,7 +386,7 @@ apply_tc_kernel(const __grid_constant__ CUtensorMap xmap, const float* __restric
       }
     }
   } else {
-    // epilogue (warps 6-9): warp w reads TMEM lanes 32 (w % 4) ... = rows t
+    // epilogue (warps 10-13): warp w reads TMEM lanes 32 (w % 4) ... = rows t
     const int quad = warp & 3;
     const bool live = 32 * quad < TP;         // warp-uniform
     float* my = stg + (live ? quad : 0) * kAStg;
