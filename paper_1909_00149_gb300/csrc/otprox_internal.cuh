@@ -176,7 +176,7 @@ cudaError_t svt_launch_gram(const float* X, long long ld, long long N, int T, do
                             cudaStream_t st);
 // tensor-core partial Grams (gram_tcgen05.cu); T > 16
 int svt_gram_tc_blocks(long long N);
-cudaError_t svt_launch_gram_tc(const float* X, long long ld, long long N, int T, double* partials, int* err,
+cudaError_t svt_launch_gram_tc(const float* X, long long ld, long long N, int T, float* partials, int* err,
                                cudaStream_t st);
 cudaError_t svt_launch_eig(const double* G, int T, int warm, float theta, int max_sweeps, float tol, float* V_io,
                            float* Wm, float* sig, int* sweeps, cudaStream_t st);

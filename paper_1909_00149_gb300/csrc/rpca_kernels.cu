@@ -89,14 +89,22 @@ rpca_post_kernel(const RpcaGeom g, const RpcaPlanes P, double* __restrict__ part
   float acc[kNumSums] = {};
   const long long per_frame = g.plane / 4;
   const long long total = per_frame * g.T;
+  const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
   for (long long q = blockIdx.x * (long long)kRpcaThreads + threadIdx.x; q < total;
        q += (long long)gridDim.x * kRpcaThreads) {
     const int t = (int)(q / per_frame);
     const long long o = 4 * q;
     const long long op = o - (long long)t * g.plane;
     const bool hz = t < g.T - 1, hw = t > 0;
+    const long long oz = (long long)t * g.plane + op;         // pair t: z_t pairs with s_t
+    const long long ow = (long long)(t - 1) * g.plane + op;   // pair t-1: w_{t} pairs with s_t
+    // every load before any store (the planes are not marked restrict)
     const float4 x = ldg4(P.X + o), s = ldg4(P.S + o), l = ldg4(P.L + o), tn = ldg4(P.Tn + o), tm = ldg4(P.Tm + o);
     float4 a = ldg4(P.A + o), d = ldg4(P.D + o);
+    const float4 z = hz ? ldg4(P.z + oz) : z4, zp = hz ? ldg4(P.zprev + oz) : z4;
+    float4 b = hz ? ldg4(P.Bz + oz) : z4;
+    const float4 w = hw ? ldg4(P.w + ow) : z4, wp = hw ? ldg4(P.wprev + ow) : z4;
+    float4 cc = hw ? ldg4(P.Cw + ow) : z4;
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
       const float r1 = f4c(x, e) - f4c(s, e) - f4c(l, e);
@@ -107,37 +115,23 @@ rpca_post_kernel(const RpcaGeom g, const RpcaPlanes P, double* __restrict__ part
       acc[1] = fmaf(dt, dt, acc[1]);
       acc[2] = fmaf(r1, r1, acc[2]);
       acc[3] = fmaf(r2, r2, acc[3]);
+      const float rz = f4c(z, e) - f4c(s, e), dz = f4c(z, e) - f4c(zp, e);
+      const float rw = f4c(w, e) - f4c(s, e), dw = f4c(w, e) - f4c(wp, e);
+      f4(b, e) += rz;
+      f4(cc, e) += rw;
+      if (hz) {
+        acc[4] = fmaf(rz, rz, acc[4]);
+        acc[6] = fmaf(dz, dz, acc[6]);
+      }
+      if (hw) {
+        acc[5] = fmaf(rw, rw, acc[5]);
+        acc[7] = fmaf(dw, dw, acc[7]);
+      }
     }
     stg4v(P.A + o, a);
     stg4v(P.D + o, d);
-    if (hz) {   // pair t: z_t pairs with s_t
-      const long long oz = (long long)t * g.plane + op;
-      const float4 z = ldg4(P.z + oz), zp = ldg4(P.zprev + oz);
-      float4 b = ldg4(P.Bz + oz);
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const float r = f4c(z, e) - f4c(s, e);
-        const float dz = f4c(z, e) - f4c(zp, e);
-        f4(b, e) += r;
-        acc[4] = fmaf(r, r, acc[4]);
-        acc[6] = fmaf(dz, dz, acc[6]);
-      }
-      stg4v(P.Bz + oz, b);
-    }
-    if (hw) {   // pair t-1: w_{t} pairs with s_t
-      const long long ow = (long long)(t - 1) * g.plane + op;
-      const float4 w = ldg4(P.w + ow), wp = ldg4(P.wprev + ow);
-      float4 cc = ldg4(P.Cw + ow);
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const float r = f4c(w, e) - f4c(s, e);
-        const float dw = f4c(w, e) - f4c(wp, e);
-        f4(cc, e) += r;
-        acc[5] = fmaf(r, r, acc[5]);
-        acc[7] = fmaf(dw, dw, acc[7]);
-      }
-      stg4v(P.Cw + ow, cc);
-    }
+    if (hz) stg4v(P.Bz + oz, b);
+    if (hw) stg4v(P.Cw + ow, cc);
   }
   block_sums_to<kRpcaThreads>(acc, partials + (size_t)blockIdx.x * kNumSums);
 }

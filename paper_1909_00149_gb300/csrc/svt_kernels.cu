@@ -105,7 +105,8 @@ gram_partial_kernel(const float* __restrict__ X, long long ld, long long N, int 
 // partial and are summed in warp order.
 constexpr int kRedWarps = 32;
 
-__global__ void __launch_bounds__(32 * kRedWarps) gram_reduce_kernel(const double* __restrict__ partials, int nparts,
+template <typename P>
+__global__ void __launch_bounds__(32 * kRedWarps) gram_reduce_kernel(const P* __restrict__ partials, int nparts,
                                                                    int n, double* __restrict__ G) {
   __shared__ double s[kRedWarps][32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -114,16 +115,16 @@ __global__ void __launch_bounds__(32 * kRedWarps) gram_reduce_kernel(const doubl
   if (e < n) {
     int b = warp;
     for (; b + 3 * kRedWarps < nparts; b += 4 * kRedWarps) {   // four loads in flight, summed in order
-      const double x0 = __ldg(partials + (size_t)b * n + e);
-      const double x1 = __ldg(partials + (size_t)(b + kRedWarps) * n + e);
-      const double x2 = __ldg(partials + (size_t)(b + 2 * kRedWarps) * n + e);
-      const double x3 = __ldg(partials + (size_t)(b + 3 * kRedWarps) * n + e);
+      const double x0 = (double)__ldg(partials + (size_t)b * n + e);
+      const double x1 = (double)__ldg(partials + (size_t)(b + kRedWarps) * n + e);
+      const double x2 = (double)__ldg(partials + (size_t)(b + 2 * kRedWarps) * n + e);
+      const double x3 = (double)__ldg(partials + (size_t)(b + 3 * kRedWarps) * n + e);
       v += x0;
       v += x1;
       v += x2;
       v += x3;
     }
-    for (; b < nparts; b += kRedWarps) v += __ldg(partials + (size_t)b * n + e);
+    for (; b < nparts; b += kRedWarps) v += (double)__ldg(partials + (size_t)b * n + e);
   }
   s[warp][lane] = v;
   __syncthreads();
@@ -905,9 +906,10 @@ cudaError_t svt_launch_gram(const float* X, long long ld, long long N, int T, do
   const int TP = svt_padded_T(T);
   const int n = TP * TP;
   if (err && TP >= 32 && (ld * 4) % 16 == 0 && (reinterpret_cast<uintptr_t>(X) & 15) == 0) {
-    cudaError_t e = svt_launch_gram_tc(X, ld, N, T, partials, err, st);
+    float* fpart = reinterpret_cast<float*>(partials);   // FP32 partials in the same buffer
+    cudaError_t e = svt_launch_gram_tc(X, ld, N, T, fpart, err, st);
     if (e != cudaSuccess) return e;
-    gram_reduce_kernel<<<(n + 31) / 32, 32 * kRedWarps, 0, st>>>(partials, svt_gram_tc_blocks(N), n, G);
+    gram_reduce_kernel<float><<<(n + 31) / 32, 32 * kRedWarps, 0, st>>>(fpart, svt_gram_tc_blocks(N), n, G);
     return cudaGetLastError();
   }
   const int nb = gram_simt_blocks(N);
@@ -919,7 +921,7 @@ cudaError_t svt_launch_gram(const float* X, long long ld, long long N, int T, do
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  gram_reduce_kernel<<<(n + 31) / 32, 32 * kRedWarps, 0, st>>>(partials, nb, n, G);
+  gram_reduce_kernel<double><<<(n + 31) / 32, 32 * kRedWarps, 0, st>>>(partials, nb, n, G);
   return cudaGetLastError();
 }
 
@@ -944,7 +946,8 @@ cudaError_t svt_launch_apply(const float* X, long long ld, long long N, int T, c
   const int TP = svt_padded_T(T);
   int gy = 1;
   const int nb = svt_apply_blocks(N, T, &gy);
-  if (err && !reduce && (TP == 32 || TP == 64) && ld % 4 == 0 && (reinterpret_cast<uintptr_t>(X) & 15) == 0)
+  if (err && !reduce && (TP == 32 || TP == 64) && ld % 4 == 0 && ldy % 4 == 0 &&
+      (reinterpret_cast<uintptr_t>(X) & 15) == 0 && (reinterpret_cast<uintptr_t>(Y) & 15) == 0)
     return svt_launch_apply_tc(X, ld, N, T, Wm, Y, ldy, err, st);
   const dim3 grid(nb, gy);
   const int vec = ((ld % 4) == 0 && (ldy % 4) == 0 && (reinterpret_cast<uintptr_t>(X) % 16) == 0 &&

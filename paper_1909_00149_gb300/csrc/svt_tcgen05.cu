@@ -48,14 +48,40 @@ constexpr uint32_t gram_stage_bytes() { return (uint32_t)TP * kGK * 4; }
 template <int TP>
 constexpr size_t gram_tc_smem() { return 1024 + 2 * (size_t)kSetBytes + (size_t)gram_stages<TP>() * gram_stage_bytes<TP>(); }
 
-__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
-  const __nv_bfloat162 v = __floats2bfloat162_rn(a, b);   // .x = a (low half), .y = b
-  return *reinterpret_cast<const uint32_t*>(&v);
+
+// Exact 3-piece BF16 split of 8 values, two at a time (cvt.rn.bf16x2.f32):
+// x = h + m + l with h = bf16(x), m = bf16(x - h), l = bf16(x - h - m).
+__device__ __forceinline__ uint32_t bf2_bits(__nv_bfloat162 v) { return *reinterpret_cast<const uint32_t*>(&v); }
+__device__ __forceinline__ void split8(const float (&x)[8], uint4& H, uint4& M, uint4& L) {
+  uint32_t h[4], m[4], l[4];
+#pragma unroll
+  for (int p = 0; p < 4; ++p) {
+    const float2 v = make_float2(x[2 * p], x[2 * p + 1]);
+    const __nv_bfloat162 hb = __float22bfloat162_rn(v);
+    const float2 hf = __bfloat1622float2(hb);
+    const float2 r = make_float2(v.x - hf.x, v.y - hf.y);
+    const __nv_bfloat162 mb = __float22bfloat162_rn(r);
+    const float2 mf = __bfloat1622float2(mb);
+    const __nv_bfloat162 lb = __float22bfloat162_rn(make_float2(r.x - mf.x, r.y - mf.y));
+    h[p] = bf2_bits(hb);
+    m[p] = bf2_bits(mb);
+    l[p] = bf2_bits(lb);
+  }
+  H = make_uint4(h[0], h[1], h[2], h[3]);
+  M = make_uint4(m[0], m[1], m[2], m[3]);
+  L = make_uint4(l[0], l[1], l[2], l[3]);
+}
+
+__device__ __forceinline__ void bulk_store(void* gdst, uint32_t ssrc, uint32_t bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(gdst), "r"(ssrc), "r"(bytes)
+               : "memory");
+  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+  asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
 }
 
 template <int TP>
 __global__ void __launch_bounds__(kGThreads, 1)
-gram_tc_kernel(const __grid_constant__ CUtensorMap xmap, int T, int nchunks, double* __restrict__ partials,
+gram_tc_kernel(const __grid_constant__ CUtensorMap xmap, int T, int nchunks, float* __restrict__ partials,
                int* __restrict__ err) {
   constexpr int NS = gram_stages<TP>();
   constexpr uint32_t SB = gram_stage_bytes<TP>();
@@ -143,21 +169,12 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap xmap, int T, int nchunks, dou
         const float4 u0 = *reinterpret_cast<const float4*>(src + row * kGK + g * 8);
         const float4 u1 = *reinterpret_cast<const float4*>(src + row * kGK + g * 8 + 4);
         const float x[8] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w};
-        float h[8], m[8], l[8];
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          h[j] = __bfloat162float(__float2bfloat16_rn(x[j]));
-          const float r1 = x[j] - h[j];
-          m[j] = __bfloat162float(__float2bfloat16_rn(r1));
-          l[j] = r1 - m[j];
-        }
+        uint4 H, M, L;
+        split8(x, H, M, L);
         const uint32_t off = (uint32_t)row * 128 + (uint32_t)((g ^ (row & 7)) << 4);
-        *reinterpret_cast<uint4*>(dst + off) =
-            make_uint4(pack_bf16(h[0], h[1]), pack_bf16(h[2], h[3]), pack_bf16(h[4], h[5]), pack_bf16(h[6], h[7]));
-        *reinterpret_cast<uint4*>(dst + kPieceBytes + off) =
-            make_uint4(pack_bf16(m[0], m[1]), pack_bf16(m[2], m[3]), pack_bf16(m[4], m[5]), pack_bf16(m[6], m[7]));
-        *reinterpret_cast<uint4*>(dst + 2 * kPieceBytes + off) =
-            make_uint4(pack_bf16(l[0], l[1]), pack_bf16(l[2], l[3]), pack_bf16(l[4], l[5]), pack_bf16(l[6], l[7]));
+        *reinterpret_cast<uint4*>(dst + off) = H;
+        *reinterpret_cast<uint4*>(dst + kPieceBytes + off) = M;
+        *reinterpret_cast<uint4*>(dst + 2 * kPieceBytes + off) = L;
       }
       fence_async_shared();
       __syncwarp();
@@ -166,23 +183,30 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap xmap, int T, int nchunks, dou
         bar_arrive(s_u32(&freef[s]));
       }
     }
-    // epilogue (warps 2-5): warp w reads TMEM lanes 32 (w % 4) ... (tile rows t)
+    // epilogue (warps 2-5): warp w reads TMEM lanes 32 (w % 4) ... (rows t).
+    // The partial is symmetric, so thread t writes its row as column t of a
+    // shared-memory tile (conflict-free), and one bulk copy stores the tile.
     const bool fin = ok && bar_wait(s_u32(&done), 0);
     const int quad = warp & 3;
-    if (fin && warp < 6 && 32 * quad < TP) {
-      fence_after_sync();
-      const int t = 32 * quad + lane;
-      double* out = partials + (size_t)blockIdx.x * TP * TP + (size_t)t * TP;
+    float* tile = reinterpret_cast<float*>(stages);            // the FP32 ring is idle now
+    if (warp < 6) {
+      if (fin && 32 * quad < TP) {
+        fence_after_sync();
+        const int t = 32 * quad + lane;
 #pragma unroll 1
-      for (int cc = 0; cc < TP / 32; ++cc) {
-        float v[32];
-        tmem_ld32(tmem + ((uint32_t)(32 * quad) << 16) + (uint32_t)(32 * cc), v);
+        for (int cc = 0; cc < TP / 32; ++cc) {
+          float v[32];
+          tmem_ld32(tmem + ((uint32_t)(32 * quad) << 16) + (uint32_t)(32 * cc), v);
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          const int sidx = 32 * cc + j;
-          out[sidx] = (t < T && sidx < T) ? (double)v[j] : 0.0;
+          for (int j = 0; j < 32; ++j) {
+            const int sidx = 32 * cc + j;
+            tile[sidx * TP + t] = (t < T && sidx < T) ? v[j] : 0.f;
+          }
         }
       }
+      fence_async_shared();
+      asm volatile("bar.sync 1, 128;" ::: "memory");          // warps 2-5 only
+      if (fin && tid == 64) bulk_store(partials + (size_t)blockIdx.x * TP * TP, s_u32(tile), TP * TP * 4);
     }
     if (!fin) ok = false;
   }
@@ -196,7 +220,7 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap xmap, int T, int nchunks, dou
 }
 
 template <int TP>
-cudaError_t launch_gram_tc(const CUtensorMap& m, int T, int nchunks, int grid, double* partials, int* err,
+cudaError_t launch_gram_tc(const CUtensorMap& m, int T, int nchunks, int grid, float* partials, int* err,
                            cudaStream_t st) {
   static bool attr = false;
   if (!attr) {
@@ -222,9 +246,11 @@ cudaError_t launch_gram_tc(const CUtensorMap& m, int T, int nchunks, int grid, d
 //   warps 2-9:         transpose + split into the BF16 pieces of B,
 //   warp 1 (one lane): 24 MMAs per tile into one of two TMEM accumulators
 //                      (128 lanes x 128 columns each),
-//   warps 10-13:       read the accumulator and store the rows t < T of Y,
-//                      transposed through shared memory so that each store
-//                      instruction writes 128 contiguous bytes of one row.
+//   warps 10-13:       read the accumulator; each warp holding rows t < TP
+//                      writes 32 x 32 blocks into a 128-byte-swizzled,
+//                      double-buffered staging box that one lane stores
+//                      with a TMA tile store (rows t >= T and pixels >= N
+//                      fall outside the map and are not written).
 constexpr int kAN = 128;                     // pixels per tile (MMA N)
 constexpr int kAEpi = 2 + kSplitWarps;        // first epilogue warp
 constexpr int kAThreads = 32 * (kAEpi + 4);
@@ -234,24 +260,18 @@ constexpr int kABSet = 3 * kABPiece;
 constexpr int kAAPiece = 128 * 128;          // one BF16 piece of A: 128 rows x 64 frames
 template <int TP>
 constexpr uint32_t apply_stage_bytes() { return (uint32_t)TP * kAN * 4; }
-constexpr int kAStg = 32 * 33;               // epilogue staging per TMEM-reading warp (floats)
+constexpr int kAStgBytes = 32 * 32 * 4;       // one staging box: 32 rows x 32 pixels, FP32
 template <int TP>
 constexpr size_t apply_tc_smem() {
   return 1024 + 3 * (size_t)kAAPiece + 2 * (size_t)kABSet + (size_t)kAStages * apply_stage_bytes<TP>() +
-         (size_t)(TP / 32) * kAStg * 4;
+         (size_t)(TP / 32) * 2 * kAStgBytes;
 }
 
-__device__ __forceinline__ void split3(float x, float& h, float& m, float& l) {
-  h = __bfloat162float(__float2bfloat16_rn(x));
-  const float r1 = x - h;
-  m = __bfloat162float(__float2bfloat16_rn(r1));
-  l = r1 - m;
-}
 
 template <int TP>
 __global__ void __launch_bounds__(kAThreads, 1)
-apply_tc_kernel(const __grid_constant__ CUtensorMap xmap, const float* __restrict__ Wm, int T, long long N,
-                float* __restrict__ Y, long long ldy, int ntiles, int* __restrict__ err) {
+apply_tc_kernel(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ CUtensorMap ymap,
+                const float* __restrict__ Wm, int T, long long N, int ntiles, int* __restrict__ err) {
   constexpr uint32_t SB = apply_stage_bytes<TP>();
   constexpr uint32_t IDESC = bf16_idesc(128, kAN);
   extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -259,7 +279,7 @@ apply_tc_kernel(const __grid_constant__ CUtensorMap xmap, const float* __restric
   unsigned char* apieces = smem;                              // [H | M | L] of Wm
   unsigned char* bsets = smem + 3 * kAAPiece;                 // 2 x [H | M | L] of X^T
   unsigned char* stages = bsets + 2 * kABSet;                 // kAStages x FP32 [TP][128]
-  float* stg = reinterpret_cast<float*>(stages + (size_t)kAStages * SB);   // [TP / 32][32][33]
+  unsigned char* stg = stages + (size_t)kAStages * SB;        // [TP / 32][2] staging boxes
   __shared__ __align__(8) uint64_t full[kAStages], freef[kAStages], conv[2], freeb[2], tfull[2], tfree[2], aready,
       drain;
   __shared__ uint32_t s_tmem;
@@ -346,14 +366,15 @@ apply_tc_kernel(const __grid_constant__ CUtensorMap xmap, const float* __restric
       const int row = task / (TP / 8), g = task % (TP / 8);
       float h[8], m[8], l[8];
 #pragma unroll
-      for (int j = 0; j < 8; ++j) split3(__ldg(Wm + (size_t)row * TP + g * 8 + j), h[j], m[j], l[j]);
+      float x[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) x[j] = __ldg(Wm + (size_t)row * TP + g * 8 + j);
+      uint4 H, M, L;
+      split8(x, H, M, L);
       const uint32_t off = (uint32_t)row * 128 + (uint32_t)((g ^ (row & 7)) << 4);
-      *reinterpret_cast<uint4*>(apieces + off) =
-          make_uint4(pack_bf16(h[0], h[1]), pack_bf16(h[2], h[3]), pack_bf16(h[4], h[5]), pack_bf16(h[6], h[7]));
-      *reinterpret_cast<uint4*>(apieces + kAAPiece + off) =
-          make_uint4(pack_bf16(m[0], m[1]), pack_bf16(m[2], m[3]), pack_bf16(m[4], m[5]), pack_bf16(m[6], m[7]));
-      *reinterpret_cast<uint4*>(apieces + 2 * kAAPiece + off) =
-          make_uint4(pack_bf16(l[0], l[1]), pack_bf16(l[2], l[3]), pack_bf16(l[4], l[5]), pack_bf16(l[6], l[7]));
+      *reinterpret_cast<uint4*>(apieces + off) = H;
+      *reinterpret_cast<uint4*>(apieces + kAAPiece + off) = M;
+      *reinterpret_cast<uint4*>(apieces + 2 * kAAPiece + off) = L;
     }
     fence_async_shared();
     __syncwarp();
@@ -367,16 +388,15 @@ apply_tc_kernel(const __grid_constant__ CUtensorMap xmap, const float* __restric
 #pragma unroll
       for (int gg = 0; gg < TP / 16; ++gg) {
         const int g = 2 * gg + half;
-        float h[8], m[8], l[8];
+        float x[8];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) split3(src[(g * 8 + j) * kAN + px], h[j], m[j], l[j]);
+        for (int j = 0; j < 8; ++j) x[j] = src[(g * 8 + j) * kAN + px];
+        uint4 H, M, L;
+        split8(x, H, M, L);
         const uint32_t off = (uint32_t)px * 128 + (uint32_t)((g ^ (px & 7)) << 4);
-        *reinterpret_cast<uint4*>(dst + off) =
-            make_uint4(pack_bf16(h[0], h[1]), pack_bf16(h[2], h[3]), pack_bf16(h[4], h[5]), pack_bf16(h[6], h[7]));
-        *reinterpret_cast<uint4*>(dst + kABPiece + off) =
-            make_uint4(pack_bf16(m[0], m[1]), pack_bf16(m[2], m[3]), pack_bf16(m[4], m[5]), pack_bf16(m[6], m[7]));
-        *reinterpret_cast<uint4*>(dst + 2 * kABPiece + off) =
-            make_uint4(pack_bf16(l[0], l[1]), pack_bf16(l[2], l[3]), pack_bf16(l[4], l[5]), pack_bf16(l[6], l[7]));
+        *reinterpret_cast<uint4*>(dst + off) = H;
+        *reinterpret_cast<uint4*>(dst + kABPiece + off) = M;
+        *reinterpret_cast<uint4*>(dst + 2 * kABPiece + off) = L;
       }
       fence_async_shared();
       __syncwarp();
@@ -389,33 +409,40 @@ apply_tc_kernel(const __grid_constant__ CUtensorMap xmap, const float* __restric
     // epilogue (warps 10-13): warp w reads TMEM lanes 32 (w % 4) ... = rows t
     const int quad = warp & 3;
     const bool live = 32 * quad < TP;         // warp-uniform
-    float* my = stg + (live ? quad : 0) * kAStg;
+    unsigned char* my = stg + (size_t)(live ? quad : 0) * 2 * kAStgBytes;
+    int buf = 0;
     for (int i = 0; i < nmine && ok; ++i) {
       const int b = i & 1;
       if (!bar_wait(s_u32(&tfull[b]), (uint32_t)((i >> 1) & 1))) { ok = false; break; }
       fence_after_sync();
       if (live) {
-        const long long n0 = (long long)((int)blockIdx.x + i * (int)gridDim.x) * kAN;
+        const int n0 = ((int)blockIdx.x + i * (int)gridDim.x) * kAN;
 #pragma unroll 1
         for (int cc = 0; cc < kAN / 32; ++cc) {
           float v[32];
           tmem_ld32(tmem + ((uint32_t)(32 * quad) << 16) + (uint32_t)(b * kAN + 32 * cc), v);
+          unsigned char* box = my + buf * kAStgBytes;
+          if (lane == 0) bulk_wait_read<1>();   // the store that last used this box has read it
+          __syncwarp();
 #pragma unroll
-          for (int j = 0; j < 32; ++j) my[lane * 33 + j] = v[j];   // row lane, column j
+          for (int c4 = 0; c4 < 8; ++c4)        // row lane, 16-byte chunk c4, 128-byte swizzle
+            *reinterpret_cast<float4*>(box + lane * 128 + ((c4 ^ (lane & 7)) << 4)) =
+                make_float4(v[4 * c4], v[4 * c4 + 1], v[4 * c4 + 2], v[4 * c4 + 3]);
+          fence_async_shared();
           __syncwarp();
-          const long long n = n0 + 32 * cc + lane;
-#pragma unroll 4
-          for (int r = 0; r < 32; ++r) {
-            const int t = 32 * quad + r;
-            if (t < T && n < N) Y[(long long)t * ldy + n] = my[r * 33 + lane];
+          // a box entirely beyond the last pixel is not stored (stores start in range)
+          if (lane == 0 && n0 + 32 * cc < N && 32 * quad < T) {
+            tma_store2d(&ymap, s_u32(box), n0 + 32 * cc, 32 * quad);
+            bulk_commit();
           }
-          __syncwarp();
+          buf ^= 1;
         }
       }
       fence_before_sync();
       __syncwarp();
       if (lane == 0) bar_arrive(s_u32(&tfree[b]));
     }
+    if (live && lane == 0) bulk_wait_all();   // the stores complete before the CTA exits
   }
   if (!ok) atomicExch(err, 1);
   fence_before_sync();
@@ -427,7 +454,7 @@ apply_tc_kernel(const __grid_constant__ CUtensorMap xmap, const float* __restric
 }
 
 template <int TP>
-cudaError_t launch_apply_tc(const CUtensorMap& m, const float* Wm, int T, long long N, float* Y, long long ldy,
+cudaError_t launch_apply_tc(const CUtensorMap& xm, const CUtensorMap& ym, const float* Wm, int T, long long N,
                             int ntiles, int grid, int* err, cudaStream_t st) {
   static bool attr = false;
   if (!attr) {
@@ -436,11 +463,12 @@ cudaError_t launch_apply_tc(const CUtensorMap& m, const float* Wm, int T, long l
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  apply_tc_kernel<TP><<<grid, kAThreads, apply_tc_smem<TP>(), st>>>(m, Wm, T, N, Y, ldy, ntiles, err);
+  apply_tc_kernel<TP><<<grid, kAThreads, apply_tc_smem<TP>(), st>>>(xm, ym, Wm, T, N, ntiles, err);
   return cudaGetLastError();
 }
 
-// FP32 map over X [T rows][N] (row pitch ld floats), box [box_rows][box_inner].
+// FP32 map over X [T rows][N] (row pitch ld floats), box [box_rows][box_inner];
+// 128-byte swizzle when the box rows are exactly 128 bytes (box_inner = 32).
 int x_map(CUtensorMap* m, const float* X, long long ld, long long N, int T, int box_inner, int box_rows) {
   PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
   if (!fn) return -1;
@@ -449,8 +477,9 @@ int x_map(CUtensorMap* m, const float* X, long long ld, long long N, int T, int 
   const cuuint32_t box[2] = {(cuuint32_t)box_inner, (cuuint32_t)box_rows};
   const cuuint32_t es[2] = {1, 1};
   const CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(X), dims, strides, box, es,
-                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                        CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        box_inner == 32 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? 0 : (int)r;
 }
 
@@ -484,10 +513,10 @@ int svt_gram_tc_blocks(long long N) {
   return (int)(nch < 152 ? nch : 152);
 }
 
-// Partial Grams (FP64, [grid][TP][TP]) of the N x T matrix X (row t at X + t ld)
+// Partial Grams (FP32, [grid][TP][TP]) of the N x T matrix X (row t at X + t ld)
 // on the tensor cores; TP = 32, 64 or 128 (T > 16).  ld * 4 must be a
 // multiple of 16 bytes and X 16-byte aligned (the TMA rules).
-cudaError_t svt_launch_gram_tc(const float* X, long long ld, long long N, int T, double* partials, int* err,
+cudaError_t svt_launch_gram_tc(const float* X, long long ld, long long N, int T, float* partials, int* err,
                                cudaStream_t st) {
   const int TP = svt_padded_T(T);
   if (TP < 32 || (ld * 4) % 16 != 0 || (reinterpret_cast<uintptr_t>(X) & 15) != 0) return cudaErrorInvalidValue;
@@ -513,20 +542,31 @@ int svt_apply_tc_blocks(long long N) {
 }
 
 // Y = X Wm on the tensor cores for T_pad = 32 or 64 (see apply_tc_kernel).
-// X, Y: [T][N] with row pitch ld / ldy floats; ld a multiple of 4 and X
-// 16-byte aligned (the TMA rules).
+// X, Y: [T][N] with row pitch ld / ldy floats; ld, ldy multiples of 4 and X,
+// Y 16-byte aligned (the TMA rules).
 cudaError_t svt_launch_apply_tc(const float* X, long long ld, long long N, int T, const float* Wm, float* Y,
                                 long long ldy, int* err, cudaStream_t st) {
   const int TP = svt_padded_T(T);
-  if ((TP != 32 && TP != 64) || ld % 4 != 0 || (reinterpret_cast<uintptr_t>(X) & 15) != 0)
+  if ((TP != 32 && TP != 64) || ld % 4 != 0 || ldy % 4 != 0 || (reinterpret_cast<uintptr_t>(X) & 15) != 0 ||
+      (reinterpret_cast<uintptr_t>(Y) & 15) != 0)
     return cudaErrorInvalidValue;
-  static thread_local MapCache cache = {};
-  const CUtensorMap* m = cached_map(cache, X, ld, N, T, kAN, TP);
-  if (!m) return cudaErrorInvalidValue;
+  static thread_local MapCache xcache = {};
+  static thread_local MapCache ycache[2] = {};   // the RPCA solver alternates two output planes
+  static thread_local int ynext = 0;
+  const CUtensorMap* xm = cached_map(xcache, X, ld, N, T, kAN, TP);
+  const CUtensorMap* ym = nullptr;
+  for (int k = 0; k < 2 && !ym; ++k)
+    if (ycache[k].valid && ycache[k].X == Y && ycache[k].ld == ldy && ycache[k].N == N && ycache[k].T == T)
+      ym = &ycache[k].m;
+  if (!ym) {
+    ym = cached_map(ycache[ynext], Y, ldy, N, T, 32, 32);
+    ynext ^= 1;
+  }
+  if (!xm || !ym) return cudaErrorInvalidValue;
   const int ntiles = (int)((N + kAN - 1) / kAN);
   const int grid = svt_apply_tc_blocks(N);
-  return TP == 32 ? launch_apply_tc<32>(*m, Wm, T, N, Y, ldy, ntiles, grid, err, st)
-                  : launch_apply_tc<64>(*m, Wm, T, N, Y, ldy, ntiles, grid, err, st);
+  return TP == 32 ? launch_apply_tc<32>(*xm, *ym, Wm, T, N, ntiles, grid, err, st)
+                  : launch_apply_tc<64>(*xm, *ym, Wm, T, N, ntiles, grid, err, st);
 }
 
 }  // namespace otp
