@@ -277,6 +277,50 @@ int ot_rpca_get_params(ot_rpca_t h, ot_rpca_params* out);
 int ot_rpca_destroy(ot_rpca_t h);
 
 /* ------------------------------------------------------------------------
+ * Batched Algorithm 1 over sequences of uneven size.  Sequence i holds B_i
+ * independent H_i x W_i problems of eq. Prox_UOT (e.g. the T_i - 1 frame
+ * pairs of a T_i-frame video, Alg. 3 line 11).  One launch per iteration
+ * runs every active sequence's tiles (a work list in device memory); each
+ * sequence has its own Theorem 1 step sizes, its own residuals (segmented
+ * FP64 sums) and leaves the work list when it meets tol.  Iterates are
+ * bit-identical to ot_prox_* with kernel OT_KERNEL_TILED on the same inputs.
+ * `common` supplies mode, norm, balanced, p_exp, mu, rho, tol, max_iter,
+ * check_every (even, >= 2) and use_graph; tau1, tau2 must be 0 (chosen per
+ * sequence); B, H, W, kernel, algorithm and precision are ignored. */
+typedef struct ot_prox_batch* ot_prox_batch_t;
+
+typedef struct {
+  int32_t iters;          /* iterations run on this sequence                     */
+  int32_t status;         /* OT_OK, OT_ENOTCONV or OT_ENONFINITE                  */
+  double  res_pri;        /* ||K(z)|| / ||p|| at the last check                   */
+  double  res_fp;         /* relative change of (z, a) at the last check          */
+} ot_prox_batch_result;
+
+/* n_seq in [1, 256]; B, H, W: host arrays of n_seq sizes.  State zero. */
+int ot_prox_batch_create(int32_t n_seq, const int32_t* B, const int32_t* H, const int32_t* W,
+                         const ot_prox_params* common, void* cuda_stream, ot_prox_batch_t* out);
+/* Prox centres of sequence seq, [B_i][H_i][W_i] float32, host or device. */
+int ot_prox_batch_set_input(ot_prox_batch_t h, int32_t seq, const float* p0, const float* p1);
+/* n_iter iterations of every sequence, no stopping test (stream-ordered). */
+int ot_prox_batch_step(ot_prox_batch_t h, int32_t n_iter);
+/* Iterate every sequence to the stopping rule; res: host array of n_seq.
+ * launches (optional): kernel launches made.  Synchronises.  Returns
+ * OT_ENOTCONV if some sequence hit max_iter (results still valid). */
+int ot_prox_batch_solve(ot_prox_batch_t h, ot_prox_batch_result* res, int32_t* launches);
+/* State of sequence seq, [B_i][H_i][W_i] each (NULL to skip); synchronises. */
+int ot_prox_batch_get_state(ot_prox_batch_t h, int32_t seq, float* Mx, float* My, float* x0, float* x1, float* r,
+                            float* a);
+/* Tile height (8 or 16 rows of 128 columns) and persistent CTAs per SM (1..8). */
+int ot_prox_batch_set_config(ot_prox_batch_t h, int32_t tile_rows, int32_t ctas_per_sm);
+/* Time every candidate configuration on the loaded problems (4 plain
+ * iterations each, CUDA events) and keep the fastest; outputs optional.  The
+ * iterates advance: call ot_prox_batch_reset for a cold start. */
+int ot_prox_batch_autotune(ot_prox_batch_t h, int32_t* tile_rows, int32_t* ctas_per_sm, float* ms_per_iter);
+/* Zero every sequence's state (keeps the inputs). */
+int ot_prox_batch_reset(ot_prox_batch_t h);
+int ot_prox_batch_destroy(ot_prox_batch_t h);
+
+/* ------------------------------------------------------------------------
  * UOT-DF / BPDN+UOT-DF (Algorithm 2, Sec. IV-A.1), Phi = I, for B
  * independent frames [B][H][W]:
  *   min_{s >= 0} 1/2 ||y - s||^2 + lambda ||s||_1 + kappa V_mu(s, s0)

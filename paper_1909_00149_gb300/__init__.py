@@ -259,6 +259,75 @@ class Rpca:
         return out
 
 
+class ProxBatch:
+    """Algorithm 1 on sequences of uneven size in one launch per iteration.
+    ``sizes``: list of (B_i, H_i, W_i); ``params``: the shared ot_prox_params
+    fields (mode, norm, mu, rho, tol, max_iter, check_every, use_graph, ...)."""
+
+    def __init__(self, sizes, stream=None, **params):
+        self.sizes = [(int(b), int(h), int(w)) for b, h, w in sizes]
+        n = len(self.sizes)
+        arr = lambda k: (ctypes.c_int32 * n)(*[s[k] for s in self.sizes])
+        p = default_params(**params)
+        h = ctypes.c_void_p()
+        self._stream = _stream_handle(stream)
+        check(_lib.ot_prox_batch_create(n, arr(0), arr(1), arr(2), ctypes.byref(p), self._stream, ctypes.byref(h)),
+              "ot_prox_batch_create")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            _lib.ot_prox_batch_destroy(self.h)
+            self.h = None
+
+    __del__ = close
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def set_input(self, seq: int, p0, p1):
+        b, hh, w = self.sizes[seq]
+        A = _Arrays(b * hh * w)
+        check(_lib.ot_prox_batch_set_input(self.h, int(seq), A.ptr(p0), A.ptr(p1)), "ot_prox_batch_set_input")
+
+    def step(self, n_iter: int):
+        check(_lib.ot_prox_batch_step(self.h, int(n_iter)), "ot_prox_batch_step")
+
+    def solve(self):
+        n = len(self.sizes)
+        res = (_abi.ot_prox_batch_result * n)()
+        launches = ctypes.c_int32()
+        check(_lib.ot_prox_batch_solve(self.h, res, ctypes.byref(launches)), "ot_prox_batch_solve",
+              ok=(OT_OK, OT_ENOTCONV))
+        return [r.as_dict() for r in res], launches.value
+
+    def set_config(self, tile_rows: int, ctas_per_sm: int):
+        check(_lib.ot_prox_batch_set_config(self.h, int(tile_rows), int(ctas_per_sm)), "ot_prox_batch_set_config")
+
+    def autotune(self) -> dict:
+        th, cp, ms = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_float()
+        check(_lib.ot_prox_batch_autotune(self.h, ctypes.byref(th), ctypes.byref(cp), ctypes.byref(ms)),
+              "ot_prox_batch_autotune")
+        return {"tile_rows": th.value, "ctas_per_sm": cp.value, "ms_per_iter": ms.value}
+
+    def reset(self):
+        check(_lib.ot_prox_batch_reset(self.h), "ot_prox_batch_reset")
+
+    def get_state(self, seq: int, device=None) -> dict:
+        import torch
+        b, hh, w = self.sizes[seq]
+        dev = torch.device("cuda") if device is None else torch.device(device)
+        names = ("Mx", "My", "x0", "x1", "r", "a")
+        out = {k: torch.empty((b, hh, w), dtype=torch.float32, device=dev) for k in names}
+        A = _Arrays(b * hh * w)
+        check(_lib.ot_prox_batch_get_state(self.h, int(seq), *(A.ptr(out[k], True) for k in names)),
+              "ot_prox_batch_get_state")
+        return out
+
+
 def uotdf_default_params(**kw) -> "_abi.ot_uotdf_params":
     p = _abi.ot_uotdf_params()
     _lib.ot_uotdf_default_params(ctypes.byref(p))
@@ -351,4 +420,4 @@ def svt(X, theta: float, stream=None):
     return Y
 
 
-__all__ = ["Uotdf", "uotdf_default_params", "Rpca", "svt", "neumann_solve", "rpca_default_params", "OtProx", "OtError", "default_params", "check", "LIB_PATH", "ot_prox_params", "ot_prox_result"]
+__all__ = ["ProxBatch", "Uotdf", "uotdf_default_params", "Rpca", "svt", "neumann_solve", "rpca_default_params", "OtProx", "OtError", "default_params", "check", "LIB_PATH", "ot_prox_params", "ot_prox_result"]

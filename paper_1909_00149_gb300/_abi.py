@@ -64,6 +64,14 @@ class ot_rpca_result(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class ot_prox_batch_result(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int32), ("status", ctypes.c_int32), ("res_pri", ctypes.c_double),
+                ("res_fp", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class ot_uotdf_params(ctypes.Structure):
     _fields_ = [("B", ctypes.c_int32), ("H", ctypes.c_int32), ("W", ctypes.c_int32),
                 ("kappa", ctypes.c_double), ("mu", ctypes.c_double), ("rho", ctypes.c_double),
@@ -115,6 +123,20 @@ PROTOTYPES = [
     ("ot_rpca_reset", ctypes.c_int, [ctypes.c_void_p]),
     ("ot_rpca_get_params", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ot_rpca_params)]),
     ("ot_rpca_destroy", ctypes.c_int, [ctypes.c_void_p]),
+    ("ot_prox_batch_create", ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
+                                            ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
+                                            ctypes.POINTER(ot_prox_params), ctypes.c_void_p,
+                                            ctypes.POINTER(ctypes.c_void_p)]),
+    ("ot_prox_batch_set_input", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p]),
+    ("ot_prox_batch_step", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
+    ("ot_prox_batch_solve", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ot_prox_batch_result),
+                                           ctypes.POINTER(ctypes.c_int32)]),
+    ("ot_prox_batch_get_state", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32] + [ctypes.c_void_p] * 6),
+    ("ot_prox_batch_set_config", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32]),
+    ("ot_prox_batch_autotune", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32),
+                                              ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_float)]),
+    ("ot_prox_batch_reset", ctypes.c_int, [ctypes.c_void_p]),
+    ("ot_prox_batch_destroy", ctypes.c_int, [ctypes.c_void_p]),
     ("ot_uotdf_default_params", None, [ctypes.POINTER(ot_uotdf_params)]),
     ("ot_uotdf_create", ctypes.c_int, [ctypes.POINTER(ot_uotdf_params), ctypes.c_void_p,
                                        ctypes.POINTER(ctypes.c_void_p)]),
