@@ -283,7 +283,8 @@ int ot_rpca_destroy(ot_rpca_t h);
  * runs every active sequence's tiles (a work list in device memory); each
  * sequence has its own Theorem 1 step sizes, its own residuals (segmented
  * FP64 sums) and leaves the work list when it meets tol.  Iterates are
- * bit-identical to ot_prox_* with kernel OT_KERNEL_TILED on the same inputs.
+ * bit-identical to ot_prox_* with kernel OT_KERNEL_TILED on the same inputs
+ * (and so to its TMA kernel); OT_ETIMEOUT if a bounded wait expired.
  * `common` supplies mode, norm, balanced, p_exp, mu, rho, tol, max_iter,
  * check_every (even, >= 2) and use_graph; tau1, tau2 must be 0 (chosen per
  * sequence); B, H, W, kernel, algorithm and precision are ignored. */
@@ -310,12 +311,15 @@ int ot_prox_batch_solve(ot_prox_batch_t h, ot_prox_batch_result* res, int32_t* l
 /* State of sequence seq, [B_i][H_i][W_i] each (NULL to skip); synchronises. */
 int ot_prox_batch_get_state(ot_prox_batch_t h, int32_t seq, float* Mx, float* My, float* x0, float* x1, float* r,
                             float* a);
-/* Tile height (8 or 16 rows of 128 columns) and persistent CTAs per SM (1..8). */
-int ot_prox_batch_set_config(ot_prox_batch_t h, int32_t tile_rows, int32_t ctas_per_sm);
+/* Iteration kernel: OT_KERNEL_TMA (the TMA pipeline, one CTA per SM,
+ * 16-row tiles; the default) or OT_KERNEL_TILED with tile_rows 8 or 16 and
+ * ctas_per_sm persistent CTAs per SM (1..8).  Iterates do not depend on it. */
+int ot_prox_batch_set_config(ot_prox_batch_t h, int32_t kernel, int32_t tile_rows, int32_t ctas_per_sm);
 /* Time every candidate configuration on the loaded problems (4 plain
  * iterations each, CUDA events) and keep the fastest; outputs optional.  The
  * iterates advance: call ot_prox_batch_reset for a cold start. */
-int ot_prox_batch_autotune(ot_prox_batch_t h, int32_t* tile_rows, int32_t* ctas_per_sm, float* ms_per_iter);
+int ot_prox_batch_autotune(ot_prox_batch_t h, int32_t* kernel, int32_t* tile_rows, int32_t* ctas_per_sm,
+                           float* ms_per_iter);
 /* Zero every sequence's state (keeps the inputs). */
 int ot_prox_batch_reset(ot_prox_batch_t h);
 int ot_prox_batch_destroy(ot_prox_batch_t h);

@@ -304,14 +304,18 @@ class ProxBatch:
               ok=(OT_OK, OT_ENOTCONV))
         return [r.as_dict() for r in res], launches.value
 
-    def set_config(self, tile_rows: int, ctas_per_sm: int):
-        check(_lib.ot_prox_batch_set_config(self.h, int(tile_rows), int(ctas_per_sm)), "ot_prox_batch_set_config")
+    def set_config(self, kernel="tma", tile_rows: int = 16, ctas_per_sm: int = 1):
+        k = KERNELS[kernel] if isinstance(kernel, str) else kernel
+        check(_lib.ot_prox_batch_set_config(self.h, int(k), int(tile_rows), int(ctas_per_sm)),
+              "ot_prox_batch_set_config")
 
     def autotune(self) -> dict:
-        th, cp, ms = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_float()
-        check(_lib.ot_prox_batch_autotune(self.h, ctypes.byref(th), ctypes.byref(cp), ctypes.byref(ms)),
-              "ot_prox_batch_autotune")
-        return {"tile_rows": th.value, "ctas_per_sm": cp.value, "ms_per_iter": ms.value}
+        k, th, cp, ms = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_float()
+        check(_lib.ot_prox_batch_autotune(self.h, ctypes.byref(k), ctypes.byref(th), ctypes.byref(cp),
+                                          ctypes.byref(ms)), "ot_prox_batch_autotune")
+        names = {v: n for n, v in KERNELS.items()}
+        return {"kernel": names.get(k.value, k.value), "tile_rows": th.value, "ctas_per_sm": cp.value,
+                "ms_per_iter": ms.value}
 
     def reset(self):
         check(_lib.ot_prox_batch_reset(self.h), "ot_prox_batch_reset")

@@ -132,9 +132,10 @@ PROTOTYPES = [
     ("ot_prox_batch_solve", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ot_prox_batch_result),
                                            ctypes.POINTER(ctypes.c_int32)]),
     ("ot_prox_batch_get_state", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32] + [ctypes.c_void_p] * 6),
-    ("ot_prox_batch_set_config", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32]),
+    ("ot_prox_batch_set_config", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]),
     ("ot_prox_batch_autotune", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32),
-                                              ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_float)]),
+                                              ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
+                                              ctypes.POINTER(ctypes.c_float)]),
     ("ot_prox_batch_reset", ctypes.c_int, [ctypes.c_void_p]),
     ("ot_prox_batch_destroy", ctypes.c_int, [ctypes.c_void_p]),
     ("ot_uotdf_default_params", None, [ctypes.POINTER(ot_uotdf_params)]),

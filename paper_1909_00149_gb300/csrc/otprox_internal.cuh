@@ -62,6 +62,28 @@ struct TmaMaps {
   CUtensorMap a, Mx, My, x0, x1, r, p0, p1;
 };
 
+// Batched Algorithm 1 (prox_batch.cu, prox_tma.cu): the sequences' planes
+// share one slab per state plane (sequence i at base + off); each sequence
+// has its own geometry, step sizes and, for the TMA pipeline, tensor maps
+// per ping-pong parity of M, a (in device memory, 64-byte aligned).
+struct BatchPlanes {
+  float *Mx[2], *My[2], *a[2];
+  float *x0, *x1, *r, *p0, *p1;
+};
+struct BatchSeq {
+  TmaMaps maps[2];
+  Geometry G;
+  IterCoeffs C;
+  long long off;      // element offset of the sequence in every plane
+  int tile0;          // first tile of the sequence in the partial-sum rows
+  int ntiles;         // tiles of one iteration at the current tile height
+};
+constexpr int kBatchMaxSeq = 256;   // sequences per batch (work list in shared memory)
+cudaError_t prepare_prox_tma_batch(int mode, bool balanced);
+cudaError_t launch_prox_tma_batch(int mode, bool balanced, bool reduce, const BatchSeq* seqs, const int* act,
+                                  int parity, const BatchPlanes& P, double* partials, int* err, int grid,
+                                  cudaStream_t st);
+
 struct CertCoeffs {
   double mu, rho;
   int iso, pexp, mode, balanced;

@@ -20,9 +20,11 @@
 // tolerance leave the work list.  A check interval (an even number of
 // iterations, so that all active sequences share the ping-pong parity) is
 // captured once as a CUDA graph; the work list is data, so the graph stays
-// valid as sequences finish.  The tile height (8 or 16 rows) and the CTAs
-// per SM (1, 2, 4) are chosen by timing every candidate on the loaded
-// problems (ot_prox_batch_autotune).
+// valid as sequences finish.  Two iteration kernels walk the list: this
+// file's tiled kernel (tile height 8 or 16 rows, 1-4 CTAs per SM) and the
+// TMA pipeline of prox_tma.cu (one CTA per SM, per-sequence tensor maps);
+// ot_prox_batch_autotune times every candidate on the loaded problems and
+// keeps the fastest.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdlib.h>
@@ -38,20 +40,8 @@ using namespace otp;
 
 namespace {
 
-struct SeqDesc {
-  Geometry G;
-  IterCoeffs C;
-  long long off;      // element offset of the sequence in every plane
-  int tile0;          // first tile of the sequence in the partial-sum rows
-  int ntiles;         // tiles of one iteration at the current tile height
-};
-
-constexpr int kMaxSeq = 256;    // sequences per batch (the shared-memory work list)
-
-struct BatchPlanes {
-  float *Mx[2], *My[2], *a[2];
-  float *x0, *x1, *r, *p0, *p1;
-};
+using SeqDesc = BatchSeq;
+constexpr int kMaxSeq = kBatchMaxSeq;
 
 template <int MODE, bool BAL, bool RED, int TH>
 __global__ void __launch_bounds__(kTiledThreads, 2)
@@ -78,12 +68,13 @@ prox_batch_kernel(const SeqDesc* __restrict__ seqs, const int* __restrict__ act,
     const SeqDesc& d = seqs[s_seq[lo]];
     const int t = w - s_pre[lo];
     StatePtrs S;
-    S.Mx_in = P.Mx[parity] + d.off;
-    S.My_in = P.My[parity] + d.off;
-    S.a_in = P.a[parity] + d.off;
-    S.Mx_out = P.Mx[parity ^ 1] + d.off;
-    S.My_out = P.My[parity ^ 1] + d.off;
-    S.a_out = P.a[parity ^ 1] + d.off;
+    // selects, not P.Mx[parity]: a runtime index into a kernel parameter would go through local memory
+    S.Mx_in = (parity ? P.Mx[1] : P.Mx[0]) + d.off;
+    S.My_in = (parity ? P.My[1] : P.My[0]) + d.off;
+    S.a_in = (parity ? P.a[1] : P.a[0]) + d.off;
+    S.Mx_out = (parity ? P.Mx[0] : P.Mx[1]) + d.off;
+    S.My_out = (parity ? P.My[0] : P.My[1]) + d.off;
+    S.a_out = (parity ? P.a[0] : P.a[1]) + d.off;
     S.x0 = P.x0 + d.off;
     S.x1 = P.x1 + d.off;
     S.r = P.r + d.off;
@@ -175,7 +166,9 @@ struct ot_prox_batch {
   int* hact;                          // pinned work list
   int n_act, act_tiles;
   int parity;
-  int tile_rows, ctas_per_sm, n_sm;
+  int kernel, tile_rows, ctas_per_sm, n_sm;   // kernel: OT_KERNEL_TILED or OT_KERNEL_TMA
+  int* derr;                          // TMA pipeline: bounded-wait error flag
+  int* herr;
   int max_tiles;
   cudaGraphExec_t graph;              // one check interval
   int graph_n, graph_par;
@@ -190,9 +183,10 @@ int tiles_of(const Geometry& G, int th) {
 // Tile counts and offsets for the current tile height; descriptors to the device.
 int set_tiles(ot_prox_batch* h) {
   int t0 = 0;
+  const int th = h->kernel == OT_KERNEL_TMA ? kTH : h->tile_rows;
   for (auto& d : h->host) {
     d.G.tiles_x = (d.G.Wp + kTW - 1) / kTW;
-    d.G.tiles_y = (d.G.H + h->tile_rows - 1) / h->tile_rows;
+    d.G.tiles_y = (d.G.H + th - 1) / th;
     d.ntiles = d.G.B * d.G.tiles_x * d.G.tiles_y;
     d.tile0 = t0;
     t0 += d.ntiles;
@@ -230,11 +224,19 @@ int grid_of(const ot_prox_batch* h) {
 }
 
 cudaError_t launch_iter(ot_prox_batch* h, bool red) {
-  BatchKernel k = pick_kernel(h->prm.mode, h->prm.balanced != 0, red, h->tile_rows);
-  const dim3 block(kTX, kTY);
-  k<<<grid_of(h), block, 0, h->stream>>>(h->dseqs, h->dact, h->parity, h->P, h->partials);
+  cudaError_t e;
+  if (h->kernel == OT_KERNEL_TMA) {
+    const int grid = h->act_tiles < h->n_sm ? (h->act_tiles > 0 ? h->act_tiles : 1) : h->n_sm;
+    e = launch_prox_tma_batch(h->prm.mode, h->prm.balanced != 0, red, h->dseqs, h->dact, h->parity, h->P,
+                              h->partials, h->derr, grid, h->stream);
+  } else {
+    BatchKernel k = pick_kernel(h->prm.mode, h->prm.balanced != 0, red, h->tile_rows);
+    const dim3 block(kTX, kTY);
+    k<<<grid_of(h), block, 0, h->stream>>>(h->dseqs, h->dact, h->parity, h->P, h->partials);
+    e = cudaGetLastError();
+  }
   h->parity ^= 1;
-  return cudaGetLastError();
+  return e;
 }
 
 // n iterations of every active sequence; the last one reduces, and the
@@ -247,6 +249,7 @@ int enqueue_interval(ot_prox_batch* h, int n, bool sums) {
     OT_CUDA(cudaMemcpyAsync(h->hsums, h->dsums, (size_t)h->n_seq * kNumSums * sizeof(double), cudaMemcpyDeviceToHost,
                             h->stream),
             "batch: sums copy");
+    OT_CUDA(cudaMemcpyAsync(h->herr, h->derr, sizeof(int), cudaMemcpyDeviceToHost, h->stream), "batch: error flag");
   }
   return OT_OK;
 }
@@ -302,6 +305,8 @@ int ot_prox_batch_destroy(ot_prox_batch_t h) {
   cudaFree(h->dseqs);
   cudaFree(h->dact);
   cudaFree(h->partials);
+  cudaFree(h->derr);
+  if (h->herr) cudaFreeHost(h->herr);
   if (h->hsums) cudaFreeHost(h->hsums);
   if (h->hact) cudaFreeHost(h->hact);
   delete h;
@@ -328,6 +333,7 @@ int ot_prox_batch_create(int32_t n_seq, const int32_t* B, const int32_t* H, cons
   h->prm = p;
   h->stream = (cudaStream_t)cuda_stream;
   h->n_seq = n_seq;
+  h->kernel = OT_KERNEL_TMA;
   h->tile_rows = 16;
   h->ctas_per_sm = 2;
   int dev = 0;
@@ -382,6 +388,10 @@ int ot_prox_batch_create(int32_t n_seq, const int32_t* B, const int32_t* H, cons
   if (e == cudaSuccess) e = cudaMalloc(&h->partials, ((size_t)h->max_tiles + (size_t)n_seq) * kNumSums * sizeof(double));
   if (e == cudaSuccess) e = cudaMallocHost(&h->hsums, (size_t)n_seq * kNumSums * sizeof(double));
   if (e == cudaSuccess) e = cudaMallocHost(&h->hact, (2 * (size_t)n_seq + 2) * sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&h->derr, sizeof(int));
+  if (e == cudaSuccess) e = cudaMallocHost(&h->herr, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->derr, 0, sizeof(int), h->stream);
+  if (e == cudaSuccess) e = prepare_prox_tma_batch(p.mode, p.balanced != 0);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->slab, 0, off * 11 * sizeof(float), h->stream);
   if (e != cudaSuccess) {
     ot_prox_batch_destroy(h);
@@ -400,7 +410,29 @@ int ot_prox_batch_create(int32_t n_seq, const int32_t* B, const int32_t* H, cons
   h->P.r = q; q += off;
   h->P.p0 = q; q += off;
   h->P.p1 = q;
-  int rc = set_tiles(h);
+  if (h->herr) *h->herr = 0;
+  // per-sequence tensor maps of the TMA pipeline, for both parities of M, a
+  int rc = OT_OK;
+  for (int i = 0; i < n_seq && rc == OT_OK; ++i) {
+    SeqDesc& d = h->host[i];
+    int bw, bh, r2 = 0;
+    for (int par = 0; par < 2; ++par) {
+      TmaMaps& m = d.maps[par];
+      tma_box(0, &bw, &bh);
+      r2 |= encode_plane_map(&m.a, h->P.a[par] + d.off, d.G, bw, bh);
+      tma_box(1, &bw, &bh);
+      r2 |= encode_plane_map(&m.Mx, h->P.Mx[par] + d.off, d.G, bw, bh);
+      r2 |= encode_plane_map(&m.My, h->P.My[par] + d.off, d.G, bw, bh);
+      tma_box(2, &bw, &bh);
+      r2 |= encode_plane_map(&m.x0, h->P.x0 + d.off, d.G, bw, bh);
+      r2 |= encode_plane_map(&m.x1, h->P.x1 + d.off, d.G, bw, bh);
+      r2 |= encode_plane_map(&m.r, h->P.r + d.off, d.G, bw, bh);
+      r2 |= encode_plane_map(&m.p0, h->P.p0 + d.off, d.G, bw, bh);
+      r2 |= encode_plane_map(&m.p1, h->P.p1 + d.off, d.G, bw, bh);
+    }
+    if (r2 != 0) h->kernel = OT_KERNEL_TILED;   // no TMA maps: the tiled kernel only
+  }
+  rc = set_tiles(h);
   if (rc == OT_OK) rc = upload_work(h);
   if (rc == OT_OK) {
     e = cudaStreamSynchronize(h->stream);
@@ -461,6 +493,7 @@ int ot_prox_batch_solve(ot_prox_batch_t h, ot_prox_batch_result* res, int32_t* l
     n_launch += ce + 1;
     done_iters += ce;
     OT_CUDA(cudaStreamSynchronize(h->stream), "ot_prox_batch_solve: sync");
+    if (*h->herr) return fail(OT_ETIMEOUT, "ot_prox_batch_solve: a bounded device wait expired in the TMA pipeline");
     bool changed = false;
     for (int i = 0; i < h->n_seq; ++i) {
       if (!h->active[i]) continue;
@@ -516,10 +549,13 @@ int ot_prox_batch_get_state(ot_prox_batch_t h, int32_t seq, float* Mx, float* My
   return OT_OK;
 }
 
-int ot_prox_batch_set_config(ot_prox_batch_t h, int32_t tile_rows, int32_t ctas_per_sm) {
+int ot_prox_batch_set_config(ot_prox_batch_t h, int32_t kernel, int32_t tile_rows, int32_t ctas_per_sm) {
   if (!h) return fail(OT_EINVAL, "ot_prox_batch_set_config: NULL handle");
+  if (kernel != OT_KERNEL_TILED && kernel != OT_KERNEL_TMA)
+    return fail(OT_EINVAL, "ot_prox_batch_set_config: kernel must be OT_KERNEL_TILED or OT_KERNEL_TMA");
   if (tile_rows != 8 && tile_rows != 16) return fail(OT_EINVAL, "ot_prox_batch_set_config: tile_rows must be 8 or 16");
   if (ctas_per_sm < 1 || ctas_per_sm > 8) return fail(OT_EINVAL, "ot_prox_batch_set_config: ctas_per_sm in [1, 8]");
+  h->kernel = kernel;
   h->tile_rows = tile_rows;
   h->ctas_per_sm = ctas_per_sm;
   destroy_graph(h);
@@ -532,18 +568,25 @@ int ot_prox_batch_set_config(ot_prox_batch_t h, int32_t tile_rows, int32_t ctas_
 // (plain iterations, CUDA events, after one warm-up launch) and keep the
 // fastest.  The iterates advance by the timed iterations; call
 // ot_prox_batch_reset afterwards for a cold start.
-int ot_prox_batch_autotune(ot_prox_batch_t h, int32_t* tile_rows, int32_t* ctas_per_sm, float* best_ms) {
+int ot_prox_batch_autotune(ot_prox_batch_t h, int32_t* kernel, int32_t* tile_rows, int32_t* ctas_per_sm,
+                           float* best_ms) {
   if (!h) return fail(OT_EINVAL, "ot_prox_batch_autotune: NULL handle");
-  const int ths[2] = {8, 16}, cps[3] = {1, 2, 4};
+  // candidates: the TMA pipeline (one CTA per SM), then the tiled kernel
+  // with 8 or 16 rows per tile and 1, 2 or 4 CTAs per SM
+  struct Cand { int kernel, th, cp; };
+  std::vector<Cand> cands;
+  if (h->kernel == OT_KERNEL_TMA) cands.push_back({OT_KERNEL_TMA, 16, 1});
+  for (int th : {8, 16})
+    for (int cp : {1, 2, 4}) cands.push_back({OT_KERNEL_TILED, th, cp});
   float best = INFINITY;
-  int bth = 16, bcp = 2;
+  Cand bc = cands[0];
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   OT_CUDA(cudaEventCreate(&e0), "autotune: event");
   OT_CUDA(cudaEventCreate(&e1), "autotune: event");
   int rc = OT_OK;
-  for (int a = 0; a < 2 && rc == OT_OK; ++a)
-    for (int b = 0; b < 3 && rc == OT_OK; ++b) {
-      rc = ot_prox_batch_set_config(h, ths[a], cps[b]);
+  for (size_t c = 0; c < cands.size() && rc == OT_OK; ++c) {
+    {
+      rc = ot_prox_batch_set_config(h, cands[c].kernel, cands[c].th, cands[c].cp);
       if (rc != OT_OK) break;
       cudaError_t e = launch_iter(h, false);
       if (e == cudaSuccess) e = cudaEventRecord(e0, h->stream);
@@ -555,16 +598,17 @@ int ot_prox_batch_autotune(ot_prox_batch_t h, int32_t* tile_rows, int32_t* ctas_
       if (e != cudaSuccess) rc = cuda_fail(e, "ot_prox_batch_autotune");
       else if (ms < best) {
         best = ms;
-        bth = ths[a];
-        bcp = cps[b];
+        bc = cands[c];
       }
     }
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (rc != OT_OK) return rc;
-  rc = ot_prox_batch_set_config(h, bth, bcp);
-  if (tile_rows) *tile_rows = bth;
-  if (ctas_per_sm) *ctas_per_sm = bcp;
+  rc = ot_prox_batch_set_config(h, bc.kernel, bc.th, bc.cp);
+  if (kernel) *kernel = bc.kernel;
+  if (tile_rows) *tile_rows = bc.th;
+  if (ctas_per_sm) *ctas_per_sm = bc.cp;
   if (best_ms) *best_ms = best / 4.f;
   return rc;
 }

@@ -364,8 +364,6 @@ apply_tc_kernel(const __grid_constant__ CUtensorMap xmap, const __grid_constant_
     // A = Wm (symmetric), once: rows t < TP, frames s < TP, groups of 8 frames
     for (int task = q; task < TP * (TP / 8); task += 32 * kSplitWarps) {
       const int row = task / (TP / 8), g = task % (TP / 8);
-      float h[8], m[8], l[8];
-#pragma unroll
       float x[8];
 #pragma unroll
       for (int j = 0; j < 8; ++j) x[j] = __ldg(Wm + (size_t)row * TP + g * 8 + j);

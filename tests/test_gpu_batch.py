@@ -31,13 +31,13 @@ def single_state(lib, b, h, w, p0, p1, n, **kw):
         return s.get_state()
 
 
-@pytest.mark.parametrize("tile_rows", [8, 16])
+@pytest.mark.parametrize("config", [("tma", 16, 1), ("tiled", 8, 2), ("tiled", 16, 2)])
 @pytest.mark.parametrize("mode", ["prox", "fixed_first", "eval"])
-def test_batch_iterates_equal_single_problem_bit_for_bit(lib, tile_rows, mode):
+def test_batch_iterates_equal_single_problem_bit_for_bit(lib, config, mode):
     n = 7
     ins = [seq_inputs(k, *sz) for k, sz in enumerate(SIZES)]
     with lib.ProxBatch(SIZES, mode=mode, **KW) as bt:
-        bt.set_config(tile_rows, 2)
+        bt.set_config(*config)
         for k, (p0, p1) in enumerate(ins):
             bt.set_input(k, p0, p1)
         bt.step(n)
@@ -48,9 +48,11 @@ def test_batch_iterates_equal_single_problem_bit_for_bit(lib, tile_rows, mode):
             assert torch.equal(got[k][name], ref[name]), (k, name)
 
 
-def test_batch_solve_matches_single_problem_solves(lib):
+@pytest.mark.parametrize("kernel", ["tma", "tiled"])
+def test_batch_solve_matches_single_problem_solves(lib, kernel):
     ins = [seq_inputs(10 + k, *sz) for k, sz in enumerate(SIZES)]
     with lib.ProxBatch(SIZES, tol=1e-5, max_iter=40000, **KW) as bt:
+        bt.set_config(kernel, 16, 2)
         for k, (p0, p1) in enumerate(ins):
             bt.set_input(k, p0, p1)
         res, launches = bt.solve()
@@ -93,7 +95,8 @@ def test_batch_autotune_keeps_results(lib):
         for k, (p0, p1) in enumerate(ins):
             bt.set_input(k, p0, p1)
         cfg = bt.autotune()
-        assert cfg["tile_rows"] in (8, 16) and cfg["ctas_per_sm"] in (1, 2, 4) and cfg["ms_per_iter"] > 0
+        assert cfg["kernel"] in ("tma", "tiled") and cfg["tile_rows"] in (8, 16)
+        assert cfg["ctas_per_sm"] in (1, 2, 4) and cfg["ms_per_iter"] > 0
         bt.reset()
         bt.step(5)
         got = bt.get_state(2)
