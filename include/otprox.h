@@ -388,6 +388,43 @@ int ot_uotdf_reset(ot_uotdf_t h);
 int ot_uotdf_get_params(ot_uotdf_t h, ot_uotdf_params* out);
 int ot_uotdf_destroy(ot_uotdf_t h);
 
+/* ------------------------------------------------------------------------
+ * Learned warm start for Algorithm 1.  Sec. III-B caches converged iterates
+ * and warm-starts the next solve from them; this network predicts such a
+ * state for a new frame pair: a 4-level U-Net (base C channels; 3x3
+ * zero-padded convolutions with ReLU, 2x2 average pooling, nearest 2x
+ * upsampling, skips concatenated after the upsampled channels, 1x1 head)
+ * maps x = (p0, p1) [n][2][H][W] to y = (Mx, My, r, a) [n][4][H][W].
+ * Weights are BF16 (FP32 master copy for the optimiser), activations FP32,
+ * products accumulated in FP32.  The solver still runs to its stopping rule
+ * from the predicted state, so the network only changes the iteration count.
+ *
+ * Parameters are one flat float32 array: for each convolution in forward
+ * order (enc0a, enc0b, enc1a, enc1b, enc2a, enc2b, botta, bottb, dec2a,
+ * dec2b, dec1a, dec1b, dec0a, dec0b, head) its weights [co][ci][k][k]
+ * followed by its biases [co].  All pointers may be host or device. */
+typedef struct ot_unet* ot_unet_t;
+
+/* H, W multiples of 8; max_batch >= 1; base_channels in [1, 256].  All
+ * parameters start at zero (set them with ot_unet_set_params). */
+int ot_unet_create(int32_t H, int32_t W, int32_t max_batch, int32_t base_channels, void* cuda_stream,
+                   ot_unet_t* out);
+/* Length of the flat parameter array (-1 for a NULL handle). */
+int64_t ot_unet_param_count(ot_unet_t h);
+/* Load parameters (resets the optimiser state).  Synchronises. */
+int ot_unet_set_params(ot_unet_t h, const float* params);
+int ot_unet_get_params(ot_unet_t h, float* params);
+/* y = net(x) for n <= max_batch inputs.  Synchronises. */
+int ot_unet_forward(ot_unet_t h, const float* x, float* y, int32_t n);
+/* Mean squared error between net(x) and target [n][4][H][W] (loss, optional)
+ * and its gradient with respect to the parameters (grads, flat layout,
+ * optional).  Synchronises; OT_ENONFINITE on a non-finite loss. */
+int ot_unet_gradients(ot_unet_t h, const float* x, const float* target, int32_t n, float* grads, double* loss);
+/* ot_unet_gradients followed by one Adam step (beta 0.9, 0.999, eps 1e-8)
+ * with learning rate lr on the FP32 master weights. */
+int ot_unet_train_step(ot_unet_t h, const float* x, const float* target, int32_t n, float lr, double* loss);
+int ot_unet_destroy(ot_unet_t h);
+
 /* Singular-value thresholding shrink*_theta(X) = U max(Sigma - theta, 0) V^T
  * (Sec. IV-B.1, Algorithm 3 line 10) of an N x T matrix stored as T columns of
  * N floats (X + t*N), via the T x T Gram matrix and a Jacobi eigensolver.

@@ -402,6 +402,100 @@ class Uotdf:
         return out
 
 
+def unet_layer_specs(base: int = 32) -> list[tuple[str, int, int, int]]:
+    """(name, in channels, out channels, kernel size) of the warm-start
+    network's convolutions in the library's parameter order."""
+    c = base
+    return [("enc0a", 2, c, 3), ("enc0b", c, c, 3), ("enc1a", c, 2 * c, 3), ("enc1b", 2 * c, 2 * c, 3),
+            ("enc2a", 2 * c, 4 * c, 3), ("enc2b", 4 * c, 4 * c, 3), ("botta", 4 * c, 8 * c, 3),
+            ("bottb", 8 * c, 8 * c, 3), ("dec2a", 12 * c, 4 * c, 3), ("dec2b", 4 * c, 4 * c, 3),
+            ("dec1a", 6 * c, 2 * c, 3), ("dec1b", 2 * c, 2 * c, 3), ("dec0a", 3 * c, c, 3), ("dec0b", c, c, 3),
+            ("head", c, 4, 1)]
+
+
+class UNet:
+    """The learned warm start of Algorithm 1: (p0, p1) [n, 2, H, W] ->
+    (Mx, My, r, a) [n, 4, H, W].  Parameters are one flat float32 array in
+    the order of :func:`unet_layer_specs` (weights [co, ci, k, k], then
+    biases [co], per layer)."""
+
+    def __init__(self, H: int, W: int, max_batch: int, base_channels: int = 32, stream=None):
+        self.H, self.W, self.max_batch, self.base = int(H), int(W), int(max_batch), int(base_channels)
+        h = ctypes.c_void_p()
+        self._stream = _stream_handle(stream)
+        check(_lib.ot_unet_create(self.H, self.W, self.max_batch, self.base, self._stream, ctypes.byref(h)),
+              "ot_unet_create")
+        self.h = h
+        self.n_params = int(_lib.ot_unet_param_count(self.h))
+
+    def close(self):
+        if getattr(self, "h", None):
+            _lib.ot_unet_destroy(self.h)
+            self.h = None
+
+    __del__ = close
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def init(self, seed: int = 0):
+        """He-normal weights, zero biases (numpy generator ``seed``)."""
+        rng = np.random.default_rng(seed)
+        parts = []
+        for _, ci, co, k in unet_layer_specs(self.base):
+            parts.append(rng.normal(0.0, np.sqrt(2.0 / (ci * k * k)), co * ci * k * k))
+            parts.append(np.zeros(co))
+        self.set_params(np.concatenate(parts).astype(np.float32))
+
+    def set_params(self, flat):
+        A = _Arrays(self.n_params)
+        check(_lib.ot_unet_set_params(self.h, A.ptr(flat)), "ot_unet_set_params")
+
+    def get_params(self) -> np.ndarray:
+        out = np.empty(self.n_params, dtype=np.float32)
+        check(_lib.ot_unet_get_params(self.h, out.ctypes.data), "ot_unet_get_params")
+        return out
+
+    def _n(self, x) -> int:
+        n = int(np.prod(x.shape)) // (2 * self.H * self.W)
+        if n < 1 or n * 2 * self.H * self.W != int(np.prod(x.shape)):
+            raise ValueError("input must hold n x 2 x H x W values")
+        return n
+
+    def forward(self, x, out=None):
+        """Prediction for x [n, 2, H, W] (host or device); a CUDA tensor."""
+        import torch
+        n = self._n(x)
+        y = torch.empty((n, 4, self.H, self.W), dtype=torch.float32, device="cuda") if out is None else out
+        check(_lib.ot_unet_forward(self.h, _Arrays(n * 2 * self.H * self.W).ptr(x),
+                                   _Arrays(n * 4 * self.H * self.W).ptr(y, True), n), "ot_unet_forward")
+        return y
+
+    def gradients(self, x, target) -> tuple[float, np.ndarray]:
+        """(MSE loss, d loss / d params) for one batch; no update."""
+        n = self._n(x)
+        g = np.empty(self.n_params, dtype=np.float32)
+        loss = ctypes.c_double()
+        Ax = _Arrays(n * 2 * self.H * self.W)
+        At = _Arrays(n * 4 * self.H * self.W)
+        check(_lib.ot_unet_gradients(self.h, Ax.ptr(x), At.ptr(target), n, g.ctypes.data, ctypes.byref(loss)),
+              "ot_unet_gradients")
+        return loss.value, g
+
+    def train_step(self, x, target, lr: float) -> float:
+        """One Adam step on the MSE loss; returns the loss before the step."""
+        n = self._n(x)
+        loss = ctypes.c_double()
+        Ax = _Arrays(n * 2 * self.H * self.W)
+        At = _Arrays(n * 4 * self.H * self.W)
+        check(_lib.ot_unet_train_step(self.h, Ax.ptr(x), At.ptr(target), n, float(lr), ctypes.byref(loss)),
+              "ot_unet_train_step")
+        return loss.value
+
+
 def neumann_solve(X, c: float, precision="fp32", out=None, stream=None):
     """(D D* + c I)^{-1} X for X [B, H, W] float32 CUDA (DCT-II)."""
     import torch
