@@ -185,6 +185,14 @@ int ot_prox_get_state(ot_prox_t h, float* Mx, float* My, float* x0, float* x1,
 int ot_prox_set_state(ot_prox_t h, const float* Mx, const float* My, const float* x0,
                       const float* x1, const float* r, const float* a);
 
+/* Warm start from a predicted state (e.g. ot_unet_forward's output): pred
+ * is a DEVICE array [B][4][H][W] float32 of (Mx, My, r, a) per problem.
+ * Mx, My, r (unless balanced) and a are copied in, the flux zeroed on the
+ * slots without an edge; each free x is set from its step's fixed point
+ * given a: x0 = max(p0 + rho a, 0), x1 = max(p1 - rho a, 0) (the inputs
+ * must be set).  Stream-ordered, no sync. */
+int ot_prox_warm_start(ot_prox_t h, const float* pred);
+
 /* Zero the state (Algorithm 2 line 2 initialises the prox state to 0). */
 int ot_prox_reset(ot_prox_t h);
 

@@ -181,6 +181,15 @@ class OtProx:
         check(_lib.ot_prox_set_state(self.h, A.ptr(Mx), A.ptr(My), A.ptr(x0), A.ptr(x1), A.ptr(r), A.ptr(a)),
               "ot_prox_set_state")
 
+    def warm_start(self, pred):
+        """Warm state from a prediction [B, 4, H, W] (Mx, My, r, a) CUDA
+        tensor, x from the x-step's fixed point (ot_prox_warm_start)."""
+        import torch
+        if not (isinstance(pred, torch.Tensor) and pred.is_cuda and pred.dtype == torch.float32
+                and pred.is_contiguous() and pred.numel() == 4 * self.n):
+            raise ValueError("pred must be a contiguous float32 CUDA tensor of B x 4 x H x W values")
+        check(_lib.ot_prox_warm_start(self.h, pred.data_ptr()), "ot_prox_warm_start")
+
 
 def rpca_default_params(**kw) -> "_abi.ot_rpca_params":
     p = _abi.ot_rpca_params()

@@ -244,6 +244,19 @@ static int evaluate_into(ot_prox* h, ot_prox_result* res) {
   return OT_OK;
 }
 
+// projection form: restart the splitting at w = z, u = 0 after the state
+// was written from outside
+static int restart_projection(ot_prox* h) {
+  if (!h->admm) return OT_OK;
+  for (int k = 0; k < 5; ++k)
+    OT_CUDA(cudaMemcpyAsync(h->AP.w[k], h->AP.z[k], h->plane_elems * sizeof(float), cudaMemcpyDeviceToDevice,
+                            h->stream),
+            "restart of the projection form: w = z");
+  OT_CUDA(cudaMemsetAsync(h->AP.u[0], 0, h->plane_elems * 5 * sizeof(float), h->stream),
+          "restart of the projection form: u = 0");
+  return OT_OK;
+}
+
 static int copy_plane_in(ot_prox* h, float* dst, const float* src) {
   const size_t wb = (size_t)h->G.W * sizeof(float);
   OT_CUDA(cudaMemcpy2DAsync(dst, (size_t)h->G.Wp * sizeof(float), src, wb, wb, (size_t)h->G.B * h->G.H,
@@ -610,14 +623,17 @@ int ot_prox_set_state(ot_prox_t h, const float* Mx, const float* My, const float
     OT_CUDA(cudaMemset2DAsync(h->My[c] + (h->G.W - 1), (size_t)h->G.Wp * fb, 0, fb, (size_t)h->G.B * h->G.H,
                               h->stream),
             "ot_prox_set_state: zeroing My[:,W-1]");
-  if (h->admm) {   // projection form: restart the splitting at w = z, u = 0
-    for (int k = 0; k < 5; ++k)
-      OT_CUDA(cudaMemcpyAsync(h->AP.w[k], h->AP.z[k], h->plane_elems * sizeof(float), cudaMemcpyDeviceToDevice,
-                              h->stream),
-              "ot_prox_set_state: w = z");
-    OT_CUDA(cudaMemsetAsync(h->AP.u[0], 0, h->plane_elems * 5 * sizeof(float), h->stream), "ot_prox_set_state: u = 0");
-  }
-  return OT_OK;
+  return restart_projection(h);
+}
+
+int ot_prox_warm_start(ot_prox_t h, const float* pred) {
+  if (!h || !pred) return fail(OT_EINVAL, "ot_prox_warm_start: NULL argument");
+  const int c = h->cur;
+  const bool fx0 = h->prm.mode != OT_MODE_PROX, fx1 = h->prm.mode == OT_MODE_EVAL;
+  OT_CUDA(launch_warm_start(pred, h->G, h->Mx[c], h->My[c], h->prm.balanced ? nullptr : h->r, h->a[c],
+                            fx0 ? nullptr : h->x0, fx1 ? nullptr : h->x1, h->p0, h->p1, (float)h->prm.rho, h->stream),
+          "ot_prox_warm_start");
+  return restart_projection(h);
 }
 
 int ot_prox_destroy(ot_prox_t h) {

@@ -1,0 +1,51 @@
+// Warm start of Algorithm 1 from a predicted state (Sec. III-B warm-starts
+// the iterates from a cache; here the cache is a network's prediction).
+//
+// pred is [B][4][H][W] (channels Mx, My, r, a, the layout the warm-start
+// network writes).  Mx, My, r and a go to the solver's current planes, with
+// the flux zeroed on the slots that have no edge (Mx on the last row, My on
+// the last column).  A free x is set from the x-step's fixed point, which is
+// the optimality condition of the (1/2 rho) ||x - p||^2 term given a:
+// x0 = max(p0 + rho a, 0), x1 = max(p1 - rho a, 0).
+#include <cuda_runtime.h>
+
+#include "otprox_internal.cuh"
+
+namespace otp {
+namespace {
+
+__global__ void warm_start_kernel(const float* __restrict__ pred, Geometry G, float* __restrict__ Mx,
+                                  float* __restrict__ My, float* __restrict__ r, float* __restrict__ a,
+                                  float* __restrict__ x0, float* __restrict__ x1, const float* __restrict__ p0,
+                                  const float* __restrict__ p1, float rho) {
+  const long long hw = (long long)G.H * G.W;
+  const long long total = (long long)G.B * hw;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const long long b = idx / hw;
+    const int i = (int)((idx / G.W) % G.H), j = (int)(idx % G.W);
+    const float* src = pred + b * 4 * hw + (long long)i * G.W + j;
+    const long long o = b * G.plane + (long long)i * G.Wp + j;
+    const float av = src[3 * hw];
+    Mx[o] = i == G.H - 1 ? 0.f : src[0];
+    My[o] = j == G.W - 1 ? 0.f : src[hw];
+    if (r) r[o] = src[2 * hw];
+    a[o] = av;
+    if (x0) x0[o] = fmaxf(fmaf(rho, av, p0[o]), 0.f);
+    if (x1) x1[o] = fmaxf(fmaf(-rho, av, p1[o]), 0.f);
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_warm_start(const float* pred, const Geometry& G, float* Mx, float* My, float* r, float* a,
+                              float* x0, float* x1, const float* p0, const float* p1, float rho, cudaStream_t st) {
+  const long long total = (long long)G.B * G.H * G.W;
+  long long blocks = (total + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  if (blocks < 1) blocks = 1;
+  warm_start_kernel<<<(int)blocks, 256, 0, st>>>(pred, G, Mx, My, r, a, x0, x1, p0, p1, rho);
+  return cudaGetLastError();
+}
+
+}  // namespace otp

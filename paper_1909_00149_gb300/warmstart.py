@@ -1,0 +1,94 @@
+"""Learned warm start of Algorithm 1: data, training and the warm solve.
+
+Sec. III-B warm-starts Algorithm 1 from cached iterates.  Here the cache is
+predicted by the U-Net of ``ot_unet_*`` from the frame pair alone, trained on
+states that the plain solver reaches at its stopping rule.  From the
+predicted state the plain iterations run to the same stopping rule, so the
+network changes the iteration count, never the answer's tolerance.
+
+Everything numerical runs in the library's kernels (the solver, the
+network's forward and backward passes, Adam, the state write of
+``ot_prox_warm_start``); this module only moves tensors into the layouts the
+C calls take: the pair as [n, 2, H, W] and the state as [n, 4, H, W] in the
+order (Mx, My, r, a).
+"""
+from __future__ import annotations
+
+import time
+
+import numpy as np
+
+from . import OtProx, UNet
+
+STATE_CHANNELS = ("Mx", "My", "r", "a")
+
+
+def pair_tensor(p0, p1):
+    """(p0, p1) [n, H, W] each, host or device -> [n, 2, H, W] CUDA tensor."""
+    import torch
+    p0 = torch.as_tensor(p0, dtype=torch.float32).cuda()
+    p1 = torch.as_tensor(p1, dtype=torch.float32).cuda()
+    return torch.stack([p0, p1], 1).contiguous()
+
+
+def solve_targets(p0, p1, chunk: int = 128, **params):
+    """Solve every pair with the plain method (cold start) in chunks of
+    ``chunk`` problems; returns (inputs [n, 2, H, W], targets [n, 4, H, W],
+    iterations per chunk), tensors on the GPU."""
+    import torch
+    n, H, W = np.shape(p0)
+    X = torch.empty((n, 2, H, W), dtype=torch.float32, device="cuda")
+    T = torch.empty((n, 4, H, W), dtype=torch.float32, device="cuda")
+    iters = []
+    for k in range(0, n, chunk):
+        m = min(chunk, n - k)
+        with OtProx(m, H, W, **params) as s:
+            s.set_input(p0[k:k + m], p1[k:k + m])
+            r = s.solve()
+            st = s.get_state()
+        iters.append(r["iters"])
+        X[k:k + m] = pair_tensor(p0[k:k + m], p1[k:k + m])
+        for c, name in enumerate(STATE_CHANNELS):
+            T[k:k + m, c] = st[name]
+    return X, T, iters
+
+
+def train(net: UNet, X, T, epochs: int, batch: int, lr: float = 1e-3, seed: int = 0) -> list[float]:
+    """Adam on the MSE between net(X) and T, cosine-decayed learning rate,
+    shuffled mini-batches; returns the mean loss of each epoch."""
+    import torch
+    n = X.shape[0]
+    g = torch.Generator().manual_seed(seed)
+    steps = epochs * (n // batch)
+    step = 0
+    out = []
+    for _ in range(epochs):
+        perm = torch.randperm(n, generator=g).cuda()
+        losses = []
+        for k in range(0, n - batch + 1, batch):
+            idx = perm[k:k + batch]
+            rate = lr * 0.5 * (1.0 + np.cos(np.pi * step / max(steps, 1)))
+            losses.append(net.train_step(X[idx].contiguous(), T[idx].contiguous(), rate))
+            step += 1
+        out.append(float(np.mean(losses)))
+    return out
+
+
+def solve(p0, p1, net: UNet | None = None, **params) -> dict:
+    """Solve the pairs [B, H, W] to the stopping rule, from the network's
+    prediction when ``net`` is given (its max_batch must cover B), cold
+    otherwise.  Returns the solver's result plus ``seconds`` (host time
+    around prediction + solve, inputs already on the device)."""
+    import torch
+    B, H, W = np.shape(p0)
+    x = pair_tensor(p0, p1) if net is not None else None
+    with OtProx(B, H, W, **params) as s:
+        s.set_input(p0, p1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        if net is not None:
+            s.warm_start(net.forward(x))
+        r = s.solve()
+        torch.cuda.synchronize()
+        r["seconds"] = time.perf_counter() - t0
+    return r
