@@ -23,10 +23,28 @@ Plain definitions, no fusion: conv2d is the direct sum over input channels
 and kernel offsets; its gradients are the same sums with the roles of the
 tensors exchanged.  Pinned in tests/test_oracle_unet.py by central finite
 differences of the loss.
+
+Storage precision.  ``forward`` and ``backward`` take an optional rounding
+``rnd`` applied wherever a mixed-precision implementation stores a tensor in
+a narrower type: every hidden activation (after ReLU), every pooled tensor,
+every data gradient and every summed gradient (upsampling's adjoint, the
+skip plus pooled paths).  The network output, the loss gradient and the
+weight gradients are not rounded.  ``round_bf16`` is the bfloat16 rounding
+(8 significant bits, ties to even); with ``rnd=None`` everything is FP64.
 """
 from __future__ import annotations
 
 import numpy as np
+
+
+def round_bf16(x) -> np.ndarray:
+    """Nearest bfloat16 value (8 significant bits, ties to even), in FP64."""
+    m, e = np.frexp(np.asarray(x, np.float64))      # x = m 2^e, 0.5 <= |m| < 1
+    return np.ldexp(np.rint(m * 256.0), e - 8)
+
+
+def _ident(v):
+    return v
 
 
 def layer_specs(base: int = 32, cin: int = 2, cout: int = 4) -> list[tuple[str, int, int, int]]:
@@ -101,20 +119,21 @@ def up2_grad(g: np.ndarray) -> np.ndarray:
     return g.reshape(n, c, h // 2, 2, w // 2, 2).sum(axis=(3, 5))
 
 
-def forward(params: dict, x: np.ndarray):
+def forward(params: dict, x: np.ndarray, rnd=None):
     """Network output [N, 4, H, W] and the activations the backward pass needs."""
+    rnd = rnd or _ident
     cache = {"x": x}
 
     def cr(name, inp):
         w, b = params[name]
-        y = np.maximum(conv2d(inp, w, b), 0.0)
+        y = rnd(np.maximum(conv2d(inp, w, b), 0.0))
         cache[name] = (inp, y)
         return y
 
     s0 = cr("enc0b", cr("enc0a", x))
-    s1 = cr("enc1b", cr("enc1a", avgpool2(s0)))
-    s2 = cr("enc2b", cr("enc2a", avgpool2(s1)))
-    bt = cr("bottb", cr("botta", avgpool2(s2)))
+    s1 = cr("enc1b", cr("enc1a", rnd(avgpool2(s0))))
+    s2 = cr("enc2b", cr("enc2a", rnd(avgpool2(s1))))
+    bt = cr("bottb", cr("botta", rnd(avgpool2(s2))))
     d2 = cr("dec2b", cr("dec2a", np.concatenate([up2(bt), s2], axis=1)))
     d1 = cr("dec1b", cr("dec1a", np.concatenate([up2(d2), s1], axis=1)))
     d0 = cr("dec0b", cr("dec0a", np.concatenate([up2(d1), s0], axis=1)))
@@ -124,8 +143,9 @@ def forward(params: dict, x: np.ndarray):
     return out, cache
 
 
-def backward(params: dict, cache: dict, g_out: np.ndarray) -> dict:
+def backward(params: dict, cache: dict, g_out: np.ndarray, rnd=None) -> dict:
     """dL/d(params) given dL/d(output)."""
+    rnd = rnd or _ident
     grads = {}
 
     def back(name, gy, relu=True):
@@ -134,7 +154,7 @@ def backward(params: dict, cache: dict, g_out: np.ndarray) -> dict:
             gy = gy * (y > 0)
         gx, gw, gb = conv2d_grads(inp, params[name][0], gy)
         grads[name] = (gw, gb)
-        return gx
+        return rnd(gx)
 
     c8 = params["bottb"][0].shape[0]
     c4 = params["dec2b"][0].shape[0]
@@ -142,14 +162,14 @@ def backward(params: dict, cache: dict, g_out: np.ndarray) -> dict:
     g = back("head", g_out, relu=False)
     g = back("dec0a", back("dec0b", g))
     g_up1, g_s0 = g[:, :c2], g[:, c2:]
-    g = back("dec1a", back("dec1b", up2_grad(g_up1)))
+    g = back("dec1a", back("dec1b", rnd(up2_grad(g_up1))))
     g_up2, g_s1 = g[:, :c4], g[:, c4:]
-    g = back("dec2a", back("dec2b", up2_grad(g_up2)))
+    g = back("dec2a", back("dec2b", rnd(up2_grad(g_up2))))
     g_bt, g_s2 = g[:, :c8], g[:, c8:]
-    g = back("botta", back("bottb", up2_grad(g_bt)))
-    g = back("enc2a", back("enc2b", avgpool2_grad(g) + g_s2))
-    g = back("enc1a", back("enc1b", avgpool2_grad(g) + g_s1))
-    back("enc0a", back("enc0b", avgpool2_grad(g) + g_s0))
+    g = back("botta", back("bottb", rnd(up2_grad(g_bt))))
+    g = back("enc2a", back("enc2b", rnd(avgpool2_grad(g) + g_s2)))
+    g = back("enc1a", back("enc1b", rnd(avgpool2_grad(g) + g_s1)))
+    back("enc0a", back("enc0b", rnd(avgpool2_grad(g) + g_s0)))
     return grads
 
 

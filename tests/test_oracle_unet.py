@@ -65,3 +65,37 @@ def test_backward_matches_finite_differences(seed):
         pp[name] = (w, bm)
         lm = U.mse(U.forward(pp, x)[0], t)[0]
         assert abs(grads[name][1][k] - (lp - lm) / (2 * eps)) <= 1e-6 * max(1.0, abs((lp - lm) / (2 * eps)))
+
+
+def test_round_bf16_matches_torch_conversion():
+    """The oracle's bfloat16 rounding against PyTorch's float32 -> bfloat16
+    conversion (round to nearest even) on values of many magnitudes."""
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(3)
+    x = (rng.normal(size=20000) * np.exp(rng.uniform(-20, 20, 20000))).astype(np.float32)
+    want = torch.from_numpy(x).to(torch.bfloat16).to(torch.float64).numpy()
+    assert np.array_equal(U.round_bf16(x), want)
+
+
+def test_round_bf16_ties_go_to_even():
+    one = 1.0
+    assert U.round_bf16(one + 2.0 ** -8) == 1.0                 # halfway to 1 + 2^-7: even is 1
+    assert U.round_bf16(one + 3 * 2.0 ** -8) == 1.0 + 2.0 ** -6  # halfway: even is 1 + 2^-6
+    assert U.round_bf16(-(one + 2.0 ** -8)) == -1.0
+    assert U.round_bf16(0.0) == 0.0
+    v = np.array([0.5, 1.0 + 2.0 ** -7, -3.0, 2.0 ** -100])
+    assert np.array_equal(U.round_bf16(v), v)                   # already 8 significant bits
+    assert U.round_bf16(1.0 + 2.0 ** -9) == 1.0
+
+
+def test_rounded_network_stays_near_fp64():
+    """Storage rounding perturbs the output by about the bfloat16 unit
+    roundoff (2^-9) per stored tensor: visibly, but far below O(1)."""
+    rng = np.random.default_rng(4)
+    params = U.init_params(rng, 2)
+    params = {k: (w, rng.normal(0, 0.1, b.shape)) for k, (w, b) in params.items()}
+    x = rng.normal(size=(2, 2, 16, 16))
+    y64, _ = U.forward(params, x)
+    y16, _ = U.forward(params, x, rnd=U.round_bf16)
+    e = np.linalg.norm(y16 - y64) / np.linalg.norm(y64)
+    assert 1e-5 < e < 2e-2
