@@ -2,7 +2,7 @@
 """Benchmark of the unbalanced Beckmann-OT proximal hot path on GB300.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload rpca|prox] [--n-inner I]
+                    [--workload rpca|prox|batch|warmstart] [--n-inner I]
 
 Prints ONE JSON line (rank 0).  Workloads (synthetic, seeded):
 
@@ -63,8 +63,9 @@ def measured_peaks() -> dict:
     if os.path.exists(path):
         with open(path) as f:
             d = json.load(f)
-        return {"hbm_gbs": d["hbm_gbs"], "sm_max_mhz": d.get("sm_max_mhz", 2070.0), "source": "measured"}
-    return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0, "source": "fallback"}
+        return {"hbm_gbs": d["hbm_gbs"], "bf16_tflops": d.get("bf16_tflops", 1900.0),
+                "sm_max_mhz": d.get("sm_max_mhz", 2070.0), "source": "measured"}
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0, "source": "fallback"}
 
 
 def jacobi_flops(T: int, rounds: int) -> float:
@@ -545,13 +546,132 @@ def run_ours_batch(args, rank, world, local_rank):
     }
 
 
+UNET_MACS_PER_PIXEL = 161984   # multiply-adds of the warm-start U-Net's forward pass per full-resolution pixel
+
+
+def warmstart_pairs(seed: int, n: int, S: int):
+    """n consecutive-frame pairs of 17-frame S x S blob videos (config-1
+    blobs and moves, 3-8 blobs a video): the evaluation's distribution."""
+    from synth import blob_video, rng_for
+    rng = rng_for(5, seed)
+    p0s, p1s = [], []
+    for k in range(0, n, 16):
+        v = blob_video(rng, 17, S, S, n_blobs=int(rng.integers(3, 9)))
+        m = min(16, n - k)
+        p0s.append(v[:m])
+        p1s.append(v[1:m + 1])
+    return np.concatenate(p0s), np.concatenate(p1s)
+
+
+def run_ours_warmstart(args, rank, world, local_rank):
+    """The learned warm start (config 5, scaled): train the U-Net with the
+    library's kernels on pairs the plain solver takes to 1e-5, then solve every
+    frame pair of a T-frame blob video at the evaluation size from zero and
+    from the network's prediction, both to the same 1e-5 stopping rule.  A
+    step is one solve of all pairs; value = warm-start time to the tolerance."""
+    import torch
+    import paper_1909_00149_gb300 as otp
+    from paper_1909_00149_gb300 import warmstart as WS
+    from synth import blob_video, rng_for
+    torch.cuda.set_device(local_rank)
+    kw = dict(mode="prox", mu=PROX_KW["mu"], rho=PROX_KW["rho"], tol=1e-5, max_iter=100000, check_every=10)
+    S, ntr, E = args.ws_train_size, args.ws_train_pairs, args.ws_epochs
+    t0 = time.perf_counter()
+    p0, p1 = warmstart_pairs(1000 + rank, ntr, S)
+    t_gen = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    X, T, its = WS.solve_targets(p0, p1, **kw)
+    torch.cuda.synchronize()
+    t_solve = time.perf_counter() - t0
+    net = otp.UNet(S, S, 16, 32, bias_free=args.ws_bias_free)
+    net.init(seed=0)
+    t0 = time.perf_counter()
+    losses = WS.train(net, X, T, epochs=E, batch=16, lr=1e-3)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    del X, T
+    Se, Te = args.ws_eval_size, args.ws_eval_frames
+    v = blob_video(rng_for(5, 5000 + rank), Te, Se, Se)
+    q0, q1 = v[:-1].copy(), v[1:].copy()
+    B = Te - 1
+    ev = otp.UNet(Se, Se, B, 32)
+    ev.set_params(net.get_params())
+    x = WS.pair_tensor(q0, q1)
+    pred = torch.empty((B, 4, Se, Se), dtype=torch.float32, device="cuda")
+    d0, d1 = torch.from_numpy(q0).cuda(), torch.from_numpy(q1).cuda()
+    ev_s, ev_e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def solve(warm: bool, gate: float = args.ws_gate):
+        with otp.OtProx(B, Se, Se, **kw) as s:
+            s.set_input(d0, d1)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            if warm:
+                ev_s.record()
+                ev.forward(x, out=pred)
+                ev_e.record()
+                s.warm_start(pred, gate)
+            r = s.solve()
+            torch.cuda.synchronize()
+            r["seconds"] = time.perf_counter() - t0
+            r["forward_ms"] = ev_s.elapsed_time(ev_e) if warm else 0.0
+        return r
+
+    for _ in range(args.warmup if args.warmup < 3 else 1):
+        solve(False), solve(True)
+    sampler = ClockSampler(local_rank)
+    sampler.start()
+    cold = [solve(False) for _ in range(args.steps)]
+    warm = [solve(True) for _ in range(args.steps)]
+    clocks = sampler.stop()
+    sweep = {}
+    for g in (float(v) for v in args.ws_gate_sweep.split(",") if v):
+        r = solve(True, g)
+        sweep[str(g)] = {"iters": r["iters"], "seconds": r["seconds"], "status": r["status"]}
+    tc = statistics.median(r["seconds"] for r in cold)
+    tw = statistics.median(r["seconds"] for r in warm)
+    fwd_ms = statistics.median(r["forward_ms"] for r in warm)
+    fl = 2.0 * UNET_MACS_PER_PIXEL * B * Se * Se
+    peaks = measured_peaks()
+    achieved = fl / (fwd_ms * 1e-3) / 1e12
+    return {
+        "metric": "time to the 1e-5 stopping rule, learned warm start (U-Net forward + Algorithm 1)",
+        "value": tw, "unit": "s", "n_gpus": world, "steps": args.steps, "warmup": 1, "ms_per_step": tw * 1e3,
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32 solver, bf16 network",
+        "data": "synthetic",
+        "config": {"workload": f"warmstart: train on {ntr} config-1 pairs at {S}x{S} (3-8 blobs), evaluate on the "
+                               f"{B} pairs of a {Te}-frame {Se}x{Se} blob video", **kw,
+                   "epochs": E, "batch": 16, "bias_free": args.ws_bias_free, "l2": "inputs larger than L2"},
+        "cold": {"seconds": tc, "iters": cold[0]["iters"], "status": cold[0]["status"]},
+        "warm": {"seconds": tw, "iters": warm[0]["iters"], "status": warm[0]["status"],
+                 "res_pri": warm[0]["res_pri"], "res_fp": warm[0]["res_fp"], "forward_ms": fwd_ms},
+        "speedup_time": tc / tw, "speedup_iters": cold[0]["iters"] / max(warm[0]["iters"], 1),
+        "gate": args.ws_gate, "gate_sweep": sweep,
+        "training": {"gen_s": t_gen, "solve_s": t_solve, "train_s": t_train, "target_iters": its[:4],
+                     "loss_per_epoch": [float(f"{l:.4g}") for l in losses]},
+        "roofline": {"bound": "tensor", "achieved": achieved, "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
+                     "frac": achieved / peaks["bf16_tflops"], "traffic": None,
+                     "kernel": "U-Net forward (13 tcgen05 convolutions + CUDA-core layers), whole pass",
+                     "peak_source": peaks["source"] + " bf16 (of measured)"},
+        "gpu_launches": None, "e2e": None, "clocks": clocks,
+    }
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["rpca", "prox", "batch"], default="rpca")
+    ap.add_argument("--workload", choices=["rpca", "prox", "batch", "warmstart"], default="rpca")
+    ap.add_argument("--ws-train-size", type=int, default=128)
+    ap.add_argument("--ws-train-pairs", type=int, default=4096)
+    ap.add_argument("--ws-epochs", type=int, default=8)
+    ap.add_argument("--ws-eval-size", type=int, default=512)
+    ap.add_argument("--ws-eval-frames", type=int, default=128)
+    ap.add_argument("--ws-bias-free", action="store_true", help="train without biases")
+    ap.add_argument("--ws-gate", type=float, default=1e-3, help="warm-start mass gate (0: none)")
+    ap.add_argument("--ws-gate-sweep", default="", help="comma-separated gates to report as well")
     ap.add_argument("--n-inner", type=int, default=1)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -567,7 +687,8 @@ def main():
             import torch
             torch.cuda.set_device(local_rank)
             torch.distributed.init_process_group("nccl")
-        run = {"rpca": run_ours_rpca, "prox": run_ours_prox, "batch": run_ours_batch}[args.workload]
+        run = {"rpca": run_ours_rpca, "prox": run_ours_prox, "batch": run_ours_batch,
+               "warmstart": run_ours_warmstart}[args.workload]
         line = run(args, rank, world, local_rank)
         if world > 1:
             import torch

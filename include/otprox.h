@@ -190,8 +190,11 @@ int ot_prox_set_state(ot_prox_t h, const float* Mx, const float* My, const float
  * Mx, My, r (unless balanced) and a are copied in, the flux zeroed on the
  * slots without an edge; each free x is set from its step's fixed point
  * given a: x0 = max(p0 + rho a, 0), x1 = max(p1 - rho a, 0) (the inputs
- * must be set).  Stream-ordered, no sync. */
-int ot_prox_warm_start(ot_prox_t h, const float* pred);
+ * must be set).  gate > 0 takes the prediction only at pixels where p0 + p1
+ * exceeds gate somewhere in the 5 x 5 neighbourhood; elsewhere the state is
+ * written as for a zero prediction (M = r = a = 0, x = p).  gate = 0 takes
+ * it everywhere.  Stream-ordered, no sync. */
+int ot_prox_warm_start(ot_prox_t h, const float* pred, double gate);
 
 /* Zero the state (Algorithm 2 line 2 initialises the prox state to 0). */
 int ot_prox_reset(ot_prox_t h);
@@ -422,6 +425,11 @@ int64_t ot_unet_param_count(ot_unet_t h);
 /* Load parameters (resets the optimiser state).  Synchronises. */
 int ot_unet_set_params(ot_unet_t h, const float* params);
 int ot_unet_get_params(ot_unet_t h, float* params);
+/* bias_free = 1: report every bias gradient as 0, so training keeps the
+ * biases at their values (zero after ot_unet_set_params with zero biases).
+ * A bias-free network maps an all-zero neighbourhood to exactly 0 (every
+ * layer is positively homogeneous), which is the converged state there. */
+int ot_unet_set_bias_free(ot_unet_t h, int32_t bias_free);
 /* y = net(x) for n <= max_batch inputs.  Synchronises. */
 int ot_unet_forward(ot_unet_t h, const float* x, float* y, int32_t n);
 /* Mean squared error between net(x) and target [n][4][H][W] (loss, optional)

@@ -181,14 +181,15 @@ class OtProx:
         check(_lib.ot_prox_set_state(self.h, A.ptr(Mx), A.ptr(My), A.ptr(x0), A.ptr(x1), A.ptr(r), A.ptr(a)),
               "ot_prox_set_state")
 
-    def warm_start(self, pred):
+    def warm_start(self, pred, gate: float = 0.0):
         """Warm state from a prediction [B, 4, H, W] (Mx, My, r, a) CUDA
-        tensor, x from the x-step's fixed point (ot_prox_warm_start)."""
+        tensor, x from the x-step's fixed point; with gate > 0 only near
+        mass (ot_prox_warm_start)."""
         import torch
         if not (isinstance(pred, torch.Tensor) and pred.is_cuda and pred.dtype == torch.float32
                 and pred.is_contiguous() and pred.numel() == 4 * self.n):
             raise ValueError("pred must be a contiguous float32 CUDA tensor of B x 4 x H x W values")
-        check(_lib.ot_prox_warm_start(self.h, pred.data_ptr()), "ot_prox_warm_start")
+        check(_lib.ot_prox_warm_start(self.h, pred.data_ptr(), float(gate)), "ot_prox_warm_start")
 
 
 def rpca_default_params(**kw) -> "_abi.ot_rpca_params":
@@ -428,7 +429,8 @@ class UNet:
     the order of :func:`unet_layer_specs` (weights [co, ci, k, k], then
     biases [co], per layer)."""
 
-    def __init__(self, H: int, W: int, max_batch: int, base_channels: int = 32, stream=None):
+    def __init__(self, H: int, W: int, max_batch: int, base_channels: int = 32, stream=None,
+                 bias_free: bool = False):
         self.H, self.W, self.max_batch, self.base = int(H), int(W), int(max_batch), int(base_channels)
         h = ctypes.c_void_p()
         self._stream = _stream_handle(stream)
@@ -436,6 +438,7 @@ class UNet:
               "ot_unet_create")
         self.h = h
         self.n_params = int(_lib.ot_unet_param_count(self.h))
+        check(_lib.ot_unet_set_bias_free(self.h, int(bool(bias_free))), "ot_unet_set_bias_free")
 
     def close(self):
         if getattr(self, "h", None):

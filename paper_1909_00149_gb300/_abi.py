@@ -149,12 +149,13 @@ PROTOTYPES = [
     ("ot_uotdf_reset", ctypes.c_int, [ctypes.c_void_p]),
     ("ot_uotdf_get_params", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ot_uotdf_params)]),
     ("ot_uotdf_destroy", ctypes.c_int, [ctypes.c_void_p]),
-    ("ot_prox_warm_start", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    ("ot_prox_warm_start", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double]),
     ("ot_unet_create", ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
                                       ctypes.POINTER(ctypes.c_void_p)]),
     ("ot_unet_param_count", ctypes.c_int64, [ctypes.c_void_p]),
     ("ot_unet_set_params", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     ("ot_unet_get_params", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    ("ot_unet_set_bias_free", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
     ("ot_unet_forward", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32]),
     ("ot_unet_gradients", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
                                          ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),

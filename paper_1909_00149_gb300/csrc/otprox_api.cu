@@ -626,12 +626,14 @@ int ot_prox_set_state(ot_prox_t h, const float* Mx, const float* My, const float
   return restart_projection(h);
 }
 
-int ot_prox_warm_start(ot_prox_t h, const float* pred) {
+int ot_prox_warm_start(ot_prox_t h, const float* pred, double gate) {
   if (!h || !pred) return fail(OT_EINVAL, "ot_prox_warm_start: NULL argument");
+  if (!(gate >= 0.0)) return fail(OT_EINVAL, "ot_prox_warm_start: gate must be >= 0");
   const int c = h->cur;
   const bool fx0 = h->prm.mode != OT_MODE_PROX, fx1 = h->prm.mode == OT_MODE_EVAL;
   OT_CUDA(launch_warm_start(pred, h->G, h->Mx[c], h->My[c], h->prm.balanced ? nullptr : h->r, h->a[c],
-                            fx0 ? nullptr : h->x0, fx1 ? nullptr : h->x1, h->p0, h->p1, (float)h->prm.rho, h->stream),
+                            fx0 ? nullptr : h->x0, fx1 ? nullptr : h->x1, h->p0, h->p1, (float)h->prm.rho, (float)gate,
+                            h->stream),
           "ot_prox_warm_start");
   return restart_projection(h);
 }

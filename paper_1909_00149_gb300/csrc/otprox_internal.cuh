@@ -119,9 +119,11 @@ int encode_plane_map(CUtensorMap* map, const float* base, const Geometry& g, int
 int tma_box(int which, int* w, int* h);
 
 // Solver planes from a predicted state pred [B][4][H][W] (Mx, My, r, a);
-// r, x0, x1 may be null (not a variable); warm_start.cu.
+// r, x0, x1 may be null (not a variable); gate > 0 keeps the prediction only
+// near mass (warm_start.cu).
 cudaError_t launch_warm_start(const float* pred, const Geometry& G, float* Mx, float* My, float* r, float* a,
-                              float* x0, float* x1, const float* p0, const float* p1, float rho, cudaStream_t st);
+                              float* x0, float* x1, const float* p0, const float* p1, float rho, float gate,
+                              cudaStream_t st);
 
 // Sum partials[n][kNumSums] in a fixed order into out[kNumSums].
 cudaError_t launch_finalize_sums(const double* partials, int n, double* out, cudaStream_t st);

@@ -432,12 +432,14 @@ wgrad_kernel(const void* __restrict__ xa, int ca, const void* __restrict__ xb, i
 }
 
 // g[i] = sum_{z < S} ws[z][i] in order of z (a layer's weights and biases
-// are contiguous in the flat parameter layout, as in ws).
-__global__ void wgrad_reduce_kernel(const float* __restrict__ ws, int S, long long stride, float* __restrict__ g) {
+// are contiguous in the flat parameter layout, as in ws); the bias entries
+// (i >= nweights) are reported as 0 when the network is trained bias-free.
+__global__ void wgrad_reduce_kernel(const float* __restrict__ ws, int S, long long stride, long long nweights,
+                                    int bias_free, float* __restrict__ g) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < stride; i += (long long)gridDim.x * blockDim.x) {
     float s = 0.f;
     for (int z = 0; z < S; ++z) s += ws[z * stride + i];
-    g[i] = s;
+    g[i] = (bias_free && i >= nweights) ? 0.f : s;
   }
 }
 
@@ -617,8 +619,12 @@ struct ot_unet {
   LayerDev* dL;
   CUtensorMap wf_map[15], wd_map[15];
   int nf_out[15], nd_out[15];
-  bf16* act_slab;
-  float* f_slab;
+  bf16* act_slab;              // forward activations
+  float* f_slab;                // input, output
+  bf16* grad_slab;              // activation gradients (allocated by the first gradient call)
+  float* gf_slab;               // loss gradient, target
+  bool bwd;
+  int bias_free;                // 1: bias gradients are 0 (biases keep their values)
   Act A[NBUF];
   float* F[NFBUF];
   float* ws;                    // weight-gradient partials
@@ -753,8 +759,9 @@ cudaError_t wgrad_raw(ot_unet* h, int l, const void* xa, int ca, const void* xb,
   const int S = wgrad_splits(d, n, Hh, Ww);
   const dim3 grid((d.co + kCO - 1) / kCO, (d.ci + kCI - 1) / kCI, S);
   wgrad_kernel<KS, XF32, GF32><<<grid, kCT * kCT, 0, h->stream>>>(xa, ca, xb, cb, n, Hh, Ww, gy, d.co, h->ws);
-  const long long stride = (long long)d.co * d.ci * d.ks * d.ks + d.co;
-  wgrad_reduce_kernel<<<grid_for(stride), 256, 0, h->stream>>>(h->ws, S, stride, h->g + d.w_off);
+  const long long nweights = (long long)d.co * d.ci * d.ks * d.ks;
+  wgrad_reduce_kernel<<<grid_for(nweights + d.co), 256, 0, h->stream>>>(h->ws, S, nweights + d.co, nweights,
+                                                                        h->bias_free, h->g + d.w_off);
   return cudaGetLastError();
 }
 
@@ -902,6 +909,57 @@ int read_loss(ot_unet* h, double* loss, long long count) {
   return OT_OK;
 }
 
+// Allocate (zeroed) and map the BF16 buffers [b0, b1) and the FP32 buffers
+// [f0, f1) for max_batch images, one slab each.
+int alloc_buffers(ot_unet* h, int b0, int b1, int f0, int f1, bf16** slab, float** fslab) {
+  const long long hw = (long long)h->H * h->W;
+  const int fch[NFBUF] = {2, 4, 4, 4};
+  long long act = 0, fl = 0;
+  for (int b = b0; b < b1; ++b)
+    act += ((long long)h->maxN * (h->H >> kBufL[b]) * (h->W >> kBufL[b]) * kBufC[b] * h->C + 63) / 64 * 64;
+  for (int b = f0; b < f1; ++b) fl += ((long long)h->maxN * fch[b] * hw + 63) / 64 * 64;
+  cudaError_t e = cudaMalloc(slab, (size_t)act * sizeof(bf16));
+  if (e == cudaSuccess) e = cudaMalloc(fslab, (size_t)fl * sizeof(float));
+  if (e == cudaSuccess) e = cudaMemsetAsync(*slab, 0, (size_t)act * sizeof(bf16), h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(*fslab, 0, (size_t)fl * sizeof(float), h->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "unet: activation buffers");
+  bf16* q = *slab;
+  for (int b = b0; b < b1; ++b) {
+    Act& a = h->A[b];
+    a.p = q;
+    a.C = kBufC[b] * h->C;
+    a.level = kBufL[b];
+    q += ((long long)h->maxN * (h->H >> a.level) * (h->W >> a.level) * a.C + 63) / 64 * 64;
+    if (encode_act(a, h->maxN, h->H >> a.level, h->W >> a.level))
+      return fail(OT_ECUDA, "unet: tensor map of an activation buffer");
+  }
+  float* fq = *fslab;
+  for (int b = f0; b < f1; ++b) {
+    h->F[b] = fq;
+    fq += ((long long)h->maxN * fch[b] * hw + 63) / 64 * 64;
+  }
+  return OT_OK;
+}
+
+// The gradient buffers and the weight-gradient workspace, on first use.
+int ensure_backward(ot_unet* h) {
+  if (h->bwd) return OT_OK;
+  int rc = alloc_buffers(h, G_D0, NBUF, G_OUT, NFBUF, &h->grad_slab, &h->gf_slab);
+  if (rc != OT_OK) return rc;
+  long long ws = 0;   // the largest split count any layer can take times that layer's size
+  for (const LayerDev& d : h->L) {
+    const long long ctas = (long long)((d.co + kCO - 1) / kCO) * ((d.ci + kCI - 1) / kCI);
+    long long sp = (2 * 152 + ctas - 1) / ctas;
+    if (sp > kMaxSplits) sp = kMaxSplits;
+    const long long need = sp * ((long long)d.co * d.ci * d.ks * d.ks + d.co);
+    if (need > ws) ws = need;
+  }
+  const cudaError_t e = cudaMalloc(&h->ws, (size_t)ws * sizeof(float));
+  if (e != cudaSuccess) return cuda_fail(e, "unet: weight-gradient workspace");
+  h->bwd = true;
+  return OT_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -913,6 +971,8 @@ int ot_unet_destroy(ot_unet_t h) {
   cudaFree(h->dL);
   cudaFree(h->act_slab);
   cudaFree(h->f_slab);
+  cudaFree(h->grad_slab);
+  cudaFree(h->gf_slab);
   cudaFree(h->partials);
   cudaFree(h->ws);
   cudaFree(h->derr);
@@ -955,28 +1015,10 @@ int ot_unet_create(int32_t H, int32_t W, int32_t max_batch, int32_t base_channel
   }
   h->nparams = off;
   h->nw = wboff;
-  long long act = 0;
-  for (int b = 0; b < NBUF; ++b)
-    act += ((long long)max_batch * (H >> kBufL[b]) * (W >> kBufL[b]) * kBufC[b] * C + 63) / 64 * 64;
-  const long long hw = (long long)H * W;
-  const long long fsz[NFBUF] = {max_batch * 2 * hw, max_batch * 4 * hw, max_batch * 4 * hw, max_batch * 4 * hw};
-  long long fl = 0;
-  for (long long s : fsz) fl += (s + 63) / 64 * 64;
-  long long ws = 0;   // the largest split count any layer can take times that layer's size
-  for (const LayerDev& d : h->L) {
-    const long long ctas = (long long)((d.co + kCO - 1) / kCO) * ((d.ci + kCI - 1) / kCI);
-    long long sp = (2 * 152 + ctas - 1) / ctas;
-    if (sp > kMaxSplits) sp = kMaxSplits;
-    const long long need = sp * ((long long)d.co * d.ci * d.ks * d.ks + d.co);
-    if (need > ws) ws = need;
-  }
   cudaError_t e = cudaMalloc(&h->p, 4 * (size_t)off * sizeof(float));
   if (e == cudaSuccess) e = cudaMalloc(&h->wb, 3 * (size_t)wboff * sizeof(bf16));
   if (e == cudaSuccess) e = cudaMalloc(&h->dL, h->L.size() * sizeof(LayerDev));
-  if (e == cudaSuccess) e = cudaMalloc(&h->act_slab, (size_t)act * sizeof(bf16));
-  if (e == cudaSuccess) e = cudaMalloc(&h->f_slab, (size_t)fl * sizeof(float));
   if (e == cudaSuccess) e = cudaMalloc(&h->partials, ((size_t)152 * 8 + 1) * kNumSums * sizeof(double));
-  if (e == cudaSuccess) e = cudaMalloc(&h->ws, (size_t)ws * sizeof(float));
   if (e == cudaSuccess) e = cudaMalloc(&h->derr, sizeof(int));
   if (e == cudaSuccess) e = cudaMallocHost(&h->hsums, kNumSums * sizeof(double));
   if (e == cudaSuccess) e = cudaMallocHost(&h->herr, sizeof(int));
@@ -984,8 +1026,6 @@ int ot_unet_create(int32_t H, int32_t W, int32_t max_batch, int32_t base_channel
   if (e == cudaSuccess) e = cudaMemsetAsync(h->wb, 0, 3 * (size_t)wboff * sizeof(bf16), h->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(h->dL, h->L.data(), h->L.size() * sizeof(LayerDev), cudaMemcpyHostToDevice, h->stream);
-  if (e == cudaSuccess) e = cudaMemsetAsync(h->act_slab, 0, (size_t)act * sizeof(bf16), h->stream);
-  if (e == cudaSuccess) e = cudaMemsetAsync(h->f_slab, 0, (size_t)fl * sizeof(float), h->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->derr, 0, sizeof(int), h->stream);
   if (e != cudaSuccess) {
     ot_unet_destroy(h);
@@ -998,22 +1038,10 @@ int ot_unet_create(int32_t H, int32_t W, int32_t max_batch, int32_t base_channel
   h->wf = h->wb + wboff;
   h->wd = h->wf + wboff;
   h->dsums = h->partials + (size_t)152 * 8 * kNumSums;
-  bf16* q = h->act_slab;
-  for (int b = 0; b < NBUF; ++b) {
-    Act& a = h->A[b];
-    a.p = q;
-    a.C = kBufC[b] * C;
-    a.level = kBufL[b];
-    q += ((long long)max_batch * (H >> a.level) * (W >> a.level) * a.C + 63) / 64 * 64;
-    if (encode_act(a, max_batch, H >> a.level, W >> a.level)) {
-      ot_unet_destroy(h);
-      return fail(OT_ECUDA, "ot_unet_create: tensor map of an activation buffer");
-    }
-  }
-  float* fq = h->f_slab;
-  for (int b = 0; b < NFBUF; ++b) {
-    h->F[b] = fq;
-    fq += (fsz[b] + 63) / 64 * 64;
+  const int rc = alloc_buffers(h, 0, G_D0, X_IN, G_OUT, &h->act_slab, &h->f_slab);
+  if (rc != OT_OK) {
+    ot_unet_destroy(h);
+    return rc;
   }
   for (int l = 1; l <= 13; ++l) {
     const LayerDev& d = h->L[l];
@@ -1055,6 +1083,12 @@ int ot_unet_get_params(ot_unet_t h, float* params) {
   return OT_OK;
 }
 
+int ot_unet_set_bias_free(ot_unet_t h, int32_t bias_free) {
+  if (!h) return fail(OT_EINVAL, "ot_unet_set_bias_free: NULL handle");
+  h->bias_free = bias_free ? 1 : 0;
+  return OT_OK;
+}
+
 int ot_unet_forward(ot_unet_t h, const float* x, float* y, int32_t n) {
   if (!h || !x || !y) return fail(OT_EINVAL, "ot_unet_forward: NULL argument");
   if (n < 1 || n > h->maxN) return fail(OT_EINVAL, "ot_unet_forward: batch must be in [1, %d]", h->maxN);
@@ -1070,6 +1104,8 @@ int ot_unet_forward(ot_unet_t h, const float* x, float* y, int32_t n) {
 int ot_unet_gradients(ot_unet_t h, const float* x, const float* target, int32_t n, float* grads, double* loss) {
   if (!h || !x || !target) return fail(OT_EINVAL, "ot_unet_gradients: NULL argument");
   if (n < 1 || n > h->maxN) return fail(OT_EINVAL, "ot_unet_gradients: batch must be in [1, %d]", h->maxN);
+  const int rc = ensure_backward(h);
+  if (rc != OT_OK) return rc;
   const long long hw = (long long)h->H * h->W;
   OT_CUDA(cudaMemcpyAsync(h->F[X_IN], x, (size_t)n * 2 * hw * sizeof(float), cudaMemcpyDefault, h->stream),
           "ot_unet_gradients: input");

@@ -74,11 +74,12 @@ def train(net: UNet, X, T, epochs: int, batch: int, lr: float = 1e-3, seed: int 
     return out
 
 
-def solve(p0, p1, net: UNet | None = None, **params) -> dict:
+def solve(p0, p1, net: UNet | None = None, gate: float = 0.0, **params) -> dict:
     """Solve the pairs [B, H, W] to the stopping rule, from the network's
-    prediction when ``net`` is given (its max_batch must cover B), cold
-    otherwise.  Returns the solver's result plus ``seconds`` (host time
-    around prediction + solve, inputs already on the device)."""
+    prediction when ``net`` is given (its max_batch must cover B; ``gate`` as
+    in ``OtProx.warm_start``), cold otherwise.  Returns the solver's result
+    plus ``seconds`` (host time around prediction + solve, inputs already on
+    the device)."""
     import torch
     B, H, W = np.shape(p0)
     x = pair_tensor(p0, p1) if net is not None else None
@@ -87,7 +88,7 @@ def solve(p0, p1, net: UNet | None = None, **params) -> dict:
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         if net is not None:
-            s.warm_start(net.forward(x))
+            s.warm_start(net.forward(x), gate)
         r = s.solve()
         torch.cuda.synchronize()
         r["seconds"] = time.perf_counter() - t0

@@ -227,3 +227,22 @@ def test_exact_network_gradients(lib):
     for name, _, _, _ in U.layer_specs(BASE):
         for j in (0, 1):
             assert rel(got[name][j], grads[name][j]) <= 1e-4, (name, j, rel(got[name][j], grads[name][j]))
+
+
+def test_bias_free_training_keeps_zero_biases_and_a_zero_far_field(lib):
+    """Bias-free: every bias gradient is reported as 0, so Adam leaves the
+    zero biases alone, and an all-zero neighbourhood maps to exactly 0."""
+    S = 256
+    rng = np.random.default_rng(9)
+    x = np.zeros((2, 2, S, S), np.float32)
+    x[:, :, :24, :24] = rng.random((2, 2, 24, 24))
+    t = rng.normal(size=(2, 4, S, S)).astype(np.float32) * (x[:, :1] > 0)
+    with lib.UNet(S, S, 2, BASE, bias_free=True) as net:
+        net.init(seed=1)
+        for _ in range(3):
+            net.train_step(x, t, 1e-3)
+        params = unflat(net.get_params(), BASE)
+        y = net.forward(x).cpu().numpy()
+    assert all(np.all(b == 0) for _, b in params.values())
+    assert np.count_nonzero(y[:, :, :24, :24]) > 0
+    assert np.all(y[:, :, 128:, :] == 0) and np.all(y[:, :, :, 128:] == 0)

@@ -30,6 +30,32 @@ def pairs(seed, n, S, nb=None):
     return np.concatenate(p0s), np.concatenate(p1s)
 
 
+def test_warm_start_gate_keeps_the_prediction_only_near_mass(lib):
+    """gate > 0: where p0 + p1 stays at or below the gate in the 5 x 5
+    neighbourhood the state is that of a zero prediction (x = p); elsewhere
+    the prediction's."""
+    B, H, W, rho, gate = 2, 24, 32, 0.01, 1e-3
+    p0 = np.zeros((B, H, W), np.float32)
+    p1 = np.zeros((B, H, W), np.float32)
+    p0[:, 5, 6] = 1.0
+    p1[:, 15, 20] = 0.5
+    p1[:, 20, 3] = 0.5 * gate          # below the gate: no effect
+    pred = np.random.default_rng(1).normal(size=(B, 4, H, W)).astype(np.float32)
+    with lib.OtProx(B, H, W, mode="prox", mu=3.0, rho=rho) as s:
+        s.set_input(p0, p1)
+        s.warm_start(torch.from_numpy(pred).cuda(), gate)
+        st = {k: v.cpu().numpy() for k, v in s.get_state().items()}
+    near = np.zeros((B, H, W), bool)
+    for (i, j) in ((5, 6), (15, 20)):
+        near[:, max(i - 2, 0):i + 3, max(j - 2, 0):j + 3] = True
+    assert np.array_equal(st["a"], np.where(near, pred[:, 3], 0))
+    assert np.array_equal(st["r"], np.where(near, pred[:, 2], 0))
+    mx = np.where(near, pred[:, 0], 0)
+    mx[:, H - 1, :] = 0
+    assert np.array_equal(st["Mx"], mx)
+    assert np.array_equal(st["x0"][~near], p0[~near]) and np.array_equal(st["x1"][~near], p1[~near])
+
+
 @pytest.mark.parametrize("mode", ["prox", "fixed_first", "eval"])
 def test_warm_start_writes_the_state(lib, mode):
     B, H, W, rho = 3, 21, 34, 0.37
@@ -98,7 +124,7 @@ def test_trained_network_needs_fewer_iterations_than_a_cold_start(lib):
     ev.set_params(net.get_params())
     q0, q1 = pairs(99, 128, S)
     cold = WS.solve(q0, q1, **KW)
-    warm = WS.solve(q0, q1, net=ev, **KW)
+    warm = WS.solve(q0, q1, net=ev, gate=1e-3, **KW)
     print(f"\ncold {cold['iters']} iterations, warm {warm['iters']} iterations")
     assert cold["status"] == 0 and warm["status"] == 0
     assert warm["res_pri"] <= 1e-5 and warm["res_fp"] <= 1e-5
