@@ -251,8 +251,9 @@ class Rpca:
         return r.as_dict()
 
     def step_profiled(self) -> list:
-        """One outer iteration; device ms of its six phases (see the C header)."""
-        ms = (ctypes.c_double * 6)()
+        """Two outer iterations; device ms of their seven phases (see the C
+        header: pre, Gram, eigensolver, apply, prox, post, fused post + pre)."""
+        ms = (ctypes.c_double * 7)()
         check(_lib.ot_rpca_step_profiled(self.h, ms), "ot_rpca_step_profiled")
         return list(ms)
 

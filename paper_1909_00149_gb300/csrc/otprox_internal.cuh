@@ -193,6 +193,9 @@ int rpca_num_blocks(const RpcaGeom& g);
 cudaError_t rpca_launch_pre(const RpcaGeom& g, const RpcaCoeffs& c, const RpcaPlanes& P, double* partials,
                             cudaStream_t st);
 cudaError_t rpca_launch_post(const RpcaGeom& g, const RpcaPlanes& P, double* partials, cudaStream_t st);
+// post of outer iteration k and pre of k + 1 in one pass (slot 0 sums only)
+cudaError_t rpca_launch_post_pre(const RpcaGeom& g, const RpcaCoeffs& c, const RpcaPlanes& P, double* partials,
+                                 cudaStream_t st);
 cudaError_t rpca_launch_sumsq(const RpcaGeom& g, const float* Y, double* partials, cudaStream_t st);
 
 // ----------------------------------------------------------------- SVT

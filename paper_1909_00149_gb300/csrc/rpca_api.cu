@@ -47,7 +47,7 @@ struct ot_rpca {
   int warm;
   // residual sums
   int nb_rpca, nb_apply;
-  double* partials;          // [2 * nb_rpca + nb_apply][kNumSums]
+  double* partials;          // [3 * nb_rpca + nb_apply][kNumSums]: pre (parity 0), post, pre (parity 1)
   double* dsums;             // [kNumSums]
   double* hsums;             // pinned: [kNumSums] sums, then sweeps (as int) and sigma
   double y_norm;
@@ -189,10 +189,10 @@ int ot_rpca_create(const ot_rpca_params* params, void* cuda_stream, ot_rpca_t* o
     h->Wm = h->V + (size_t)TP * TP;
     h->sig = h->Wm + (size_t)TP * TP;
     h->sweeps = reinterpret_cast<int*>(h->sig + (size_t)TP * TP);
-    e = cudaMalloc(&h->partials, ((size_t)(2 * h->nb_rpca + h->nb_apply) * kNumSums + kNumSums) * sizeof(double));
+    e = cudaMalloc(&h->partials, ((size_t)(3 * h->nb_rpca + h->nb_apply) * kNumSums + kNumSums) * sizeof(double));
   }
   if (e == cudaSuccess) {
-    h->dsums = h->partials + (size_t)(2 * h->nb_rpca + h->nb_apply) * kNumSums;
+    h->dsums = h->partials + (size_t)(3 * h->nb_rpca + h->nb_apply) * kNumSums;
     e = cudaMallocHost(&h->hsums, (kNumSums + 2 + 128) * sizeof(double));
   }
   if (e == cudaSuccess) e = svt_prepare();
@@ -247,34 +247,64 @@ int ot_rpca_set_input(ot_rpca_t h, const float* Y) {
 
 }  // extern "C"
 
-// Enqueue one outer iteration; `sums` also finalises the residual sums and
-// copies them (with the SVT diagnostics) to the pinned host buffer.
-static int enqueue_outer(ot_rpca* h, bool sums) {
+// Residual partial sums: lines 4-9 of an outer iteration write the rows of
+// its SVT-plane parity (0: rows [0, nb), 1: rows [2 nb, 3 nb)), lines 12-15
+// the rows [nb, 2 nb), so the two regions of one iteration are adjacent.
+static double* pre_rows(ot_rpca* h, int tp) { return h->partials + (size_t)(tp ? 2 * h->nb_rpca : 0) * kNumSums; }
+static double* post_rows(ot_rpca* h) { return h->partials + (size_t)h->nb_rpca * kNumSums; }
+
+// The SVT output just written (Tn) becomes the previous one (Tm) for the next
+// outer iteration.
+static void swap_svt_planes(ot_rpca* h) {
+  float* t = h->P.Tm;
+  h->P.Tm = h->P.Tn;
+  h->P.Tn = t;
+  h->tpar ^= 1;
+}
+
+// Enqueue n >= 1 outer iterations: lines 4-9 of the first, then per
+// iteration the SVT (line 10) beside the prox (line 11), and lines 12-15
+// fused with the next iteration's lines 4-9, except after the last, whose
+// lines 12-15 run alone so the state between calls is Algorithm 3's.
+// `sums` finalises the last iteration's residual sums and copies them (with
+// the SVT diagnostics) to the pinned host buffer.
+static int enqueue_interval(ot_rpca* h, int n, bool sums) {
   const long long plane = h->G.plane;
   const long long N = plane;   // rows of the N x T matrix: one frame plane (padding columns are zero)
-  OT_CUDA(rpca_launch_pre(h->G, h->C, h->P, h->partials, h->stream), "rpca pre");
-  // line 10: the Gram pass uses every SM
-  OT_CUDA(svt_launch_gram(h->P.LD, plane, N, h->prm.T, h->gram_partials, h->Gm, h->prox->derr, h->stream), "svt gram");
-  // fork: the one-CTA T x T eigensolver on the side stream, on the SM that
-  // the persistent prox kernel leaves free
-  OT_CUDA(cudaEventRecord(h->ev_fork, h->stream), "fork");
-  OT_CUDA(cudaStreamWaitEvent(h->side, h->ev_fork, 0), "fork wait");
-  OT_CUDA(svt_launch_eig(h->Gm, h->prm.T, h->warm, (float)(h->prm.gamma / h->prm.rho), h->prm.svt_max_sweeps, svt_tolerance(h->prm.T),
-                         h->V, h->Wm, h->sig, h->sweeps, h->side),
-          "svt eig");
-  h->warm = 1;
-  OT_CUDA(cudaEventRecord(h->ev_join, h->side), "join");
-  // line 11 on the handle's stream, concurrently
-  int rc = ot_prox_step(h->prox, h->prm.n_inner);
-  if (rc != OT_OK) return rc;
-  // join, then the rest of line 10 and lines 12-15
-  OT_CUDA(cudaStreamWaitEvent(h->stream, h->ev_join, 0), "join wait");
-  OT_CUDA(svt_launch_apply(h->P.LD, plane, N, h->prm.T, h->Wm, h->P.Tn, plane, false, nullptr, h->prox->derr,
-                           h->stream),
-          "svt apply");
-  OT_CUDA(rpca_launch_post(h->G, h->P, h->partials + (size_t)h->nb_rpca * kNumSums, h->stream), "rpca post");
+  OT_CUDA(rpca_launch_pre(h->G, h->C, h->P, pre_rows(h, h->tpar), h->stream), "rpca pre");
+  int last_par = h->tpar;
+  for (int k = 0; k < n; ++k) {
+    // line 10: the Gram pass uses every SM
+    OT_CUDA(svt_launch_gram(h->P.LD, plane, N, h->prm.T, h->gram_partials, h->Gm, h->prox->derr, h->stream),
+            "svt gram");
+    // fork: the one-CTA T x T eigensolver on the side stream, on the SM that
+    // the persistent prox kernel leaves free
+    OT_CUDA(cudaEventRecord(h->ev_fork, h->stream), "fork");
+    OT_CUDA(cudaStreamWaitEvent(h->side, h->ev_fork, 0), "fork wait");
+    OT_CUDA(svt_launch_eig(h->Gm, h->prm.T, h->warm, (float)(h->prm.gamma / h->prm.rho), h->prm.svt_max_sweeps,
+                           svt_tolerance(h->prm.T), h->V, h->Wm, h->sig, h->sweeps, h->side),
+            "svt eig");
+    h->warm = 1;
+    OT_CUDA(cudaEventRecord(h->ev_join, h->side), "join");
+    // line 11 on the handle's stream, concurrently
+    const int rc = ot_prox_step(h->prox, h->prm.n_inner);
+    if (rc != OT_OK) return rc;
+    // join, then the rest of line 10 and lines 12-15
+    OT_CUDA(cudaStreamWaitEvent(h->stream, h->ev_join, 0), "join wait");
+    OT_CUDA(svt_launch_apply(h->P.LD, plane, N, h->prm.T, h->Wm, h->P.Tn, plane, false, nullptr, h->prox->derr,
+                             h->stream),
+            "svt apply");
+    last_par = h->tpar;
+    if (k == n - 1)
+      OT_CUDA(rpca_launch_post(h->G, h->P, post_rows(h), h->stream), "rpca post");
+    else
+      OT_CUDA(rpca_launch_post_pre(h->G, h->C, h->P, pre_rows(h, h->tpar ^ 1), h->stream), "rpca post + pre");
+    swap_svt_planes(h);
+  }
   if (sums) {
-    OT_CUDA(launch_finalize_sums(h->partials, 2 * h->nb_rpca, h->dsums, h->stream), "rpca finalize");
+    OT_CUDA(launch_finalize_sums(h->partials + (size_t)(last_par ? h->nb_rpca : 0) * kNumSums, 2 * h->nb_rpca,
+                                 h->dsums, h->stream),
+            "rpca finalize");
     OT_CUDA(cudaMemcpyAsync(h->hsums, h->dsums, kNumSums * sizeof(double), cudaMemcpyDeviceToHost, h->stream),
             "rpca sums copy");
     OT_CUDA(cudaMemcpyAsync(reinterpret_cast<int*>(h->hsums + kNumSums), h->sweeps, sizeof(int),
@@ -289,34 +319,24 @@ static int enqueue_outer(ot_rpca* h, bool sums) {
   return OT_OK;
 }
 
-// One outer iteration: replayed from a CUDA graph once the eigensolver is
-// warm (the graph bakes in the warm flag and the prox buffers of one
-// ping-pong parity), eager otherwise.  Graph replays always finalise the
-// residual sums (a few microseconds).
-// The SVT output just written (Tn) becomes the previous one (Tm) for the next
-// outer iteration.
-static void swap_svt_planes(ot_rpca* h) {
-  float* t = h->P.Tm;
-  h->P.Tm = h->P.Tn;
-  h->P.Tn = t;
-  h->tpar ^= 1;
-}
-
-static int run_outer(ot_rpca* h, bool sums) {
-  const bool can_graph = h->prm.use_graph && h->stream != nullptr && h->warm;
-  if (!can_graph) {
-    const int rc = enqueue_outer(h, sums);
-    if (rc == OT_OK) swap_svt_planes(h);
-    return rc;
-  }
+// n outer iterations.  An interval of check_every iterations with a warm
+// eigensolver replays from a CUDA graph (one per starting parity of the
+// inner prox state and of the SVT output planes; the graph bakes in the warm
+// flag and the buffers of those parities, and always finalises the sums);
+// anything else is enqueued directly.
+static int run_interval(ot_rpca* h, int n, bool sums) {
+  const bool can_graph = h->prm.use_graph && h->stream != nullptr && h->warm && n == h->prm.check_every;
+  if (!can_graph) return enqueue_interval(h, n, sums);
   ot_prox* px = h->prox;
   const int par = px->cur, tp = h->tpar;
   if (!h->graph[par][tp]) {
     cudaGraph_t g = nullptr;
     OT_CUDA(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal), "rpca graph capture");
-    const int rc = enqueue_outer(h, true);
+    const int rc = enqueue_interval(h, n, true);
     const cudaError_t e2 = cudaStreamEndCapture(h->stream, &g);
-    px->cur = par;   // capture enqueued nothing: undo the parity bookkeeping
+    // capture enqueued nothing: undo the parity bookkeeping
+    px->cur = par;
+    while (h->tpar != tp) swap_svt_planes(h);
     if (rc != OT_OK) {
       if (g) cudaGraphDestroy(g);
       return rc;
@@ -327,8 +347,8 @@ static int run_outer(ot_rpca* h, bool sums) {
     if (e3 != cudaSuccess) return cuda_fail(e3, "rpca graph instantiate");
   }
   OT_CUDA(cudaGraphLaunch(h->graph[par][tp], h->stream), "rpca graph launch");
-  px->cur = px->resident ? par : (par ^ (h->prm.n_inner & 1));
-  swap_svt_planes(h);
+  px->cur = px->resident ? par : (par ^ ((n * h->prm.n_inner) & 1));
+  if (n & 1) swap_svt_planes(h);
   return OT_OK;
 }
 
@@ -356,21 +376,15 @@ int ot_rpca_step(ot_rpca_t h, int32_t n_outer) {
   if (!h) return fail(OT_EINVAL, "ot_rpca_step: NULL handle");
   if (!h->have_input) return fail(OT_EINVAL, "ot_rpca_step: no input (call ot_rpca_set_input)");
   if (n_outer < 0) return fail(OT_EINVAL, "ot_rpca_step: n_outer must be >= 0");
-  for (int k = 0; k < n_outer; ++k) {
-    const int rc = run_outer(h, false);
-    if (rc != OT_OK) return rc;
-  }
-  return OT_OK;
+  return n_outer > 0 ? run_interval(h, n_outer, false) : OT_OK;
 }
 
 int ot_rpca_iterate_checked(ot_rpca_t h, int32_t n_outer, ot_rpca_result* res) {
   if (!h) return fail(OT_EINVAL, "ot_rpca_iterate_checked: NULL handle");
   if (!h->have_input) return fail(OT_EINVAL, "ot_rpca_iterate_checked: no input (call ot_rpca_set_input)");
   if (n_outer < 1) return fail(OT_EINVAL, "ot_rpca_iterate_checked: n_outer must be >= 1");
-  for (int k = 0; k < n_outer; ++k) {
-    const int rc = run_outer(h, k == n_outer - 1);
-    if (rc != OT_OK) return rc;
-  }
+  const int rc = run_interval(h, n_outer, true);
+  if (rc != OT_OK) return rc;
   OT_CUDA(cudaStreamSynchronize(h->stream), "ot_rpca_iterate_checked: sync");
   if (*h->prox->herr) return fail(OT_ETIMEOUT, "a bounded device wait expired in the prox kernel");
   ot_rpca_result r;
@@ -421,44 +435,57 @@ int ot_rpca_solve(ot_rpca_t h, ot_rpca_result* res) {
 int ot_rpca_step_profiled(ot_rpca_t h, double* phase_ms) {
   if (!h || !phase_ms) return fail(OT_EINVAL, "ot_rpca_step_profiled: NULL argument");
   if (!h->have_input) return fail(OT_EINVAL, "ot_rpca_step_profiled: no input (call ot_rpca_set_input)");
-  cudaEvent_t ev[7] = {};
+  constexpr int kEv = 9;
+  cudaEvent_t ev[kEv] = {};
   cudaError_t e = cudaSuccess;
-  for (int k = 0; k < 7 && e == cudaSuccess; ++k) e = cudaEventCreate(&ev[k]);
+  for (int k = 0; k < kEv && e == cudaSuccess; ++k) e = cudaEventCreate(&ev[k]);
   const long long plane = h->G.plane;
   int rc = OT_OK;
+  // lines 10-11 of one outer iteration, every phase on the handle's stream
+  auto middle = [&](cudaEvent_t e1, cudaEvent_t e2, cudaEvent_t e3, cudaEvent_t e4) {
+    if (e == cudaSuccess)
+      e = svt_launch_gram(h->P.LD, plane, plane, h->prm.T, h->gram_partials, h->Gm, h->prox->derr, h->stream);
+    if (e == cudaSuccess && e1) e = cudaEventRecord(e1, h->stream);
+    if (e == cudaSuccess)
+      e = svt_launch_eig(h->Gm, h->prm.T, h->warm, (float)(h->prm.gamma / h->prm.rho), h->prm.svt_max_sweeps,
+                         svt_tolerance(h->prm.T), h->V, h->Wm, h->sig, h->sweeps, h->stream);
+    if (e == cudaSuccess) {
+      h->warm = 1;
+      if (e2) e = cudaEventRecord(e2, h->stream);
+    }
+    if (e == cudaSuccess)
+      e = svt_launch_apply(h->P.LD, plane, plane, h->prm.T, h->Wm, h->P.Tn, plane, false, nullptr, h->prox->derr,
+                           h->stream);
+    if (e == cudaSuccess && e3) e = cudaEventRecord(e3, h->stream);
+    if (e == cudaSuccess) {
+      rc = ot_prox_step(h->prox, h->prm.n_inner);
+      if (rc == OT_OK && e4) e = cudaEventRecord(e4, h->stream);
+    }
+  };
   if (e == cudaSuccess) e = cudaEventRecord(ev[0], h->stream);
-  if (e == cudaSuccess) e = rpca_launch_pre(h->G, h->C, h->P, h->partials, h->stream);
+  if (e == cudaSuccess) e = rpca_launch_pre(h->G, h->C, h->P, pre_rows(h, h->tpar), h->stream);
   if (e == cudaSuccess) e = cudaEventRecord(ev[1], h->stream);
-  if (e == cudaSuccess) e = svt_launch_gram(h->P.LD, plane, plane, h->prm.T, h->gram_partials, h->Gm, h->prox->derr, h->stream);
-  if (e == cudaSuccess) e = cudaEventRecord(ev[2], h->stream);
-  if (e == cudaSuccess)
-    e = svt_launch_eig(h->Gm, h->prm.T, h->warm, (float)(h->prm.gamma / h->prm.rho), h->prm.svt_max_sweeps, svt_tolerance(h->prm.T),
-                       h->V, h->Wm, h->sig, h->sweeps, h->stream);
-  if (e == cudaSuccess) {
-    h->warm = 1;
-    e = cudaEventRecord(ev[3], h->stream);
-  }
-  if (e == cudaSuccess)
-    e = svt_launch_apply(h->P.LD, plane, plane, h->prm.T, h->Wm, h->P.Tn, plane, false, nullptr, h->prox->derr,
-                         h->stream);
-  if (e == cudaSuccess) e = cudaEventRecord(ev[4], h->stream);
-  if (e == cudaSuccess) {
-    rc = ot_prox_step(h->prox, h->prm.n_inner);
-    if (rc == OT_OK) e = cudaEventRecord(ev[5], h->stream);
-  }
-  if (e == cudaSuccess && rc == OT_OK)
-    e = rpca_launch_post(h->G, h->P, h->partials + (size_t)h->nb_rpca * kNumSums, h->stream);
+  middle(ev[2], ev[3], ev[4], ev[5]);
+  if (e == cudaSuccess && rc == OT_OK) e = rpca_launch_post_pre(h->G, h->C, h->P, pre_rows(h, h->tpar ^ 1), h->stream);
   if (e == cudaSuccess && rc == OT_OK) {
     swap_svt_planes(h);
     e = cudaEventRecord(ev[6], h->stream);
   }
-  if (e == cudaSuccess && rc == OT_OK) e = cudaEventSynchronize(ev[6]);
-  for (int k = 0; k < 6 && e == cudaSuccess && rc == OT_OK; ++k) {
+  if (rc == OT_OK) middle(nullptr, nullptr, nullptr, nullptr);
+  if (e == cudaSuccess && rc == OT_OK) e = cudaEventRecord(ev[7], h->stream);
+  if (e == cudaSuccess && rc == OT_OK) e = rpca_launch_post(h->G, h->P, post_rows(h), h->stream);
+  if (e == cudaSuccess && rc == OT_OK) {
+    swap_svt_planes(h);
+    e = cudaEventRecord(ev[8], h->stream);
+  }
+  if (e == cudaSuccess && rc == OT_OK) e = cudaEventSynchronize(ev[8]);
+  const int from[7] = {0, 1, 2, 3, 4, 7, 5}, to[7] = {1, 2, 3, 4, 5, 8, 6};
+  for (int k = 0; k < 7 && e == cudaSuccess && rc == OT_OK; ++k) {
     float ms = 0.f;
-    e = cudaEventElapsedTime(&ms, ev[k], ev[k + 1]);
+    e = cudaEventElapsedTime(&ms, ev[from[k]], ev[to[k]]);
     phase_ms[k] = ms;
   }
-  for (int k = 0; k < 7; ++k)
+  for (int k = 0; k < kEv; ++k)
     if (ev[k]) cudaEventDestroy(ev[k]);
   if (rc != OT_OK) return rc;
   if (e != cudaSuccess) return cuda_fail(e, "ot_rpca_step_profiled");

@@ -1,5 +1,7 @@
 // Elementwise passes of Algorithm 3 (RPCA+UOT-DF ADMM, Sec. IV-B.1) with
-// Phi_t = I, fused into two HBM passes over the frame planes [T][H][Wp].
+// Phi_t = I, fused into two HBM passes over the frame planes [T][H][Wp]
+// (pre, post), and between consecutive outer iterations into one (post of
+// iteration k with pre of iteration k + 1).
 //
 // pre  (lines 4-9, and the inputs of lines 10-11):
 //   k_t = (x_t - l_t + a_t) + w^z_t (z_t + b_t) + w^w_t (w_t + c_t),
@@ -30,6 +32,30 @@ namespace {
 
 constexpr int kRpcaThreads = 256;
 
+// Lines 4-9 for one pixel of frame t (x, l, a, tm, d, y: frame values; zt, bt:
+// pair t's z and b, wt, ct: pair t-1's w and c, zero where the pair does not
+// exist).  The explicit fmaf fixes the rounding, so every kernel that calls
+// this computes the same bits.
+struct PreOut {
+  float s, l, x, ld, p0, p1, dx;
+};
+__device__ __forceinline__ PreOut pre_elem(float x, float l, float a, float tm, float d, float y, float zt, float bt,
+                                           float wt, float ct, float inv_sg, float thr, float rho, float inv1r) {
+  const float k = (x - l + a) + (zt + bt) + (wt + ct);
+  const float s = fmaxf(fmaf(k, inv_sg, -thr), 0.f);
+  const float lv = 0.5f * fmaxf(tm - d + x - s + a, 0.f);
+  const float xv = fmaf(rho, s + lv - a, y) * inv1r;
+  return {s, lv, xv, lv + d, s - bt, s - ct, xv - x};
+}
+
+struct PreConst {
+  float inv_sg, thr;
+};
+__device__ __forceinline__ PreConst pre_const(const RpcaGeom& g, const RpcaCoeffs& c, int t) {
+  const float sg = 1.f + (t < g.T - 1 ? 1.f : 0.f) + (t > 0 ? 1.f : 0.f);
+  return {1.f / sg, c.lam / (c.rho * sg)};
+}
+
 __global__ void __launch_bounds__(kRpcaThreads)
 rpca_pre_kernel(const RpcaGeom g, const RpcaCoeffs c, const RpcaPlanes P, double* __restrict__ partials) {
   float acc[kNumSums] = {};
@@ -42,9 +68,7 @@ rpca_pre_kernel(const RpcaGeom g, const RpcaCoeffs c, const RpcaPlanes P, double
     const long long o = 4 * q;                          // offset in [T][plane]
     const long long op = o - (long long)t * g.plane;   // offset inside the frame
     const bool hz = t < g.T - 1, hw = t > 0;
-    const float sg = 1.f + (hz ? 1.f : 0.f) + (hw ? 1.f : 0.f);
-    const float inv_sg = 1.f / sg;
-    const float thr = c.lam / (rho * sg);
+    const PreConst k = pre_const(g, c, t);
     const float4 x = ldg4(P.X + o), l = ldg4(P.L + o), a = ldg4(P.A + o), tm = ldg4(P.Tm + o), d = ldg4(P.D + o),
                  y = ldg4(P.Y + o);
     const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -55,18 +79,15 @@ rpca_pre_kernel(const RpcaGeom g, const RpcaCoeffs c, const RpcaPlanes P, double
     float4 s4, l4, x4, ld4, p04, p14;
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
-      const float k = (f4c(x, e) - f4c(l, e) + f4c(a, e)) + (f4c(zt, e) + f4c(bt, e)) + (f4c(wt, e) + f4c(ct, e));
-      const float s = fmaxf(k * inv_sg - thr, 0.f);
-      const float lv = 0.5f * fmaxf(f4c(tm, e) - f4c(d, e) + f4c(x, e) - s + f4c(a, e), 0.f);
-      const float xv = (f4c(y, e) + rho * (s + lv - f4c(a, e))) * inv1r;
-      const float dx = xv - f4c(x, e);
-      acc[0] = fmaf(dx, dx, acc[0]);
-      f4(s4, e) = s;
-      f4(l4, e) = lv;
-      f4(x4, e) = xv;
-      f4(ld4, e) = lv + f4c(d, e);
-      f4(p04, e) = s - f4c(bt, e);
-      f4(p14, e) = s - f4c(ct, e);
+      const PreOut r = pre_elem(f4c(x, e), f4c(l, e), f4c(a, e), f4c(tm, e), f4c(d, e), f4c(y, e), f4c(zt, e),
+                                f4c(bt, e), f4c(wt, e), f4c(ct, e), k.inv_sg, k.thr, rho, inv1r);
+      acc[0] = fmaf(r.dx, r.dx, acc[0]);
+      f4(s4, e) = r.s;
+      f4(l4, e) = r.l;
+      f4(x4, e) = r.x;
+      f4(ld4, e) = r.ld;
+      f4(p04, e) = r.p0;
+      f4(p14, e) = r.p1;
     }
     stg4v(P.S + o, s4);
     stg4v(P.L + o, l4);
@@ -82,6 +103,36 @@ rpca_pre_kernel(const RpcaGeom g, const RpcaCoeffs c, const RpcaPlanes P, double
     }
   }
   block_sums_to<kRpcaThreads>(acc, partials + (size_t)blockIdx.x * kNumSums);
+}
+
+// Lines 12-15 for one pixel (a, d, b, cc updated in place); the residual
+// terms go to acc when SUMS.
+template <bool SUMS>
+__device__ __forceinline__ void post_elem(float x, float s, float l, float tn, float tm, float& a, float& d, float z,
+                                          float zp, float& b, float w, float wp, float& cc, bool hz, bool hw,
+                                          float (&acc)[kNumSums]) {
+  const float r1 = x - s - l;
+  const float r2 = l - tn;
+  a += r1;
+  d += r2;
+  const float rz = z - s, rw = w - s;
+  b += rz;
+  cc += rw;
+  if (SUMS) {
+    const float dt = tn - tm;
+    acc[1] = fmaf(dt, dt, acc[1]);
+    acc[2] = fmaf(r1, r1, acc[2]);
+    acc[3] = fmaf(r2, r2, acc[3]);
+    const float dz = z - zp, dw = w - wp;
+    if (hz) {
+      acc[4] = fmaf(rz, rz, acc[4]);
+      acc[6] = fmaf(dz, dz, acc[6]);
+    }
+    if (hw) {
+      acc[5] = fmaf(rw, rw, acc[5]);
+      acc[7] = fmaf(dw, dw, acc[7]);
+    }
+  }
 }
 
 __global__ void __launch_bounds__(kRpcaThreads)
@@ -106,32 +157,77 @@ rpca_post_kernel(const RpcaGeom g, const RpcaPlanes P, double* __restrict__ part
     const float4 w = hw ? ldg4(P.w + ow) : z4, wp = hw ? ldg4(P.wprev + ow) : z4;
     float4 cc = hw ? ldg4(P.Cw + ow) : z4;
 #pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      const float r1 = f4c(x, e) - f4c(s, e) - f4c(l, e);
-      const float r2 = f4c(l, e) - f4c(tn, e);
-      const float dt = f4c(tn, e) - f4c(tm, e);
-      f4(a, e) += r1;
-      f4(d, e) += r2;
-      acc[1] = fmaf(dt, dt, acc[1]);
-      acc[2] = fmaf(r1, r1, acc[2]);
-      acc[3] = fmaf(r2, r2, acc[3]);
-      const float rz = f4c(z, e) - f4c(s, e), dz = f4c(z, e) - f4c(zp, e);
-      const float rw = f4c(w, e) - f4c(s, e), dw = f4c(w, e) - f4c(wp, e);
-      f4(b, e) += rz;
-      f4(cc, e) += rw;
-      if (hz) {
-        acc[4] = fmaf(rz, rz, acc[4]);
-        acc[6] = fmaf(dz, dz, acc[6]);
-      }
-      if (hw) {
-        acc[5] = fmaf(rw, rw, acc[5]);
-        acc[7] = fmaf(dw, dw, acc[7]);
-      }
-    }
+    for (int e = 0; e < 4; ++e)
+      post_elem<true>(f4c(x, e), f4c(s, e), f4c(l, e), f4c(tn, e), f4c(tm, e), f4(a, e), f4(d, e), f4c(z, e),
+                      f4c(zp, e), f4(b, e), f4c(w, e), f4c(wp, e), f4(cc, e), hz, hw, acc);
     stg4v(P.A + o, a);
     stg4v(P.D + o, d);
     if (hz) stg4v(P.Bz + oz, b);
     if (hw) stg4v(P.Cw + ow, cc);
+  }
+  block_sums_to<kRpcaThreads>(acc, partials + (size_t)blockIdx.x * kNumSums);
+}
+
+// Lines 12-15 of outer iteration k fused with lines 4-9 of iteration k + 1
+// (one pass instead of two): the SVT output Tn of iteration k is the
+// previous output of iteration k + 1, the duals a, d, b, c just updated feed
+// its s-, l- and x-updates.  Same per-pixel arithmetic as the two kernels in
+// turn (pre_elem, post_elem), so the iterates are bit-identical; only the
+// sum of iteration k + 1's lines 4-9 (slot 0) is produced.
+__global__ void __launch_bounds__(kRpcaThreads)
+rpca_post_pre_kernel(const RpcaGeom g, const RpcaCoeffs c, const RpcaPlanes P, double* __restrict__ partials) {
+  float acc[kNumSums] = {};
+  const long long per_frame = g.plane / 4;
+  const long long total = per_frame * g.T;
+  const float rho = c.rho, inv1r = 1.f / (1.f + c.rho);
+  const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (long long q = blockIdx.x * (long long)kRpcaThreads + threadIdx.x; q < total;
+       q += (long long)gridDim.x * kRpcaThreads) {
+    const int t = (int)(q / per_frame);
+    const long long o = 4 * q;
+    const long long op = o - (long long)t * g.plane;
+    const bool hz = t < g.T - 1, hw = t > 0;
+    const long long oz = (long long)t * g.plane + op;
+    const long long ow = (long long)(t - 1) * g.plane + op;
+    const PreConst k = pre_const(g, c, t);
+    const float4 x = ldg4(P.X + o), s = ldg4(P.S + o), l = ldg4(P.L + o), tn = ldg4(P.Tn + o), y = ldg4(P.Y + o);
+    float4 a = ldg4(P.A + o), d = ldg4(P.D + o);
+    const float4 z = hz ? ldg4(P.z + oz) : z4;
+    float4 b = hz ? ldg4(P.Bz + oz) : z4;
+    const float4 w = hw ? ldg4(P.w + ow) : z4;
+    float4 cc = hw ? ldg4(P.Cw + ow) : z4;
+    float4 s4, l4, x4, ld4, p04, p14;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      post_elem<false>(f4c(x, e), f4c(s, e), f4c(l, e), f4c(tn, e), 0.f, f4(a, e), f4(d, e), f4c(z, e), 0.f, f4(b, e),
+                       f4c(w, e), 0.f, f4(cc, e), hz, hw, acc);
+      // a zero pair slot (hz or hw false) keeps b, cc at 0, as in rpca_pre_kernel
+      const PreOut r = pre_elem(f4c(x, e), f4c(l, e), f4c(a, e), f4c(tn, e), f4c(d, e), f4c(y, e), f4c(z, e),
+                                hz ? f4c(b, e) : 0.f, f4c(w, e), hw ? f4c(cc, e) : 0.f, k.inv_sg, k.thr, rho, inv1r);
+      acc[0] = fmaf(r.dx, r.dx, acc[0]);
+      f4(s4, e) = r.s;
+      f4(l4, e) = r.l;
+      f4(x4, e) = r.x;
+      f4(ld4, e) = r.ld;
+      f4(p04, e) = r.p0;
+      f4(p14, e) = r.p1;
+    }
+    stg4v(P.A + o, a);
+    stg4v(P.D + o, d);
+    stg4v(P.S + o, s4);
+    stg4v(P.L + o, l4);
+    stg4v(P.X + o, x4);
+    stg4v(P.LD + o, ld4);
+    if (hz) {
+      stg4v(P.Bz + oz, b);
+      stg4v(P.p0 + oz, p04);
+      stg4v(P.zprev + oz, z);
+    }
+    if (hw) {
+      stg4v(P.Cw + ow, cc);
+      stg4v(P.p1 + ow, p14);
+      stg4v(P.wprev + ow, w);
+    }
   }
   block_sums_to<kRpcaThreads>(acc, partials + (size_t)blockIdx.x * kNumSums);
 }
@@ -163,6 +259,12 @@ cudaError_t rpca_launch_pre(const RpcaGeom& g, const RpcaCoeffs& c, const RpcaPl
 
 cudaError_t rpca_launch_post(const RpcaGeom& g, const RpcaPlanes& P, double* partials, cudaStream_t st) {
   rpca_post_kernel<<<rpca_num_blocks(g), kRpcaThreads, 0, st>>>(g, P, partials);
+  return cudaGetLastError();
+}
+
+cudaError_t rpca_launch_post_pre(const RpcaGeom& g, const RpcaCoeffs& c, const RpcaPlanes& P, double* partials,
+                                 cudaStream_t st) {
+  rpca_post_pre_kernel<<<rpca_num_blocks(g), kRpcaThreads, 0, st>>>(g, c, P, partials);
   return cudaGetLastError();
 }
 

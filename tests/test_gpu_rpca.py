@@ -215,3 +215,54 @@ def test_rpca_graph_replay_matches_eager(lib):
                 out.append({k: rp.get(k).cpu() for k in ("S", "L", "T", "D", "Z", "W", "a")})
     for k in out[0]:
         assert torch.equal(out[0][k], out[1][k]), k
+
+
+def test_fused_passes_match_separate_iterations(lib):
+    """Inside one call, lines 12-15 of an outer iteration and lines 4-9 of the
+    next run as one pass.  The iterates equal those of one iteration per call
+    (every pass separate) bit for bit, eager and replayed from the interval
+    graph, and so do the residuals read at the end."""
+    Y, _, _ = rpca_video(rng_for(1, 61), T=8, H=40, W=36, n_blobs=2)
+    out, res = [], []
+    for variant in ("single", "interval", "graph"):
+        stream = torch.cuda.Stream()
+        with torch.cuda.stream(stream):
+            with lib.Rpca(8, 40, 36, stream=stream, use_graph=int(variant == "graph"), check_every=6, **RP) as rp:
+                rp.set_input(Y)
+                if variant == "single":
+                    for _ in range(11):
+                        rp.step(1)
+                    r = rp.iterate_checked(1)
+                elif variant == "interval":
+                    rp.step(6)
+                    r = rp.iterate_checked(6)
+                else:
+                    rp.iterate_checked(6)      # cold eigensolver: enqueued directly
+                    r = rp.iterate_checked(6)  # warm: the interval graph
+                out.append({k: rp.get(k).cpu() for k in ("S", "L", "X", "T", "A", "D", "B", "C", "Z", "W", "a")})
+                res.append(r)
+    for k in out[0]:
+        assert torch.equal(out[0][k], out[1][k]), ("interval", k)
+        assert torch.equal(out[0][k], out[2][k]), ("graph", k)
+    for r in res[1:]:
+        assert r["res_pri"] == res[0]["res_pri"] and r["res_dual"] == res[0]["res_dual"]
+
+
+def test_step_profiled_is_two_outer_iterations(lib):
+    """The profiled path (phases serialised, the first post fused with the
+    second pre) leaves the state of two plain outer iterations, bit for bit."""
+    Y, _, _ = rpca_video(rng_for(1, 62), T=6, H=32, W=24, n_blobs=2)
+    out = []
+    for profiled in (False, True):
+        with lib.Rpca(6, 32, 24, **RP) as rp:
+            rp.set_input(Y)
+            rp.step(1)
+            if profiled:
+                ms = rp.step_profiled()
+                assert len(ms) == 7 and all(m > 0 for m in ms)
+            else:
+                rp.step(2)
+            rp.step(1)
+            out.append({k: rp.get(k).cpu() for k in ("S", "L", "X", "T", "A", "D", "B", "C", "Z", "W", "a")})
+    for k in out[0]:
+        assert torch.equal(out[0][k], out[1][k]), k
