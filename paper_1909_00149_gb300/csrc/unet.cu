@@ -69,7 +69,7 @@ struct ConvArgs {
   int co_total;          // output channels of the convolution (weight rows per offset)
   int n_out;             // output channels per CTA (multiple of 32, <= 256)
   int split;             // output channels [0, split) -> outA, [split, co_total) -> outB
-  int H, W, tiles_x, tiles_y;
+  int H, W, tiles_x, tiles_y, n_img;
   int relu, nstages;
   uint32_t tmem_cols;
   const float* bias;     // may be null
@@ -99,6 +99,9 @@ __device__ __forceinline__ uint4 pack8(const float (&f)[8]) {
 }
 
 // ---------------------------------------------------------------- tensor-core 3x3 convolution
+// Persistent: CTA x walks the tiles x, x + gridDim.x, ...; the stage ring runs
+// on across tiles, and two TMEM accumulators let the epilogue of one tile
+// overlap the MMAs of the next.
 __global__ void __launch_bounds__(kConvThreads, 1)
 conv3x3_tc_kernel(const __grid_constant__ ConvMaps M, const ConvArgs a) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -107,12 +110,11 @@ conv3x3_tc_kernel(const __grid_constant__ ConvMaps M, const ConvArgs a) {
   const uint32_t sb = kABytes + 3 * bbytes;
   const int NS = a.nstages;
   unsigned char* stg = smem + (size_t)NS * sb;               // 4 warps x 2 store boxes
-  __shared__ __align__(8) uint64_t full[kMaxStages], freef[kMaxStages], done;
+  __shared__ __align__(8) uint64_t full[kMaxStages], freef[kMaxStages], tfull[2], tfree[2], drain;
   __shared__ uint32_t s_tmem;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int txi = (int)blockIdx.x % a.tiles_x, rest = (int)blockIdx.x / a.tiles_x;
-  const int tyi = rest % a.tiles_y, img = rest / a.tiles_y;
-  const int x0 = txi * kTW, y0 = tyi * kTH;
+  const int ntiles = a.n_img * a.tiles_x * a.tiles_y;
+  const int nmine = ntiles > (int)blockIdx.x ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
   const int co0 = (int)blockIdx.y * a.n_out;
   const int nsteps = 3 * ((a.ca + a.cb) / kKC);
 
@@ -121,7 +123,11 @@ conv3x3_tc_kernel(const __grid_constant__ ConvMaps M, const ConvArgs a) {
       bar_init(s_u32(&full[s]), 1);
       bar_init(s_u32(&freef[s]), 1);
     }
-    bar_init(s_u32(&done), 1);
+    for (int b = 0; b < 2; ++b) {
+      bar_init(s_u32(&tfull[b]), 1);
+      bar_init(s_u32(&tfree[b]), 4);
+    }
+    bar_init(s_u32(&drain), 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) tmem_alloc(s_u32(&s_tmem), a.tmem_cols);
@@ -132,59 +138,81 @@ conv3x3_tc_kernel(const __grid_constant__ ConvMaps M, const ConvArgs a) {
   bool ok = true;
 
   if (warp == 0) {
-    if (lane == 0) {   // producer: step t = (32-channel chunk t / 3, column shift v = t % 3)
-      int issued = 0;
-      for (int t = 0; t < nsteps; ++t) {
-        const int s = t % NS;
-        if (t >= NS && !bar_wait(s_u32(&freef[s]), (uint32_t)((t / NS - 1) & 1))) { ok = false; break; }
-        const int c = (t / 3) * kKC, v = t % 3;
-        const uint32_t base = s_u32(smem + (size_t)s * sb), fb = s_u32(&full[s]);
-        bar_expect(fb, sb);
-        if (c < a.ca) tma4d(base, &M.inA, c, x0 + v - 1, y0 - 1, img, fb);
-        else tma4d(base, &M.inB, c - a.ca, x0 + v - 1, y0 - 1, img, fb);
+    if (lane == 0) {   // producer: per tile, step t = (32-channel chunk t / 3, column shift v = t % 3)
+      long long issued = 0;
+      for (int i = 0; i < nmine && ok; ++i) {
+        const int tile = (int)blockIdx.x + i * (int)gridDim.x;
+        const int txi = tile % a.tiles_x, rest = tile / a.tiles_x;
+        const int x0 = txi * kTW, y0 = (rest % a.tiles_y) * kTH, img = rest / a.tiles_y;
+        for (int t = 0; t < nsteps; ++t) {
+          const long long gs = (long long)i * nsteps + t;
+          const int s = (int)(gs % NS);
+          if (gs >= NS && !bar_wait(s_u32(&freef[s]), (uint32_t)((gs / NS - 1) & 1))) { ok = false; break; }
+          const int c = (t / 3) * kKC, v = t % 3;
+          const uint32_t base = s_u32(smem + (size_t)s * sb), fb = s_u32(&full[s]);
+          bar_expect(fb, sb);
+          if (c < a.ca) tma4d(base, &M.inA, c, x0 + v - 1, y0 - 1, img, fb);
+          else tma4d(base, &M.inB, c - a.ca, x0 + v - 1, y0 - 1, img, fb);
 #pragma unroll
-        for (int u = 0; u < 3; ++u) tma2d(base + kABytes + u * bbytes, &M.w, c, (u * 3 + v) * a.co_total + co0, fb);
-        issued = t + 1;
+          for (int u = 0; u < 3; ++u)
+            tma2d(base + kABytes + u * bbytes, &M.w, c, (u * 3 + v) * a.co_total + co0, fb);
+          issued = gs + 1;
+        }
       }
       // copies still in flight land before the CTA's shared memory goes away
-      for (int t = issued - NS < 0 ? 0 : issued - NS; t < issued; ++t)
-        (void)bar_wait(s_u32(&full[t % NS]), (uint32_t)((t / NS) & 1));
+      for (long long gs = issued - NS < 0 ? 0 : issued - NS; gs < issued; ++gs)
+        (void)bar_wait(s_u32(&full[gs % NS]), (uint32_t)((gs / NS) & 1));
     }
   } else if (warp == 1) {
     if (lane == 0) {   // MMA issuer
       const uint32_t idesc = bf16_idesc(128, a.n_out);
-      for (int t = 0; t < nsteps; ++t) {
-        const int s = t % NS;
-        if (!bar_wait(s_u32(&full[s]), (uint32_t)((t / NS) & 1))) { ok = false; break; }
+      for (int i = 0; i < nmine && ok; ++i) {
+        const int b = i & 1;
+        // the epilogue of tile i - 2 has read accumulator b
+        if (i >= 2 && !bar_wait(s_u32(&tfree[b]), (uint32_t)(((i >> 1) - 1) & 1))) { ok = false; break; }
         fence_after_sync();
-        const uint32_t base = s_u32(smem + (size_t)s * sb);
+        const uint32_t acc = tmem + (uint32_t)b * (a.tmem_cols / 2);
+        for (int t = 0; t < nsteps; ++t) {
+          const long long gs = (long long)i * nsteps + t;
+          const int s = (int)(gs % NS);
+          if (!bar_wait(s_u32(&full[s]), (uint32_t)((gs / NS) & 1))) { ok = false; break; }
+          fence_after_sync();
+          const uint32_t base = s_u32(smem + (size_t)s * sb);
 #pragma unroll
-        for (int u = 0; u < 3; ++u)
+          for (int u = 0; u < 3; ++u)
 #pragma unroll
-          for (int kk = 0; kk < 2; ++kk)   // K = 16 per instruction: 32 bytes along the row
-            mma_bf16(tmem, sw64_desc(base + u * 512 + kk * 32), sw64_desc(base + kABytes + u * bbytes + kk * 32),
-                     idesc, (t > 0 || u > 0 || kk > 0) ? 1u : 0u);
-        mma_commit(s_u32(&freef[s]));
+            for (int kk = 0; kk < 2; ++kk)   // K = 16 per instruction: 32 bytes along the row
+              mma_bf16(acc, sw64_desc(base + u * 512 + kk * 32), sw64_desc(base + kABytes + u * bbytes + kk * 32),
+                       idesc, (t > 0 || u > 0 || kk > 0) ? 1u : 0u);
+          mma_commit(s_u32(&freef[s]));
+        }
+        if (ok) mma_commit(s_u32(&tfull[b]));
       }
-      mma_commit(s_u32(&done));   // completes once every MMA issued above has
+      // every MMA issued above completes before the tensor memory is released
+      mma_commit(s_u32(&drain));
+      (void)bar_wait(s_u32(&drain), 0);
     }
   } else {
     // epilogue: warp w reads TMEM lanes 32 q ... + 31 (q = w % 4) = pixel rows 4q ... 4q + 3 of the tile
     const int q = warp & 3;
     unsigned char* my = stg + (size_t)q * 2 * kStgBytes;
-    if (!bar_wait(s_u32(&done), 0)) ok = false;
-    fence_after_sync();
-    if (ok) {
+    int buf = 0;
+    for (int i = 0; i < nmine && ok; ++i) {
+      const int b = i & 1;
+      if (!bar_wait(s_u32(&tfull[b]), (uint32_t)((i >> 1) & 1))) { ok = false; break; }
+      fence_after_sync();
+      const int tile = (int)blockIdx.x + i * (int)gridDim.x;
+      const int txi = tile % a.tiles_x, rest = tile / a.tiles_x;
+      const int x0 = txi * kTW, y0 = (rest % a.tiles_y) * kTH, img = rest / a.tiles_y;
       const int ty = 4 * q + (lane >> 3), tx = lane & 7;
       const int py = y0 + ty, px = x0 + tx;
       const bool inside = py < a.H && px < a.W;
       const long long pix = ((long long)img * a.H + py) * a.W + px;
       const bool box_live = y0 + 4 * q < a.H;   // warp-uniform
-      int buf = 0;
 #pragma unroll 1
       for (int g = 0; g < a.n_out / 32; ++g) {
         float v[32];
-        tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(32 * g), v);
+        tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)b * (a.tmem_cols / 2) + (uint32_t)(32 * g), v);
         const int c = co0 + 32 * g;
         if (a.bias) {
 #pragma unroll
@@ -228,8 +256,11 @@ conv3x3_tc_kernel(const __grid_constant__ ConvMaps M, const ConvArgs a) {
         }
         buf ^= 1;
       }
-      if (lane == 0) bulk_wait_all();   // the stores complete before the CTA exits
+      fence_before_sync();
+      __syncwarp();
+      if (lane == 0) bar_arrive(s_u32(&tfree[b]));   // accumulator b may be overwritten
     }
+    if (lane == 0) bulk_wait_all();   // the stores complete before the CTA exits
   }
   if (!ok) atomicExch(a.err, 1);
   fence_before_sync();
@@ -712,15 +743,20 @@ cudaError_t conv_tc(ot_unet* h, const Act& inA, const Act* inB, const CUtensorMa
   a.tiles_y = (a.H + kTH - 1) / kTH;
   a.relu = relu ? 1 : 0;
   const uint32_t smem = conv_smem(n_out, &a.nstages);
-  a.tmem_cols = n_out <= 32 ? 32u : n_out <= 64 ? 64u : n_out <= 128 ? 128u : 256u;
+  // two accumulators, each at a power-of-two column offset of at least n_out
+  a.tmem_cols = n_out <= 16 ? 32u : n_out <= 32 ? 64u : n_out <= 64 ? 128u : n_out <= 128 ? 256u : 512u;
+  a.n_img = n;
   a.bias = bias;
   a.maskA = maskA ? maskA->p : nullptr;
   a.mca = maskA ? maskA->C : 0;
   a.maskB = maskB ? maskB->p : nullptr;
   a.mcb = maskB ? maskB->C : 0;
   a.err = h->derr;
-  const dim3 grid((unsigned)(n * a.tiles_x * a.tiles_y), (unsigned)(co_total / n_out));
-  conv3x3_tc_kernel<<<grid, kConvThreads, smem, h->stream>>>(M, a);
+  // persistent: as many CTAs as fit at once (two per SM for the narrow layers)
+  const int gy = co_total / n_out, ntiles = n * a.tiles_x * a.tiles_y;
+  int gx = (n_out <= 64 ? 2 * 152 : 152) / gy;
+  gx = gx < 1 ? 1 : (gx > ntiles ? ntiles : gx);
+  conv3x3_tc_kernel<<<dim3((unsigned)gx, (unsigned)gy), kConvThreads, smem, h->stream>>>(M, a);
   return cudaGetLastError();
 }
 
