@@ -435,10 +435,14 @@ prox_tma_batch_kernel(const BatchSeq* __restrict__ seqs, const int* __restrict__
                               bx * kTW);
   };
 
+  // a contiguous range of work items per CTA: consecutive tiles mostly share
+  // a sequence, so its descriptors and coefficients stay in cache
+  const int w0 = (int)((long long)total * blockIdx.x / gridDim.x);
+  const int w1 = (int)((long long)total * (blockIdx.x + 1) / gridDim.x);
   if (tid == 0) {
     for (int s = 0; s < NS; ++s) {
-      const int w = blockIdx.x + s * gridDim.x;
-      if (w < total) issue(w, s);
+      const int w = w0 + s;
+      if (w < w1) issue(w, s);
     }
   }
 
@@ -447,7 +451,7 @@ prox_tma_batch_kernel(const BatchSeq* __restrict__ seqs, const int* __restrict__
   for (int k = 0; k < kNumSums; ++k) accs[k] = 0.f;
 
   int k = 0;
-  for (int w = blockIdx.x; w < total; w += gridDim.x, ++k) {
+  for (int w = w0; w < w1; ++w, ++k) {
     const int s = k % NS;
     const uint32_t ph = (uint32_t)((k / NS) & 1);
     const bool ok = mbar_wait_bounded(smem_u32(&bars[s]), ph);
@@ -500,8 +504,8 @@ prox_tma_batch_kernel(const BatchSeq* __restrict__ seqs, const int* __restrict__
     }
     __syncthreads();
     if (tid == 0) {
-      const int next = w + NS * gridDim.x;
-      if (next < total) {
+      const int next = w + NS;
+      if (next < w1) {
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         issue(next, s);
       }
