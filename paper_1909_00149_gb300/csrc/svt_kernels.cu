@@ -364,8 +364,7 @@ jacobi_svt_kernel(const double* __restrict__ G, int warm, float theta, int max_s
 // max(1 - theta / sqrt(lam), 0).  Writing A = D + E (E off-diagonal), the
 // first-order change of F is dd_ij e_ij with dd_ij the divided difference of
 // f between lam_i and lam_j, so rotations inside the subspace that f maps to
-// zero do not change Wm.  After rounds 0, 2, 4 and 8 (a warm start is often
-// that close) and then every kJregCheck rounds, the solver stops when
+// zero do not change Wm.  Every kJregCheck rounds the solver stops when
 // either the plain test ||E||_F <= tol ||diag||_2 holds, or the weighted one
 // sqrt(sum_ij (dd_ij e_ij)^2) <= tol max_i f_i, where dd_ij is bounded by the
 // largest slope of f on [min(lam_i, lam_j) - eps, max(lam_i, lam_j) + eps],
@@ -570,7 +569,7 @@ jacobi_reg_kernel(const double* __restrict__ G, int warm, float theta, int max_s
   int done = 0, r = 0, cur = 0;    // rounds done; round within the sweep; current buffer
   for (;; ++done, r = (r + 1 == R) ? 0 : r + 1) {
     A = sm + cur * (TP * LDA);
-    if (done % kJregCheck == 0 || done == 2 || done == 4 || done == 8 || done == max_rounds) {
+    if (done % kJregCheck == 0 || done == max_rounds) {
       float off = 0.f, dg = 0.f;
       for (int e = tid; e < TP * TP; e += kJregThreads) {
         const int i = e / TP, j = e % TP;
