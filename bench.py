@@ -157,6 +157,24 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# --------------------------------------------------------------------- ranks
+def dist_barrier(world: int):
+    if world > 1:
+        import torch
+        torch.distributed.barrier()
+
+
+def max_over_ranks(vals, world: int, device: str = "cuda") -> list:
+    """Elementwise maximum of per-rank values (the slowest rank sets the
+    time of a replicated step)."""
+    if world == 1:
+        return list(vals)
+    import torch
+    t = torch.tensor(list(vals), device=device, dtype=torch.float64)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return t.tolist()
+
+
 # --------------------------------------------------------------------- inputs
 def rpca_inputs(rank: int, T=T_FRAMES, H=HEIGHT, W=WIDTH):
     from synth import config2_video, rng_for, rpca_video
@@ -194,11 +212,8 @@ def run_ours_rpca(args, rank, world, local_rank):
     T, H, W = Y.shape
     P = T - 1
     px = P * H * W * args.n_inner
-    dist = world > 1
-
     def barrier():
-        if dist:
-            torch.distributed.barrier()
+        dist_barrier(world)
 
     with torch.cuda.stream(stream):
         rp = otp.Rpca(T, H, W, stream=stream, n_inner=args.n_inner, **RPCA_KW)
@@ -241,10 +256,7 @@ def run_ours_rpca(args, rank, world, local_rank):
         e2e_ms = e0.elapsed_time(e1)
         rp.close()
 
-    if dist:
-        t = torch.tensor([ms, e2e_ms] + phase_ms, device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms, e2e_ms, *phase_ms = t.tolist()
+    ms, e2e_ms, *phase_ms = max_over_ranks([ms, e2e_ms] + phase_ms, world)
     if rank != 0:
         return None
     units = px * OUTER_PER_STEP * args.steps * world
@@ -309,11 +321,9 @@ def run_ours_prox(args, rank, world, local_rank):
     p0, p1 = prox_inputs(rank)
     B, H, W = p0.shape
     px = B * H * W
-    dist = world > 1
 
     def barrier():
-        if dist:
-            torch.distributed.barrier()
+        dist_barrier(world)
 
     with torch.cuda.stream(stream):
         s = otp.OtProx(B, H, W, stream=stream, **PROX_KW)
@@ -353,10 +363,7 @@ def run_ours_prox(args, rank, world, local_rank):
         barrier()
         e2e_ms = e0.elapsed_time(e1)
         s.close()
-    if dist:
-        t = torch.tensor([ms, e2e_ms, k_ms], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms, e2e_ms, k_ms = t.tolist()
+    ms, e2e_ms, k_ms = max_over_ranks([ms, e2e_ms, k_ms], world)
     if rank != 0:
         return None
     units = px * PROX_ITERS_PER_STEP * args.steps * world
