@@ -276,10 +276,12 @@ int ot_rpca_iterate_checked(ot_rpca_t h, int32_t n_outer, ot_rpca_result* res);
 int ot_rpca_solve(ot_rpca_t h, ot_rpca_result* res);
 /* Two outer iterations (as ot_rpca_step(h, 2)) with CUDA events recorded on
  * the handle's stream between their phases, the eigensolver serialised with
- * the prox; phase_ms[0..6] receives the device time of: 0 lines 4-9 of the
+ * the prox; phase_ms[0..7] receives the device time of: 0 lines 4-9 of the
  * first, 1 its Gram matrix, 2 its T x T eigensolver, 3 its SVT apply, 4 its
  * n_inner Algorithm 1 iterations, 5 lines 12-15 of the second (alone),
- * 6 lines 12-15 of the first fused with lines 4-9 of the second.  Sync. */
+ * 6 lines 12-15 of the first fused with lines 4-9 of the second (and, for
+ * T <= 64, the second's Gram partials), 7 the second's Gram (the reduction
+ * of those partials for T <= 64).  Sync. */
 int ot_rpca_step_profiled(ot_rpca_t h, double* phase_ms);
 
 /* Copy one variable (OT_RPCA_*) out, dense.  Sync. */

@@ -251,9 +251,10 @@ class Rpca:
         return r.as_dict()
 
     def step_profiled(self) -> list:
-        """Two outer iterations; device ms of their seven phases (see the C
-        header: pre, Gram, eigensolver, apply, prox, post, fused post + pre)."""
-        ms = (ctypes.c_double * 7)()
+        """Two outer iterations; device ms of their eight phases (see the C
+        header: pre, Gram, eigensolver, apply, prox, post, fused post + pre,
+        the second Gram)."""
+        ms = (ctypes.c_double * 8)()
         check(_lib.ot_rpca_step_profiled(self.h, ms), "ot_rpca_step_profiled")
         return list(ms)
 

@@ -196,6 +196,12 @@ cudaError_t rpca_launch_post(const RpcaGeom& g, const RpcaPlanes& P, double* par
 // post of outer iteration k and pre of k + 1 in one pass (slot 0 sums only)
 cudaError_t rpca_launch_post_pre(const RpcaGeom& g, const RpcaCoeffs& c, const RpcaPlanes& P, double* partials,
                                  cudaStream_t st);
+// the same pass accumulating iteration k + 1's Gram matrix (T padded to TP
+// in {16, 32, 64}): FP32 partials gpart[rpca_gram_parts(g)][TP][TP]; writes
+// nrows slot-0 rows of partials
+int rpca_gram_parts(const RpcaGeom& g);
+cudaError_t rpca_launch_post_pre_gram(const RpcaGeom& g, const RpcaCoeffs& c, const RpcaPlanes& P, int TP,
+                                      double* partials, int nrows, float* gpart, cudaStream_t st);
 cudaError_t rpca_launch_sumsq(const RpcaGeom& g, const float* Y, double* partials, cudaStream_t st);
 
 // ----------------------------------------------------------------- SVT
@@ -206,6 +212,8 @@ int svt_apply_blocks(long long N, int T, int* gy);
 cudaError_t svt_prepare();
 cudaError_t svt_launch_gram(const float* X, long long ld, long long N, int T, double* partials, double* G, int* err,
                             cudaStream_t st);
+// G = the FP64 sum, in order, of nparts FP32 partial Grams [nparts][TP][TP]
+cudaError_t svt_launch_gram_reduce(const float* partials, int nparts, int T, double* G, cudaStream_t st);
 // tensor-core partial Grams (gram_tcgen05.cu); T > 16
 int svt_gram_tc_blocks(long long N);
 cudaError_t svt_launch_gram_tc(const float* X, long long ld, long long N, int T, float* partials, int* err,

@@ -39,6 +39,10 @@ struct ot_rpca {
   // SVT workspace
   int TP;
   double* gram_partials;
+  // T_pad <= 64: the fused pass between outer iterations also accumulates the
+  // next iteration's Gram matrix, as FP32 partials reduced before the eigensolver
+  float* fgram;
+  int fgram_parts;
   double* Gm;
   float* V;
   float* Wm;
@@ -94,6 +98,7 @@ int ot_rpca_destroy(ot_rpca_t h) {
   if (h->prox) ot_prox_destroy(h->prox);
   if (h->slab) cudaFree(h->slab);
   if (h->gram_partials) cudaFree(h->gram_partials);
+  if (h->fgram) cudaFree(h->fgram);
   if (h->partials) cudaFree(h->partials);
   if (h->hsums) cudaFreeHost(h->hsums);
   free(h);
@@ -195,6 +200,10 @@ int ot_rpca_create(const ot_rpca_params* params, void* cuda_stream, ot_rpca_t* o
     h->dsums = h->partials + (size_t)(3 * h->nb_rpca + h->nb_apply) * kNumSums;
     e = cudaMallocHost(&h->hsums, (kNumSums + 2 + 128) * sizeof(double));
   }
+  if (e == cudaSuccess && TP <= 64) {
+    h->fgram_parts = rpca_gram_parts(h->G);
+    e = cudaMalloc(&h->fgram, (size_t)h->fgram_parts * TP * TP * sizeof(float));
+  }
   if (e == cudaSuccess) e = svt_prepare();
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming);
@@ -262,6 +271,15 @@ static void swap_svt_planes(ot_rpca* h) {
   h->tpar ^= 1;
 }
 
+// Lines 12-15 of this outer iteration and lines 4-9 of the next in one pass
+// (with the next iteration's Gram partials when T_pad <= 64).
+static cudaError_t launch_between(ot_rpca* h) {
+  if (h->fgram)
+    return rpca_launch_post_pre_gram(h->G, h->C, h->P, h->TP, pre_rows(h, h->tpar ^ 1), h->nb_rpca, h->fgram,
+                                     h->stream);
+  return rpca_launch_post_pre(h->G, h->C, h->P, pre_rows(h, h->tpar ^ 1), h->stream);
+}
+
 // Enqueue n >= 1 outer iterations: lines 4-9 of the first, then per
 // iteration the SVT (line 10) beside the prox (line 11), and lines 12-15
 // fused with the next iteration's lines 4-9, except after the last, whose
@@ -274,9 +292,13 @@ static int enqueue_interval(ot_rpca* h, int n, bool sums) {
   OT_CUDA(rpca_launch_pre(h->G, h->C, h->P, pre_rows(h, h->tpar), h->stream), "rpca pre");
   int last_par = h->tpar;
   for (int k = 0; k < n; ++k) {
-    // line 10: the Gram pass uses every SM
-    OT_CUDA(svt_launch_gram(h->P.LD, plane, N, h->prm.T, h->gram_partials, h->Gm, h->prox->derr, h->stream),
-            "svt gram");
+    // line 10: the Gram matrix, from the LD just written (after the fused
+    // pass only its partials are left to reduce)
+    if (k > 0 && h->fgram)
+      OT_CUDA(svt_launch_gram_reduce(h->fgram, h->fgram_parts, h->prm.T, h->Gm, h->stream), "svt gram reduce");
+    else
+      OT_CUDA(svt_launch_gram(h->P.LD, plane, N, h->prm.T, h->gram_partials, h->Gm, h->prox->derr, h->stream),
+              "svt gram");
     // fork: the one-CTA T x T eigensolver on the side stream, on the SM that
     // the persistent prox kernel leaves free
     OT_CUDA(cudaEventRecord(h->ev_fork, h->stream), "fork");
@@ -298,7 +320,7 @@ static int enqueue_interval(ot_rpca* h, int n, bool sums) {
     if (k == n - 1)
       OT_CUDA(rpca_launch_post(h->G, h->P, post_rows(h), h->stream), "rpca post");
     else
-      OT_CUDA(rpca_launch_post_pre(h->G, h->C, h->P, pre_rows(h, h->tpar ^ 1), h->stream), "rpca post + pre");
+      OT_CUDA(launch_between(h), "rpca post + pre");
     swap_svt_planes(h);
   }
   if (sums) {
@@ -435,16 +457,18 @@ int ot_rpca_solve(ot_rpca_t h, ot_rpca_result* res) {
 int ot_rpca_step_profiled(ot_rpca_t h, double* phase_ms) {
   if (!h || !phase_ms) return fail(OT_EINVAL, "ot_rpca_step_profiled: NULL argument");
   if (!h->have_input) return fail(OT_EINVAL, "ot_rpca_step_profiled: no input (call ot_rpca_set_input)");
-  constexpr int kEv = 9;
+  constexpr int kEv = 10;
   cudaEvent_t ev[kEv] = {};
   cudaError_t e = cudaSuccess;
   for (int k = 0; k < kEv && e == cudaSuccess; ++k) e = cudaEventCreate(&ev[k]);
   const long long plane = h->G.plane;
   int rc = OT_OK;
   // lines 10-11 of one outer iteration, every phase on the handle's stream
-  auto middle = [&](cudaEvent_t e1, cudaEvent_t e2, cudaEvent_t e3, cudaEvent_t e4) {
+  auto middle = [&](bool after_fused, cudaEvent_t e1, cudaEvent_t e2, cudaEvent_t e3, cudaEvent_t e4) {
     if (e == cudaSuccess)
-      e = svt_launch_gram(h->P.LD, plane, plane, h->prm.T, h->gram_partials, h->Gm, h->prox->derr, h->stream);
+      e = (after_fused && h->fgram)
+              ? svt_launch_gram_reduce(h->fgram, h->fgram_parts, h->prm.T, h->Gm, h->stream)
+              : svt_launch_gram(h->P.LD, plane, plane, h->prm.T, h->gram_partials, h->Gm, h->prox->derr, h->stream);
     if (e == cudaSuccess && e1) e = cudaEventRecord(e1, h->stream);
     if (e == cudaSuccess)
       e = svt_launch_eig(h->Gm, h->prm.T, h->warm, (float)(h->prm.gamma / h->prm.rho), h->prm.svt_max_sweeps,
@@ -465,13 +489,13 @@ int ot_rpca_step_profiled(ot_rpca_t h, double* phase_ms) {
   if (e == cudaSuccess) e = cudaEventRecord(ev[0], h->stream);
   if (e == cudaSuccess) e = rpca_launch_pre(h->G, h->C, h->P, pre_rows(h, h->tpar), h->stream);
   if (e == cudaSuccess) e = cudaEventRecord(ev[1], h->stream);
-  middle(ev[2], ev[3], ev[4], ev[5]);
-  if (e == cudaSuccess && rc == OT_OK) e = rpca_launch_post_pre(h->G, h->C, h->P, pre_rows(h, h->tpar ^ 1), h->stream);
+  middle(false, ev[2], ev[3], ev[4], ev[5]);
+  if (e == cudaSuccess && rc == OT_OK) e = launch_between(h);
   if (e == cudaSuccess && rc == OT_OK) {
     swap_svt_planes(h);
     e = cudaEventRecord(ev[6], h->stream);
   }
-  if (rc == OT_OK) middle(nullptr, nullptr, nullptr, nullptr);
+  if (rc == OT_OK) middle(true, ev[9], nullptr, nullptr, nullptr);
   if (e == cudaSuccess && rc == OT_OK) e = cudaEventRecord(ev[7], h->stream);
   if (e == cudaSuccess && rc == OT_OK) e = rpca_launch_post(h->G, h->P, post_rows(h), h->stream);
   if (e == cudaSuccess && rc == OT_OK) {
@@ -479,8 +503,8 @@ int ot_rpca_step_profiled(ot_rpca_t h, double* phase_ms) {
     e = cudaEventRecord(ev[8], h->stream);
   }
   if (e == cudaSuccess && rc == OT_OK) e = cudaEventSynchronize(ev[8]);
-  const int from[7] = {0, 1, 2, 3, 4, 7, 5}, to[7] = {1, 2, 3, 4, 5, 8, 6};
-  for (int k = 0; k < 7 && e == cudaSuccess && rc == OT_OK; ++k) {
+  const int from[8] = {0, 1, 2, 3, 4, 7, 5, 6}, to[8] = {1, 2, 3, 4, 5, 8, 6, 9};
+  for (int k = 0; k < 8 && e == cudaSuccess && rc == OT_OK; ++k) {
     float ms = 0.f;
     e = cudaEventElapsedTime(&ms, ev[from[k]], ev[to[k]]);
     phase_ms[k] = ms;

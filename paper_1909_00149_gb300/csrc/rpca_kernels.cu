@@ -232,6 +232,120 @@ rpca_post_pre_kernel(const RpcaGeom g, const RpcaCoeffs c, const RpcaPlanes P, d
   block_sums_to<kRpcaThreads>(acc, partials + (size_t)blockIdx.x * kNumSums);
 }
 
+// The fused pass of rpca_post_pre_kernel that also accumulates the SVT Gram
+// matrix of the LD = L + D it writes (Alg. 3 line 10 of iteration k + 1):
+// a CTA owns chunks of kGC consecutive pixels of a frame plane across all T
+// frames, stages their LD values in shared memory, and adds
+// LD_chunk^T LD_chunk to a TP x TP FP32 accumulator (a 16 x 16 grid of
+// threads, each a TP/16 x TP/16 block); every CTA writes its partial Gram to
+// gpart[blockIdx.x], and the FP64 reduction of the partials follows.  Per
+// (frame, pixel) the arithmetic is that of rpca_post_pre_kernel.  The slot-0
+// rows blockIdx.x + k gridDim.x < nrows of partials are written (zero beyond
+// the CTA's own), so the residual finalisation sees nrows rows as before.
+constexpr int kGC = 64;             // pixels per Gram chunk
+constexpr int kFGThreads = 256;
+
+template <int TP>
+__global__ void __launch_bounds__(kFGThreads, 2)
+rpca_post_pre_gram_kernel(const RpcaGeom g, const RpcaCoeffs c, const RpcaPlanes P, double* __restrict__ partials,
+                          int nrows, float* __restrict__ gpart) {
+  constexpr int BE = TP / 16;       // Gram block edge per thread
+  constexpr int LDS = TP + 4;       // padded row of the staged tile (16-byte aligned)
+  __shared__ __align__(16) float sLD[kGC][LDS];
+  float acc[kNumSums] = {};
+  float gacc[BE][BE];
+#pragma unroll
+  for (int r = 0; r < BE; ++r)
+#pragma unroll
+    for (int q = 0; q < BE; ++q) gacc[r][q] = 0.f;
+  const int tid = threadIdx.x, bi = tid / 16, bj = tid % 16;
+  for (int e = tid; e < kGC * LDS; e += kFGThreads) (&sLD[0][0])[e] = 0.f;   // frames T..TP-1 stay zero
+  __syncthreads();
+  const float rho = c.rho, inv1r = 1.f / (1.f + c.rho);
+  const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+  const long long nch = (g.plane + kGC - 1) / kGC;
+  const int items = g.T * (kGC / 4);
+  for (long long ch = blockIdx.x; ch < nch; ch += gridDim.x) {
+    const long long p0 = ch * kGC;
+#pragma unroll 2
+    for (int it = tid; it < items; it += kFGThreads) {
+      const int t = it / (kGC / 4), j = it % (kGC / 4);
+      const long long op = p0 + 4 * j;            // offset inside the frame (plane is a multiple of 4)
+      if (op >= g.plane) {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) sLD[4 * j + e][t] = 0.f;
+        continue;
+      }
+      const long long o = (long long)t * g.plane + op;
+      const bool hz = t < g.T - 1, hw = t > 0;
+      const long long oz = (long long)t * g.plane + op;
+      const long long ow = (long long)(t - 1) * g.plane + op;
+      const PreConst k = pre_const(g, c, t);
+      const float4 x = ldg4(P.X + o), s = ldg4(P.S + o), l = ldg4(P.L + o), tn = ldg4(P.Tn + o), y = ldg4(P.Y + o);
+      float4 a = ldg4(P.A + o), d = ldg4(P.D + o);
+      const float4 z = hz ? ldg4(P.z + oz) : z4;
+      float4 b = hz ? ldg4(P.Bz + oz) : z4;
+      const float4 w = hw ? ldg4(P.w + ow) : z4;
+      float4 cc = hw ? ldg4(P.Cw + ow) : z4;
+      float4 s4, l4, x4, ld4, p04, p14;
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        post_elem<false>(f4c(x, e), f4c(s, e), f4c(l, e), f4c(tn, e), 0.f, f4(a, e), f4(d, e), f4c(z, e), 0.f,
+                         f4(b, e), f4c(w, e), 0.f, f4(cc, e), hz, hw, acc);
+        const PreOut r = pre_elem(f4c(x, e), f4c(l, e), f4c(a, e), f4c(tn, e), f4c(d, e), f4c(y, e), f4c(z, e),
+                                  hz ? f4c(b, e) : 0.f, f4c(w, e), hw ? f4c(cc, e) : 0.f, k.inv_sg, k.thr, rho, inv1r);
+        acc[0] = fmaf(r.dx, r.dx, acc[0]);
+        f4(s4, e) = r.s;
+        f4(l4, e) = r.l;
+        f4(x4, e) = r.x;
+        f4(ld4, e) = r.ld;
+        f4(p04, e) = r.p0;
+        f4(p14, e) = r.p1;
+        sLD[4 * j + e][t] = r.ld;
+      }
+      stg4v(P.A + o, a);
+      stg4v(P.D + o, d);
+      stg4v(P.S + o, s4);
+      stg4v(P.L + o, l4);
+      stg4v(P.X + o, x4);
+      stg4v(P.LD + o, ld4);
+      if (hz) {
+        stg4v(P.Bz + oz, b);
+        stg4v(P.p0 + oz, p04);
+        stg4v(P.zprev + oz, z);
+      }
+      if (hw) {
+        stg4v(P.Cw + ow, cc);
+        stg4v(P.p1 + ow, p14);
+        stg4v(P.wprev + ow, w);
+      }
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int p = 0; p < kGC; ++p) {
+      float av[BE], bv[BE];
+#pragma unroll
+      for (int r = 0; r < BE; ++r) {
+        av[r] = sLD[p][BE * bi + r];
+        bv[r] = sLD[p][BE * bj + r];
+      }
+#pragma unroll
+      for (int r = 0; r < BE; ++r)
+#pragma unroll
+        for (int q = 0; q < BE; ++q) gacc[r][q] = fmaf(av[r], bv[q], gacc[r][q]);
+    }
+    __syncthreads();
+  }
+  float* out = gpart + (size_t)blockIdx.x * TP * TP;
+#pragma unroll
+  for (int r = 0; r < BE; ++r)
+#pragma unroll
+    for (int q = 0; q < BE; ++q) out[(BE * bi + r) * TP + BE * bj + q] = gacc[r][q];
+  block_sums_to<kFGThreads>(acc, partials + (size_t)blockIdx.x * kNumSums);
+  for (int row = blockIdx.x + gridDim.x; row < nrows; row += gridDim.x)
+    if (tid < kNumSums) partials[(size_t)row * kNumSums + tid] = 0.0;
+}
+
 // ||Y||^2 (once per input) into partials[block][0].
 __global__ void __launch_bounds__(kRpcaThreads)
 sumsq_kernel(const float* __restrict__ Y, long long n4, double* __restrict__ partials) {
@@ -265,6 +379,28 @@ cudaError_t rpca_launch_post(const RpcaGeom& g, const RpcaPlanes& P, double* par
 cudaError_t rpca_launch_post_pre(const RpcaGeom& g, const RpcaCoeffs& c, const RpcaPlanes& P, double* partials,
                                  cudaStream_t st) {
   rpca_post_pre_kernel<<<rpca_num_blocks(g), kRpcaThreads, 0, st>>>(g, c, P, partials);
+  return cudaGetLastError();
+}
+
+// CTAs of the Gram-fused pass = its partial Grams: at most two per SM, one
+// per chunk, and no more than the residual rows it writes (rpca_num_blocks).
+int rpca_gram_parts(const RpcaGeom& g) {
+  long long n = (g.plane + kGC - 1) / kGC;
+  if (n > 2 * 152) n = 2 * 152;
+  const int nr = rpca_num_blocks(g);
+  if (n > nr) n = nr;
+  return (int)(n < 1 ? 1 : n);
+}
+
+cudaError_t rpca_launch_post_pre_gram(const RpcaGeom& g, const RpcaCoeffs& c, const RpcaPlanes& P, int TP,
+                                      double* partials, int nrows, float* gpart, cudaStream_t st) {
+  const int grid = rpca_gram_parts(g);
+  switch (TP) {
+    case 16: rpca_post_pre_gram_kernel<16><<<grid, kFGThreads, 0, st>>>(g, c, P, partials, nrows, gpart); break;
+    case 32: rpca_post_pre_gram_kernel<32><<<grid, kFGThreads, 0, st>>>(g, c, P, partials, nrows, gpart); break;
+    case 64: rpca_post_pre_gram_kernel<64><<<grid, kFGThreads, 0, st>>>(g, c, P, partials, nrows, gpart); break;
+    default: return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
 }
 

@@ -219,9 +219,10 @@ def test_rpca_graph_replay_matches_eager(lib):
 
 def test_fused_passes_match_separate_iterations(lib):
     """Inside one call, lines 12-15 of an outer iteration and lines 4-9 of the
-    next run as one pass.  The iterates equal those of one iteration per call
-    (every pass separate) bit for bit, eager and replayed from the interval
-    graph, and so do the residuals read at the end."""
+    next run as one pass that also accumulates the next Gram matrix.  Enqueued
+    directly and replayed from the interval graph the iterates agree bit for
+    bit; against one iteration per call (every pass separate, the Gram by the
+    tensor-core kernel) they differ only by the Gram's FP32 summation order."""
     Y, _, _ = rpca_video(rng_for(1, 61), T=8, H=40, W=36, n_blobs=2)
     out, res = [], []
     for variant in ("single", "interval", "graph"):
@@ -241,11 +242,14 @@ def test_fused_passes_match_separate_iterations(lib):
                     r = rp.iterate_checked(6)  # warm: the interval graph
                 out.append({k: rp.get(k).cpu() for k in ("S", "L", "X", "T", "A", "D", "B", "C", "Z", "W", "a")})
                 res.append(r)
+    ny = float(np.linalg.norm(Y.astype(np.float64)))
     for k in out[0]:
-        assert torch.equal(out[0][k], out[1][k]), ("interval", k)
-        assert torch.equal(out[0][k], out[2][k]), ("graph", k)
-    for r in res[1:]:
-        assert r["res_pri"] == res[0]["res_pri"] and r["res_dual"] == res[0]["res_dual"]
+        assert torch.equal(out[1][k], out[2][k]), ("graph", k)
+        e = float(torch.linalg.norm(out[0][k].double() - out[1][k].double()))
+        assert e <= 1e-5 * ny, (k, e / ny)
+    assert res[1]["res_pri"] == res[2]["res_pri"] and res[1]["res_dual"] == res[2]["res_dual"]
+    assert res[1]["res_pri"] == pytest.approx(res[0]["res_pri"], rel=1e-3)
+    assert res[1]["res_dual"] == pytest.approx(res[0]["res_dual"], rel=1e-3)
 
 
 def test_step_profiled_is_two_outer_iterations(lib):
@@ -259,7 +263,7 @@ def test_step_profiled_is_two_outer_iterations(lib):
             rp.step(1)
             if profiled:
                 ms = rp.step_profiled()
-                assert len(ms) == 7 and all(m > 0 for m in ms)
+                assert len(ms) == 8 and all(m > 0 for m in ms)
             else:
                 rp.step(2)
             rp.step(1)
