@@ -137,28 +137,30 @@ __global__ void __launch_bounds__(32 * kRedWarps) gram_reduce_kernel(const P* __
 
 // C = op(A) * diag(d) * B for TP x TP shared matrices (leading dimension
 // LDA).  Threads take 4 x 4 output blocks in turn.  transA: use A^T.
-template <int TP, int LDA>
+// RB x 4 output blocks (RB = 4 by default; 2 spreads a 64 x 64 product over
+// 512 threads).
+template <int TP, int LDA, int RB = 4>
 __device__ __forceinline__ void small_gemm(const float* A, const float* B, float* C, bool transA, const float* diag) {
-  constexpr int NB = TP / 4;            // 4 x 4 blocks per side
-  for (int blk = threadIdx.x; blk < NB * NB; blk += blockDim.x) {
-    const int by = blk / NB, bx = blk % NB;
-    float acc[4][4] = {};
+  constexpr int NBR = TP / RB, NBC = TP / 4;   // blocks per column, per row
+  for (int blk = threadIdx.x; blk < NBR * NBC; blk += blockDim.x) {
+    const int by = blk / NBC, bx = blk % NBC;
+    float acc[RB][4] = {};
     for (int k = 0; k < TP; ++k) {
-      float a[4], b[4];
+      float a[RB], b[4];
       const float dk = diag ? diag[k] : 1.f;
 #pragma unroll
-      for (int r = 0; r < 4; ++r) a[r] = transA ? A[k * LDA + 4 * by + r] : A[(4 * by + r) * LDA + k];
+      for (int r = 0; r < RB; ++r) a[r] = transA ? A[k * LDA + RB * by + r] : A[(RB * by + r) * LDA + k];
 #pragma unroll
       for (int c = 0; c < 4; ++c) b[c] = dk * B[k * LDA + 4 * bx + c];
 #pragma unroll
-      for (int r = 0; r < 4; ++r)
+      for (int r = 0; r < RB; ++r)
 #pragma unroll
         for (int c = 0; c < 4; ++c) acc[r][c] = fmaf(a[r], b[c], acc[r][c]);
     }
 #pragma unroll
-    for (int r = 0; r < 4; ++r)
+    for (int r = 0; r < RB; ++r)
 #pragma unroll
-      for (int c = 0; c < 4; ++c) C[(4 * by + r) * LDA + 4 * bx + c] = acc[r][c];
+      for (int c = 0; c < 4; ++c) C[(RB * by + r) * LDA + 4 * bx + c] = acc[r][c];
   }
 }
 
@@ -420,7 +422,7 @@ jacobi_reg_kernel(const double* __restrict__ G, int warm, float theta, int max_s
   float* Tmp = V + TP * LDA;              // [TP][LDA]
   float* f = Tmp + TP * LDA;              // [TP]
   __shared__ float s_rot[2][3][NP];       // (c, s, t) of each pair, by round parity
-  __shared__ unsigned char s_pl[R][TP];   // index held by each slot at round r
+  __shared__ unsigned char s_pl[TP];      // index held by each slot after the last round
   __shared__ float s_slope[TP];
   __shared__ unsigned char s_act[TP];
   __shared__ float red[2][NW];
@@ -428,16 +430,6 @@ jacobi_reg_kernel(const double* __restrict__ G, int warm, float theta, int max_s
   __shared__ float s_eps;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
-  for (int e = tid; e < R * TP; e += kJregThreads) {
-    const int r = e / TP, slot = e % TP;
-    int pl = 0;
-    if (slot != 0) {
-      const int ring = slot < NP ? slot - 1 : TP - 2 - (slot - NP);
-      const int j = ((ring - r) % R + R) % R;       // ring position this slot's index started from
-      pl = j <= NP - 2 ? j + 1 : NP + TP - 2 - j;
-    }
-    s_pl[r][slot] = (unsigned char)pl;
-  }
   // applier threads: their pair blocks (read offsets in the current buffer,
   // write offsets at the shifted slots in the next); kind 0 none, 1 off-diagonal, 2 own pair
   int rd[NBT][4], wr[NBT][4], bkb[NBT], bkc[NBT], kind[NBT];
@@ -535,9 +527,9 @@ jacobi_reg_kernel(const double* __restrict__ G, int warm, float theta, int max_s
   }
   __syncthreads();
   if (warm) {   // A <- V^T G V
-    small_gemm<TP, LDA>(A, V, Tmp, false, nullptr);
+    small_gemm<TP, LDA, (TP >= 32 ? 2 : 4)>(A, V, Tmp, false, nullptr);
     __syncthreads();
-    small_gemm<TP, LDA>(V, Tmp, A, true, nullptr);
+    small_gemm<TP, LDA, (TP >= 32 ? 2 : 4)>(V, Tmp, A, true, nullptr);
     __syncthreads();
   }
   for (int e = tid; e < TP * TP; e += kJregThreads) {   // symmetric part into the upper triangle
@@ -587,14 +579,17 @@ jacobi_reg_kernel(const double* __restrict__ G, int warm, float theta, int max_s
         red[1][warp] = dg;
       }
       __syncthreads();
-      if (tid == 0) {
-        float so = 0.f, sd = 0.f;
-        for (int w = 0; w < NW; ++w) {
-          so += red[0][w];
-          sd += red[1][w];
+      if (warp == 0) {
+        float so = lane < NW ? red[0][lane] : 0.f, sd = lane < NW ? red[1][lane] : 0.f;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          so += __shfl_down_sync(0xffffffffu, so, o);
+          sd += __shfl_down_sync(0xffffffffu, sd, o);
         }
-        s_go = so > tol * tol * sd;
-        s_eps = sqrtf(so);
+        if (lane == 0) {
+          s_go = so > tol * tol * sd;
+          s_eps = sqrtf(so);
+        }
       }
       __syncthreads();
       if (s_go && theta > 0.f) {   // the weighted test
@@ -627,13 +622,14 @@ jacobi_reg_kernel(const double* __restrict__ G, int warm, float theta, int max_s
           red[1][warp] = fmax;
         }
         __syncthreads();
-        if (tid == 0) {
-          float sw = 0.f, fm = 0.f;
-          for (int w = 0; w < NW; ++w) {
-            sw += red[0][w];
-            fm = fmaxf(fm, red[1][w]);
+        if (warp == 0) {
+          float sw = lane < NW ? red[0][lane] : 0.f, fm = lane < NW ? red[1][lane] : 0.f;
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) {
+            sw += __shfl_down_sync(0xffffffffu, sw, o);
+            fm = fmaxf(fm, __shfl_down_sync(0xffffffffu, fm, o));
           }
-          if (sw <= tol * tol * fm * fm) s_go = 0;
+          if (lane == 0 && sw <= tol * tol * fm * fm) s_go = 0;
         }
         __syncthreads();
       }
@@ -717,8 +713,18 @@ jacobi_reg_kernel(const double* __restrict__ G, int warm, float theta, int max_s
     cur ^= 1;
     __syncthreads();
   }
-  // slot s holds index s_pl[r][s]
-  const unsigned char* pl = s_pl[r];
+  // slot s holds index pl[s] after round r of the sweep
+  for (int slot = tid; slot < TP; slot += kJregThreads) {
+    int idx = 0;
+    if (slot != 0) {
+      const int ring = slot < NP ? slot - 1 : TP - 2 - (slot - NP);
+      const int j = ((ring - r) % R + R) % R;       // ring position this slot's index started from
+      idx = j <= NP - 2 ? j + 1 : NP + TP - 2 - j;
+    }
+    s_pl[slot] = (unsigned char)idx;
+  }
+  __syncthreads();
+  const unsigned char* pl = s_pl;
   if (vown) {
 #pragma unroll
     for (int j = 0; j < kJregM; ++j) {
@@ -739,7 +745,7 @@ jacobi_reg_kernel(const double* __restrict__ G, int warm, float theta, int max_s
   }
   __syncthreads();
   float* Out = sm + (cur ^ 1) * (TP * LDA);
-  small_gemm<TP, LDA>(V, Tmp, Out, false, f);    // V diag(f) V^T
+  small_gemm<TP, LDA, (TP >= 32 ? 2 : 4)>(V, Tmp, Out, false, f);    // V diag(f) V^T
   __syncthreads();
   for (int e = tid; e < TP * TP; e += kJregThreads) {
     const int i = e / TP, j = e % TP;
