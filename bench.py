@@ -193,10 +193,10 @@ def prox_inputs(rank: int):
 def rpca_phase_bytes(T: int, N: int, n_inner: int) -> list:
     """Algorithmic DRAM bytes of each phase of one outer iteration (one read
     and one write of each plane touched; frames T, pairs T-1, N pixels; the
-    fused pass's FP32 partial Grams: min(N / 64, 304) of T_pad^2)."""
+    fused pass.s FP32 partial Grams: min(N / 64, 152) of T_pad^2)."""
     P = T - 1
     TP = 16 if T <= 16 else 32 if T <= 32 else 64
-    gparts = 4.0 * min((N + 63) // 64, 2 * 152) * TP * TP
+    gparts = 4.0 * min((N + 63) // 64, 152) * TP * TP
     return [4.0 * N * (10 * T + 8 * P),        # pre: reads X L A Tm D Y z b w c, writes S L X LD p0 p1 z' w'
             4.0 * N * T,                      # Gram: reads L+D
             0.0,                              # T x T eigensolver

@@ -243,22 +243,25 @@ rpca_post_pre_kernel(const RpcaGeom g, const RpcaCoeffs c, const RpcaPlanes P, d
 // rows blockIdx.x + k gridDim.x < nrows of partials are written (zero beyond
 // the CTA's own), so the residual finalisation sees nrows rows as before.
 constexpr int kGC = 64;             // pixels per Gram chunk
-constexpr int kFGThreads = 256;
+constexpr int kFGThreads = 512;   // one CTA per SM: 152 partial Grams
 
 template <int TP>
-__global__ void __launch_bounds__(kFGThreads, 2)
+__global__ void __launch_bounds__(kFGThreads, 1)
 rpca_post_pre_gram_kernel(const RpcaGeom g, const RpcaCoeffs c, const RpcaPlanes P, double* __restrict__ partials,
                           int nrows, float* __restrict__ gpart) {
-  constexpr int BE = TP / 16;       // Gram block edge per thread
+  // Gram blocks of RB x CB entries on an (TP / RB) x (TP / CB) thread grid
+  constexpr int RB = TP >= 64 ? 2 : 1, CB = TP >= 32 ? 4 : 1;
+  constexpr int NCB = TP / CB;
   constexpr int LDS = TP + 4;       // padded row of the staged tile (16-byte aligned)
   __shared__ __align__(16) float sLD[kGC][LDS];
   float acc[kNumSums] = {};
-  float gacc[BE][BE];
+  float gacc[RB][CB];
 #pragma unroll
-  for (int r = 0; r < BE; ++r)
+  for (int r = 0; r < RB; ++r)
 #pragma unroll
-    for (int q = 0; q < BE; ++q) gacc[r][q] = 0.f;
-  const int tid = threadIdx.x, bi = tid / 16, bj = tid % 16;
+    for (int q = 0; q < CB; ++q) gacc[r][q] = 0.f;
+  const int tid = threadIdx.x, bi = tid / NCB, bj = tid % NCB;
+  const bool gown = bi < TP / RB;   // the whole grid for TP >= 32; half the threads for TP = 16
   for (int e = tid; e < kGC * LDS; e += kFGThreads) (&sLD[0][0])[e] = 0.f;   // frames T..TP-1 stay zero
   __syncthreads();
   const float rho = c.rho, inv1r = 1.f / (1.f + c.rho);
@@ -323,24 +326,25 @@ rpca_post_pre_gram_kernel(const RpcaGeom g, const RpcaCoeffs c, const RpcaPlanes
     __syncthreads();
 #pragma unroll 4
     for (int p = 0; p < kGC; ++p) {
-      float av[BE], bv[BE];
+      float av[RB], bv[CB];
 #pragma unroll
-      for (int r = 0; r < BE; ++r) {
-        av[r] = sLD[p][BE * bi + r];
-        bv[r] = sLD[p][BE * bj + r];
-      }
+      for (int r = 0; r < RB; ++r) av[r] = sLD[p][gown ? RB * bi + r : 0];
 #pragma unroll
-      for (int r = 0; r < BE; ++r)
+      for (int q = 0; q < CB; ++q) bv[q] = sLD[p][CB * bj + q];
 #pragma unroll
-        for (int q = 0; q < BE; ++q) gacc[r][q] = fmaf(av[r], bv[q], gacc[r][q]);
+      for (int r = 0; r < RB; ++r)
+#pragma unroll
+        for (int q = 0; q < CB; ++q) gacc[r][q] = fmaf(av[r], bv[q], gacc[r][q]);
     }
     __syncthreads();
   }
   float* out = gpart + (size_t)blockIdx.x * TP * TP;
+  if (gown) {
 #pragma unroll
-  for (int r = 0; r < BE; ++r)
+    for (int r = 0; r < RB; ++r)
 #pragma unroll
-    for (int q = 0; q < BE; ++q) out[(BE * bi + r) * TP + BE * bj + q] = gacc[r][q];
+      for (int q = 0; q < CB; ++q) out[(RB * bi + r) * TP + CB * bj + q] = gacc[r][q];
+  }
   block_sums_to<kFGThreads>(acc, partials + (size_t)blockIdx.x * kNumSums);
   for (int row = blockIdx.x + gridDim.x; row < nrows; row += gridDim.x)
     if (tid < kNumSums) partials[(size_t)row * kNumSums + tid] = 0.0;
@@ -382,11 +386,11 @@ cudaError_t rpca_launch_post_pre(const RpcaGeom& g, const RpcaCoeffs& c, const R
   return cudaGetLastError();
 }
 
-// CTAs of the Gram-fused pass = its partial Grams: at most two per SM, one
+// CTAs of the Gram-fused pass = its partial Grams: at most one per SM, one
 // per chunk, and no more than the residual rows it writes (rpca_num_blocks).
 int rpca_gram_parts(const RpcaGeom& g) {
   long long n = (g.plane + kGC - 1) / kGC;
-  if (n > 2 * 152) n = 2 * 152;
+  if (n > 152) n = 152;
   const int nr = rpca_num_blocks(g);
   if (n > nr) n = nr;
   return (int)(n < 1 ? 1 : n);
