@@ -676,7 +676,11 @@ def run_ours_warmstart(args, rank, world, local_rank):
                      "frac": achieved / peaks["bf16_tflops"], "traffic": None,
                      "kernel": "U-Net forward (13 tcgen05 convolutions + CUDA-core layers), whole pass",
                      "peak_source": peaks["source"] + " bf16 (of measured)"},
-        "gpu_launches": None, "e2e": None, "clocks": clocks,
+        # one warm solve: the U-Net forward (enc0a, 13 tensor-core convolutions,
+        # 3 poolings, 3 upsamplings, the head), the state write, and per
+        # check interval 10 Algorithm 1 iterations plus the residual pass
+        "gpu_launches": 22 + warm[0]["iters"] + warm[0]["iters"] // kw["check_every"],
+        "e2e": None, "clocks": clocks,
     }
 
 
