@@ -178,9 +178,9 @@ def max_over_ranks(vals, world: int, device: str = "cuda") -> list:
 
 # --------------------------------------------------------------------- inputs
 def rpca_inputs(rank: int, T=T_FRAMES, H=HEIGHT, W=WIDTH):
-    from synth import config2_video, rng_for, rpca_video
+    from synth import rpca_video_64x256x256, rng_for, rpca_video
     if rank == 0 and (T, H, W) == (T_FRAMES, HEIGHT, WIDTH):
-        return config2_video()[0]
+        return rpca_video_64x256x256()[0]
     return rpca_video(rng_for(1, 100 + rank), T, H, W)[0]
 
 
@@ -500,7 +500,7 @@ def batch_inputs(rank: int):
 
 
 def run_ours_batch(args, rank, world, local_rank):
-    """Config 3: every sequence solved to 1e-5 by one launch per iteration over
+    """The uneven batch: every sequence solved to 1e-5 by one launch per iteration over
     all active sequences (autotuned, graph-captured), against one handle per
     sequence solved in turn (per-sequence plain launches).  A step is one
     full solve of all 48 sequences."""
@@ -573,8 +573,9 @@ UNET_MACS_PER_PIXEL = 161984   # multiply-adds of the warm-start U-Net's forward
 
 
 def warmstart_pairs(seed: int, n: int, S: int):
-    """n consecutive-frame pairs of 17-frame S x S blob videos (config-1
-    blobs and moves, 3-8 blobs a video): the evaluation's distribution."""
+    """n consecutive-frame pairs of 17-frame S x S blob videos (blobs of
+    sigma 3 px, amplitude U[0.5, 1], moves in [-4, 4]^2 per frame, 3-8 blobs
+    a video): the evaluation's distribution."""
     from synth import blob_video, rng_for
     rng = rng_for(5, seed)
     p0s, p1s = [], []
@@ -587,7 +588,7 @@ def warmstart_pairs(seed: int, n: int, S: int):
 
 
 def run_ours_warmstart(args, rank, world, local_rank):
-    """The learned warm start (config 5, scaled): train the U-Net with the
+    """The learned warm start (training scaled down): train the U-Net with the
     library's kernels on pairs the plain solver takes to 1e-5, then solve every
     frame pair of a T-frame blob video at the evaluation size from zero and
     from the network's prediction, both to the same 1e-5 stopping rule.  A
@@ -662,7 +663,7 @@ def run_ours_warmstart(args, rank, world, local_rank):
         "value": tw, "unit": "s", "n_gpus": world, "steps": args.steps, "warmup": 1, "ms_per_step": tw * 1e3,
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32 solver, bf16 network",
         "data": "synthetic",
-        "config": {"workload": f"warmstart: train on {ntr} config-1 pairs at {S}x{S} (3-8 blobs), evaluate on the "
+        "config": {"workload": f"warmstart: train on {ntr} blob-video pairs at {S}x{S} (3-8 blobs), evaluate on the "
                                f"{B} pairs of a {Te}-frame {Se}x{Se} blob video", **kw,
                    "epochs": E, "batch": 16, "bias_free": args.ws_bias_free, "l2": "inputs larger than L2"},
         "cold": {"seconds": tc, "iters": cold[0]["iters"], "status": cold[0]["status"]},

@@ -27,9 +27,9 @@ import numpy as np
 SEED0 = 190900149
 
 
-def rng_for(config_index: int, stream: int = 0) -> np.random.Generator:
-    """PCG64 generator seeded from the workload index (and an optional stream)."""
-    return np.random.Generator(np.random.PCG64([SEED0 + config_index, stream]))
+def rng_for(workload: int, stream: int = 0) -> np.random.Generator:
+    """PCG64 generator seeded from a workload number (and an optional stream)."""
+    return np.random.Generator(np.random.PCG64([SEED0 + workload, stream]))
 
 
 def _blob(H: int, W: int, cy: float, cx: float, amp: float, sigma: float) -> np.ndarray:
@@ -140,13 +140,13 @@ def uneven_sequences(rng: np.random.Generator, n_seq: int = 48,
     return seqs
 
 
-def config1_pair(H: int = 64, W: int = 64):
+def blob_pair_64x64(H: int = 64, W: int = 64):
     """Single 64x64 frame pair: 3 blobs, integer shifts in [-4, 4], one blob
     rescaled by U[0.5, 1.5].  Returns (p0, p1) shaped [1, H, W]."""
     return blob_pairs(rng_for(0), 1, H, W, n_blobs=3)
 
 
-def config2_video(T: int = 64, H: int = 256, W: int = 256):
+def rpca_video_64x256x256(T: int = 64, H: int = 256, W: int = 256):
     """The 64-frame 256x256 RPCA video (rank-3 clutter, 8 moving blobs,
     noise 0.02).  Returns (Y, L, S)."""
     return rpca_video(rng_for(1), T, H, W)

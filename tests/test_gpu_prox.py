@@ -18,7 +18,7 @@ import torch
 
 from oracle import grid
 from oracle import prox as P
-from synth import blob_pairs, config1_pair, rng_for
+from synth import blob_pairs, blob_pair_64x64, rng_for
 
 pytestmark = pytest.mark.gpu
 
@@ -60,7 +60,7 @@ def check_state(g, o: P.ProxState, tol, scale):
 @pytest.mark.parametrize("k,tol", [(1, 1e-6), (10, 1e-5), (500, 1e-5)])
 def test_trajectory_parity_64x64_pair(lib, kernel, k, tol):
     """The 64x64 frame pair: 3 blobs, shifts in [-4, 4], one blob rescaled."""
-    p0, p1 = config1_pair()
+    p0, p1 = blob_pair_64x64()
     g = gpu_iterate(lib, p0, p1, k, mu=MU, rho=RHO, kernel=kernel)
     o = P.iterate(p0.astype(np.float64), p1.astype(np.float64), oracle_params(), k)
     check_state(g, o, tol, np.linalg.norm(p0))
@@ -123,7 +123,7 @@ def _gpu_masks(g):
 def test_support_masks_bit_exact_one_step(lib, kernel):
     """One iteration from an identical FP32 state: the flux, source and
     non-negativity masks agree bit for bit outside a 1e-5 guard band."""
-    p0, p1 = config1_pair()
+    p0, p1 = blob_pair_64x64()
     prm = oracle_params()
     st = _oracle_state_f32(p0, p1, 300, prm)
     g = gpu_iterate(lib, p0, p1, 1, state=st, mu=MU, rho=RHO, kernel=kernel)
@@ -141,7 +141,7 @@ def test_support_masks_bit_exact_one_step(lib, kernel):
 
 @pytest.mark.parametrize("kernel", ["tiled", "resident", "tma"])
 def test_support_masks_after_500_iterations(lib, kernel):
-    p0, p1 = config1_pair()
+    p0, p1 = blob_pair_64x64()
     prm = oracle_params()
     g = gpu_iterate(lib, p0, p1, 500, mu=MU, rho=RHO, kernel=kernel)
     st499 = _oracle_state_f32(p0, p1, 499, prm)
@@ -180,7 +180,7 @@ def test_solve_matches_oracle(lib, kernel):
 
 
 def test_evaluate_matches_oracle_certificate(lib):
-    p0, p1 = config1_pair()
+    p0, p1 = blob_pair_64x64()
     prm = P.default_steps(64, 64, oracle_params())
     st = _oracle_state_f32(p0, p1, 200, prm)
     with lib.OtProx(1, 64, 64, mu=MU, rho=RHO) as s:
@@ -199,7 +199,7 @@ def test_evaluate_matches_oracle_certificate(lib):
 @pytest.mark.parametrize("kernel", ["tiled", "resident", "tma"])
 def test_warm_restart_is_bit_exact(lib, kernel):
     """Checkpoint/resume: 500 iterations == 250 + get_state/set_state + 250."""
-    p0, p1 = config1_pair()
+    p0, p1 = blob_pair_64x64()
     a = gpu_iterate(lib, p0, p1, 500, mu=MU, rho=RHO, kernel=kernel)
     h = gpu_iterate(lib, p0, p1, 250, mu=MU, rho=RHO, kernel=kernel)
     b = gpu_iterate(lib, p0, p1, 250, state={k: v.astype(np.float32) for k, v in h.items()}, mu=MU, rho=RHO,
@@ -210,7 +210,7 @@ def test_warm_restart_is_bit_exact(lib, kernel):
 
 @pytest.mark.parametrize("other", ["resident", "tma"])
 def test_kernels_agree(lib, other):
-    p0, p1 = config1_pair()
+    p0, p1 = blob_pair_64x64()
     a = gpu_iterate(lib, p0, p1, 200, mu=MU, rho=RHO, kernel="tiled")
     b = gpu_iterate(lib, p0, p1, 200, mu=MU, rho=RHO, kernel=other)
     for k in NAMES:
@@ -255,7 +255,7 @@ def test_nonfinite_input_is_reported(lib):
 
 
 def test_max_iter_reports_not_converged(lib):
-    p0, p1 = config1_pair()
+    p0, p1 = blob_pair_64x64()
     with lib.OtProx(1, 64, 64, mu=MU, rho=RHO, max_iter=20, tol=1e-12) as s:
         s.set_input(p0, p1)
         res = s.solve()

@@ -176,8 +176,8 @@ def test_rpca_solve_converges_and_matches_oracle(lib):
 def test_rpca_full_size_two_iterations(lib):
     """The 64-frame 256x256 video (rank-3 clutter, 8 blobs, noise 0.02): two
     outer iterations of the benchmark's step against the oracle."""
-    from synth import config2_video
-    Y, _, _ = config2_video()
+    from synth import rpca_video_64x256x256
+    Y, _, _ = rpca_video_64x256x256()
     T, H, W = Y.shape
     gamma = RP["lam"] * np.sqrt(max(H * W, T))
     with lib.Rpca(T, H, W, **RP) as rp:
