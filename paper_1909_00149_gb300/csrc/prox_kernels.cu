@@ -419,10 +419,14 @@ cudaError_t launch_tiled_t(const Geometry& g, const IterCoeffs& c, const StatePt
   return cudaGetLastError();
 }
 
+// The attribute belongs to the kernel, not to a handle: raise it to the cap
+// of every resident geometry, so that a handle created later with a smaller
+// state cannot lower it under an earlier handle's launch size.
 template <int MODE, bool BAL>
 cudaError_t prepare_resident_t(const Geometry& g) {
+  (void)g;
   return cudaFuncSetAttribute(prox_resident_kernel<MODE, BAL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)resident_smem_bytes(g, MODE, BAL));
+                              (int)kResidentSmemCap);
 }
 
 template <int MODE, bool BAL>

@@ -278,3 +278,27 @@ def test_full_size_video_batch_parity(lib):
     check_state(g, o, 1e-5, np.linalg.norm(p0))
     obj = P.objective(o, p0.astype(np.float64), p1.astype(np.float64), P.default_steps(256, 256, oracle_params()))
     assert abs(res["objective"] - obj) <= 1e-5 * obj
+
+
+def test_resident_handles_of_different_sizes_coexist(lib):
+    """The shared-memory limit of the one-CTA-per-problem kernel belongs to
+    the kernel: a later handle with a smaller state must not lower it under
+    an earlier, larger handle."""
+    big = (3, 64, 64)
+    small = (2, 24, 24)
+    p_big = blob_pairs(rng_for(3, 91), *big, n_blobs=2)
+    p_small = blob_pairs(rng_for(3, 92), *small, n_blobs=2)
+    with lib.OtProx(*big, kernel="resident", mu=3.0, rho=0.01) as a, \
+            lib.OtProx(*small, kernel="resident", mu=3.0, rho=0.01) as b:
+        a.set_input(*p_big)
+        b.set_input(*p_small)
+        a.step(20)
+        b.step(20)
+        a.step(20)
+        st = a.get_state()
+    with lib.OtProx(*big, kernel="resident", mu=3.0, rho=0.01) as c:
+        c.set_input(*p_big)
+        c.step(40)
+        ref = c.get_state()
+    for k in ("Mx", "a"):
+        assert torch.equal(st[k], ref[k]), k
