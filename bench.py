@@ -193,7 +193,7 @@ def prox_inputs(rank: int):
 def rpca_phase_bytes(T: int, N: int, n_inner: int) -> list:
     """Algorithmic DRAM bytes of each phase of one outer iteration (one read
     and one write of each plane touched; frames T, pairs T-1, N pixels; the
-    fused pass.s FP32 partial Grams: min(N / 64, 152) of T_pad^2)."""
+    fused pass's FP32 partial Grams: min(N / 64, 152) of T_pad^2)."""
     P = T - 1
     TP = 16 if T <= 16 else 32 if T <= 32 else 64
     gparts = 4.0 * min((N + 63) // 64, 152) * TP * TP
