@@ -51,11 +51,12 @@ OUTER_PER_STEP = 10          # Algorithm 3 outer iterations per step (one residu
 RPCA_KW = dict(lam=0.02, kappa=0.005, mu=3.0, rho=1.0, check_every=OUTER_PER_STEP)
 PHASES = ["rpca_pre_kernel (Alg. 3 lines 4-9)", "gram_partial/reduce (SVT Gram)", "jacobi_svt_kernel (T x T eig)",
           "svt_apply_kernel (SVT apply)", "prox_tma_kernel (Alg. 1 iterations)", "rpca_post_kernel (Alg. 3 lines 12-15)",
-          "rpca_post_pre_gram_kernel (lines 12-15 fused with the next lines 4-9 and its Gram partials)",
-          "gram_reduce_kernel (the Gram after the fused pass: FP64 sum of its partials)"]
+          "rpca_post_pre_gram_kernel (lines 12-15 fused with the next lines 4-9 and its Gram, partials reduced "
+          "in the same cooperative launch)",
+          "(no launch: the Gram after the fused pass comes out of it)"]
 # launches of each phase in one step (a check interval): the first lines 4-9,
 # its Gram and the last lines 12-15 run alone, the others fused
-PHASE_COUNT = [1, 1, OUTER_PER_STEP, OUTER_PER_STEP, OUTER_PER_STEP, 1, OUTER_PER_STEP - 1, OUTER_PER_STEP - 1]
+PHASE_COUNT = [1, 1, OUTER_PER_STEP, OUTER_PER_STEP, OUTER_PER_STEP, 1, OUTER_PER_STEP - 1, 0]
 PROFILE_FILES = {  # kernel -> (ncu summary holding its DRAM traffic per launch, its source file)
     "prox_tma_kernel": ("prox_tma_63x256x256.md", "prox_tma.cu"),
     "rpca_pre_kernel": ("rpca_step_64x256x256.md", "rpca_kernels.cu"),
@@ -193,7 +194,8 @@ def prox_inputs(rank: int):
 def rpca_phase_bytes(T: int, N: int, n_inner: int) -> list:
     """Algorithmic DRAM bytes of each phase of one outer iteration (one read
     and one write of each plane touched; frames T, pairs T-1, N pixels; the
-    fused pass's FP32 partial Grams: min(N / 64, 152) of T_pad^2)."""
+    fused pass's FP32 partial Grams, min(N / 64, 152) of T_pad^2, written and
+    read back by the same launch, and its FP64 Gram)."""
     P = T - 1
     TP = 16 if T <= 16 else 32 if T <= 32 else 64
     gparts = 4.0 * min((N + 63) // 64, 152) * TP * TP
@@ -203,8 +205,8 @@ def rpca_phase_bytes(T: int, N: int, n_inner: int) -> list:
             4.0 * N * 2 * T,                  # apply: reads L+D, writes the new Tm
             56.0 * N * P * n_inner,           # Algorithm 1: 56 B per pixel-iteration
             4.0 * N * (9 * T + 8 * P),        # post: reads X S L Tm Tm_old A D z z' b w w' c, writes A D b c
-            4.0 * N * (13 * T + 10 * P) + gparts,   # post + pre (+ the Gram partials)
-            gparts]                           # Gram reduce: reads the partials
+            4.0 * N * (13 * T + 10 * P) + 2 * gparts + 8.0 * TP * TP,   # post + pre + the Gram
+            0.0]                              # no separate Gram reduction
 
 
 # --------------------------------------------------------------------- our arm
@@ -309,9 +311,10 @@ def run_ours_rpca(args, rank, world, local_rank):
                 "d2h_bytes_per_step": 8 * 8 + 4 + 4 * 64 + 4},
         # per step: lines 4-9 and their Gram (2 kernels) once; per outer
         # iteration the eigensolver, apply and n_inner prox; between outer
-        # iterations the fused pass and the Gram reduction; the last lines
-        # 12-15 and the residual finalisation once
-        "gpu_launches": (2 * OUTER_PER_STEP + 3 + (2 + args.n_inner) * OUTER_PER_STEP) * args.steps,
+        # iterations the fused pass (which also yields the next Gram); the
+        # first Gram's reduction, the last lines 12-15 and the residual
+        # finalisation once
+        "gpu_launches": (OUTER_PER_STEP + 4 + (2 + args.n_inner) * OUTER_PER_STEP) * args.steps,
         "clocks": clocks,
     }
     if not args.no_cpu_baseline:

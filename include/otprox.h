@@ -280,8 +280,9 @@ int ot_rpca_solve(ot_rpca_t h, ot_rpca_result* res);
  * first, 1 its Gram matrix, 2 its T x T eigensolver, 3 its SVT apply, 4 its
  * n_inner Algorithm 1 iterations, 5 lines 12-15 of the second (alone),
  * 6 lines 12-15 of the first fused with lines 4-9 of the second (and, for
- * T <= 64, the second's Gram partials), 7 the second's Gram (the reduction
- * of those partials for T <= 64).  Sync. */
+ * T <= 64, the second's Gram matrix, its partials reduced in the same
+ * launch), 7 the second's Gram where the fused pass does not produce it
+ * (T > 64; about 0 otherwise).  Sync. */
 int ot_rpca_step_profiled(ot_rpca_t h, double* phase_ms);
 
 /* Copy one variable (OT_RPCA_*) out, dense.  Sync. */
@@ -490,6 +491,19 @@ int ot_neumann_solve(const float* X, float* Y, int32_t B, int32_t H, int32_t W, 
 int ot_prox_evaluate_noalloc(const ot_prox_params* params, const float* p0, const float* p1,
                              const float* Mx, const float* My, const float* x0, const float* x1,
                              const float* r, const float* a, ot_prox_result* res, void* cuda_stream);
+
+/* ----------------------------------------------------------- diagnostics */
+/* Runs the grid barrier of the fused Algorithm 3 pass (the one between outer
+ * iterations, Alg. 3 lines 12-15 and 4-10) on its own: `ctas` CTAs (1 to
+ * the device's SM count) launched cooperatively on a fresh barrier whose
+ * arrival count starts at `preset_count` (0 = the state every launch leaves
+ * behind).  With 0 every CTA passes and the generation advances by one; with
+ * any value from ctas upwards no arrival completes the barrier, every CTA's
+ * bounded wait (about a second) gives up and the error flag is set; the
+ * context stays usable.  Outputs (host): *err = the device error flag (0 or
+ * 1), *generation = the barrier's generation afterwards.  Synchronous on an
+ * internal stream.  Returns OT_EINVAL for ctas out of range. */
+int ot_debug_grid_barrier(int32_t ctas, uint32_t preset_count, int32_t* err, uint32_t* generation);
 
 /* Message of the last failing call on this thread ("" if none). */
 const char* ot_last_error(void);

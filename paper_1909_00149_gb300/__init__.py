@@ -252,8 +252,8 @@ class Rpca:
 
     def step_profiled(self) -> list:
         """Two outer iterations; device ms of their eight phases (see the C
-        header: pre, Gram, eigensolver, apply, prox, post, fused post + pre,
-        the second Gram)."""
+        header: pre, Gram, eigensolver, apply, prox, post, fused post + pre
+        (with the second Gram for T <= 64), the second Gram otherwise)."""
         ms = (ctypes.c_double * 8)()
         check(_lib.ot_rpca_step_profiled(self.h, ms), "ot_rpca_step_profiled")
         return list(ms)
@@ -532,4 +532,14 @@ def svt(X, theta: float, stream=None):
     return Y
 
 
-__all__ = ["ProxBatch", "Uotdf", "uotdf_default_params", "Rpca", "svt", "neumann_solve", "rpca_default_params", "OtProx", "OtError", "default_params", "check", "LIB_PATH", "ot_prox_params", "ot_prox_result"]
+def debug_grid_barrier(ctas: int, preset_count: int = 0) -> tuple[int, int]:
+    """Run the fused RPCA pass's grid barrier alone on ``ctas`` cooperative
+    CTAs with its arrival count preset; returns (error flag, generation)."""
+    err = ctypes.c_int32(0)
+    gen = ctypes.c_uint32(0)
+    check(_lib.ot_debug_grid_barrier(int(ctas), int(preset_count), ctypes.byref(err), ctypes.byref(gen)),
+          "ot_debug_grid_barrier")
+    return err.value, gen.value
+
+
+__all__ = ["debug_grid_barrier", "ProxBatch", "Uotdf", "uotdf_default_params", "Rpca", "svt", "neumann_solve", "rpca_default_params", "OtProx", "OtError", "default_params", "check", "LIB_PATH", "ot_prox_params", "ot_prox_result"]

@@ -120,6 +120,8 @@ PROTOTYPES = [
     ("ot_rpca_solve", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ot_rpca_result)]),
     ("ot_rpca_get", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]),
     ("ot_rpca_step_profiled", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
+    ("ot_debug_grid_barrier", ctypes.c_int, [ctypes.c_int32, ctypes.c_uint32, ctypes.POINTER(ctypes.c_int32),
+                                             ctypes.POINTER(ctypes.c_uint32)]),
     ("ot_rpca_reset", ctypes.c_int, [ctypes.c_void_p]),
     ("ot_rpca_get_params", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ot_rpca_params)]),
     ("ot_rpca_destroy", ctypes.c_int, [ctypes.c_void_p]),

@@ -197,11 +197,17 @@ cudaError_t rpca_launch_post(const RpcaGeom& g, const RpcaPlanes& P, double* par
 cudaError_t rpca_launch_post_pre(const RpcaGeom& g, const RpcaCoeffs& c, const RpcaPlanes& P, double* partials,
                                  cudaStream_t st);
 // the same pass accumulating iteration k + 1's Gram matrix (T padded to TP
-// in {16, 32, 64}): FP32 partials gpart[rpca_gram_parts(g)][TP][TP]; writes
-// nrows slot-0 rows of partials
+// in {16, 32, 64}): FP32 partials gpart[rpca_gram_parts(g)][TP][TP], reduced
+// in the same cooperative launch into G (TP x TP doubles); bar: two
+// zero-initialised unsigned ints owned by the caller (its grid barrier);
+// err is set if the barrier wait expires; writes nrows slot-0 rows of partials
 int rpca_gram_parts(const RpcaGeom& g);
 cudaError_t rpca_launch_post_pre_gram(const RpcaGeom& g, const RpcaCoeffs& c, const RpcaPlanes& P, int TP,
-                                      double* partials, int nrows, float* gpart, cudaStream_t st);
+                                      double* partials, int nrows, float* gpart, double* G, unsigned* bar, int* err,
+                                      cudaStream_t st);
+// the fused pass's grid barrier alone on `ctas` cooperative CTAs, its count
+// preset (diagnostic: ot_debug_grid_barrier)
+cudaError_t grid_barrier_probe(int ctas, unsigned preset, int* err, unsigned* generation);
 cudaError_t rpca_launch_sumsq(const RpcaGeom& g, const float* Y, double* partials, cudaStream_t st);
 
 // ----------------------------------------------------------------- SVT
@@ -212,8 +218,6 @@ int svt_apply_blocks(long long N, int T, int* gy);
 cudaError_t svt_prepare();
 cudaError_t svt_launch_gram(const float* X, long long ld, long long N, int T, double* partials, double* G, int* err,
                             cudaStream_t st);
-// G = the FP64 sum, in order, of nparts FP32 partial Grams [nparts][TP][TP]
-cudaError_t svt_launch_gram_reduce(const float* partials, int nparts, int T, double* G, cudaStream_t st);
 // tensor-core partial Grams (gram_tcgen05.cu); T > 16
 int svt_gram_tc_blocks(long long N);
 cudaError_t svt_launch_gram_tc(const float* X, long long ld, long long N, int T, float* partials, int* err,

@@ -40,9 +40,11 @@ struct ot_rpca {
   int TP;
   double* gram_partials;
   // T_pad <= 64: the fused pass between outer iterations also accumulates the
-  // next iteration's Gram matrix, as FP32 partials reduced before the eigensolver
+  // next iteration's Gram matrix, as FP32 partials that the same cooperative
+  // launch reduces into Gm
   float* fgram;
   int fgram_parts;
+  unsigned* fbar;   // the fused pass's grid barrier (count, generation), after fgram
   double* Gm;
   float* V;
   float* Wm;
@@ -202,7 +204,12 @@ int ot_rpca_create(const ot_rpca_params* params, void* cuda_stream, ot_rpca_t* o
   }
   if (e == cudaSuccess && TP <= 64) {
     h->fgram_parts = rpca_gram_parts(h->G);
-    e = cudaMalloc(&h->fgram, (size_t)h->fgram_parts * TP * TP * sizeof(float));
+    const size_t nf = (size_t)h->fgram_parts * TP * TP;
+    e = cudaMalloc(&h->fgram, nf * sizeof(float) + 4 * sizeof(unsigned));
+    if (e == cudaSuccess) {
+      h->fbar = reinterpret_cast<unsigned*>(h->fgram + nf);
+      e = cudaMemsetAsync(h->fbar, 0, 4 * sizeof(unsigned), h->stream);
+    }
   }
   if (e == cudaSuccess) e = svt_prepare();
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking);
@@ -276,7 +283,7 @@ static void swap_svt_planes(ot_rpca* h) {
 static cudaError_t launch_between(ot_rpca* h) {
   if (h->fgram)
     return rpca_launch_post_pre_gram(h->G, h->C, h->P, h->TP, pre_rows(h, h->tpar ^ 1), h->nb_rpca, h->fgram,
-                                     h->stream);
+                                     h->Gm, h->fbar, h->prox->derr, h->stream);
   return rpca_launch_post_pre(h->G, h->C, h->P, pre_rows(h, h->tpar ^ 1), h->stream);
 }
 
@@ -292,11 +299,9 @@ static int enqueue_interval(ot_rpca* h, int n, bool sums) {
   OT_CUDA(rpca_launch_pre(h->G, h->C, h->P, pre_rows(h, h->tpar), h->stream), "rpca pre");
   int last_par = h->tpar;
   for (int k = 0; k < n; ++k) {
-    // line 10: the Gram matrix, from the LD just written (after the fused
-    // pass only its partials are left to reduce)
-    if (k > 0 && h->fgram)
-      OT_CUDA(svt_launch_gram_reduce(h->fgram, h->fgram_parts, h->prm.T, h->Gm, h->stream), "svt gram reduce");
-    else
+    // line 10: the Gram matrix, from the LD just written (the fused pass
+    // before iterations k > 0 has already left it in Gm)
+    if (k == 0 || !h->fgram)
       OT_CUDA(svt_launch_gram(h->P.LD, plane, N, h->prm.T, h->gram_partials, h->Gm, h->prox->derr, h->stream),
               "svt gram");
     // fork: the one-CTA T x T eigensolver on the side stream, on the SM that
@@ -408,7 +413,7 @@ int ot_rpca_iterate_checked(ot_rpca_t h, int32_t n_outer, ot_rpca_result* res) {
   const int rc = run_interval(h, n_outer, true);
   if (rc != OT_OK) return rc;
   OT_CUDA(cudaStreamSynchronize(h->stream), "ot_rpca_iterate_checked: sync");
-  if (*h->prox->herr) return fail(OT_ETIMEOUT, "a bounded device wait expired in the prox kernel");
+  if (*h->prox->herr) return fail(OT_ETIMEOUT, "a bounded device wait expired (prox kernel or grid barrier)");
   ot_rpca_result r;
   memset(&r, 0, sizeof r);
   r.iters = n_outer;
@@ -454,6 +459,20 @@ int ot_rpca_solve(ot_rpca_t h, ot_rpca_result* res) {
   return status;
 }
 
+int ot_debug_grid_barrier(int32_t ctas, uint32_t preset_count, int32_t* err, uint32_t* generation) {
+  if (!err || !generation) return fail(OT_EINVAL, "ot_debug_grid_barrier: NULL argument");
+  int dev = 0, n_sm = 0;
+  OT_CUDA(cudaGetDevice(&dev), "ot_debug_grid_barrier: device");
+  OT_CUDA(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev), "ot_debug_grid_barrier: SM count");
+  if (ctas < 1 || ctas > n_sm) return fail(OT_EINVAL, "ot_debug_grid_barrier: ctas must be in [1, %d]", n_sm);
+  int e = 0;
+  unsigned gen = 0;
+  OT_CUDA(grid_barrier_probe(ctas, preset_count, &e, &gen), "ot_debug_grid_barrier");
+  *err = e;
+  *generation = gen;
+  return OT_OK;
+}
+
 int ot_rpca_step_profiled(ot_rpca_t h, double* phase_ms) {
   if (!h || !phase_ms) return fail(OT_EINVAL, "ot_rpca_step_profiled: NULL argument");
   if (!h->have_input) return fail(OT_EINVAL, "ot_rpca_step_profiled: no input (call ot_rpca_set_input)");
@@ -465,10 +484,8 @@ int ot_rpca_step_profiled(ot_rpca_t h, double* phase_ms) {
   int rc = OT_OK;
   // lines 10-11 of one outer iteration, every phase on the handle's stream
   auto middle = [&](bool after_fused, cudaEvent_t e1, cudaEvent_t e2, cudaEvent_t e3, cudaEvent_t e4) {
-    if (e == cudaSuccess)
-      e = (after_fused && h->fgram)
-              ? svt_launch_gram_reduce(h->fgram, h->fgram_parts, h->prm.T, h->Gm, h->stream)
-              : svt_launch_gram(h->P.LD, plane, plane, h->prm.T, h->gram_partials, h->Gm, h->prox->derr, h->stream);
+    if (e == cudaSuccess && !(after_fused && h->fgram))   // else the fused pass left G in Gm
+      e = svt_launch_gram(h->P.LD, plane, plane, h->prm.T, h->gram_partials, h->Gm, h->prox->derr, h->stream);
     if (e == cudaSuccess && e1) e = cudaEventRecord(e1, h->stream);
     if (e == cudaSuccess)
       e = svt_launch_eig(h->Gm, h->prm.T, h->warm, (float)(h->prm.gamma / h->prm.rho), h->prm.svt_max_sweeps,

@@ -233,113 +233,239 @@ rpca_post_pre_kernel(const RpcaGeom g, const RpcaCoeffs c, const RpcaPlanes P, d
 }
 
 // The fused pass of rpca_post_pre_kernel that also accumulates the SVT Gram
-// matrix of the LD = L + D it writes (Alg. 3 line 10 of iteration k + 1):
-// a CTA owns chunks of kGC consecutive pixels of a frame plane across all T
-// frames, stages their LD values in shared memory, and adds
-// LD_chunk^T LD_chunk to a TP x TP FP32 accumulator (a 16 x 16 grid of
-// threads, each a TP/16 x TP/16 block); every CTA writes its partial Gram to
-// gpart[blockIdx.x], and the FP64 reduction of the partials follows.  Per
-// (frame, pixel) the arithmetic is that of rpca_post_pre_kernel.  The slot-0
-// rows blockIdx.x + k gridDim.x < nrows of partials are written (zero beyond
-// the CTA's own), so the residual finalisation sees nrows rows as before.
-constexpr int kGC = 64;             // pixels per Gram chunk
-constexpr int kFGThreads = 512;   // one CTA per SM: 152 partial Grams
+// matrix of the LD = L + D it writes (Alg. 3 line 10 of iteration k + 1).
+// A CTA owns chunks of kGC consecutive pixels of a frame plane across all T
+// frames, taken in the order blockIdx.x, blockIdx.x + gridDim.x, ...  Its
+// warps are split by role so that the Gram arithmetic overlaps the memory
+// traffic instead of alternating with it:
+//   * kFGUpd updating warps run the per-(frame, pixel) arithmetic of
+//     rpca_post_pre_kernel on a chunk and leave its LD values in one of two
+//     shared-memory tiles;
+//   * kFGGram Gram warps add LD_chunk^T LD_chunk of the other tile to a
+//     TP x TP FP32 accumulator held in registers (RB x CB entries a thread),
+//     pixel by pixel in chunk order.
+// Hand-off through named barriers (hardware barriers; every warp of the CTA
+// runs the same number of chunks): kBarFull + b says tile b holds a chunk,
+// kBarEmpty + b that the Gram warps are done with it.  Every CTA writes its
+// partial Gram to gpart[blockIdx.x].  Then the CTAs meet at a grid barrier
+// (the launch is cooperative, so all of them are resident) and each sums
+// its slice of the TP x TP entries over the partials, in partial order and
+// FP64, into G.  The slot-0 rows blockIdx.x + k gridDim.x < nrows of partials
+// are written (zero beyond the CTA's own), so the residual finalisation sees
+// nrows rows as before.
+constexpr int kGC = 64;                          // pixels per Gram chunk
+constexpr int kFGUpd = 512;                      // updating threads (16 warps)
+constexpr int kFGGram = 128;                     // Gram threads (4 warps)
+constexpr int kFGThreads = kFGUpd + kFGGram;     // one CTA per SM: 152 partial Grams
+constexpr int kBarFull = 1, kBarEmpty = 3;       // named barriers 1-2 and 3-4 (0 is __syncthreads)
+
+__device__ __forceinline__ void named_sync(int id, int n) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+__device__ __forceinline__ void named_arrive(int id, int n) {
+  asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+
+constexpr unsigned kBarSpin = 1u << 20;         // polls (about 1 s) before the grid barrier gives up
+
+// Grid barrier over the gridDim.x resident CTAs of one launch: bar[0] counts
+// arrivals, bar[1] is a generation number that the last arriver advances
+// (after resetting the count, so the next launch starts from zero).  The
+// wait is bounded: on expiry *err is set and false returned.
+__device__ bool grid_barrier(unsigned* bar, int* err) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* gen = bar + 1;
+    const unsigned g0 = *gen;
+    __threadfence();
+    int ok = 1;
+    if (atomicAdd(bar, 1u) == gridDim.x - 1) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      for (unsigned it = 0; *gen == g0; ++it) {
+        if (it >= kBarSpin) {
+          atomicExch(err, 1);
+          ok = 0;
+          break;
+        }
+        __nanosleep(128);
+      }
+    }
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// CTA b's slice [b E / nb, (b + 1) E / nb) of G = sum of the nb = gridDim.x
+// FP32 partials gpart[q][E] (E = TP^2): warp w sums partials w, w + NW, ...
+// in FP64, then warp 0 adds the NW warp sums in warp order.  Partials are
+// read through L2 (written by other CTAs of this launch).
+template <int TP>
+__device__ void gram_slice_reduce(const float* gpart, double* G) {
+  constexpr int E = TP * TP, NW = kFGThreads / 32, U = 8;
+  __shared__ double s[NW][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nparts = gridDim.x;
+  const int e0 = (int)((long long)blockIdx.x * E / nparts), e1 = (int)((long long)(blockIdx.x + 1) * E / nparts);
+  for (int eb = e0; eb < e1; eb += 32) {
+    const int e = eb + lane;
+    double v = 0.0;
+    if (e < e1) {
+      for (int qb = warp; qb < nparts; qb += U * NW) {
+        float x[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int q = qb + u * NW;
+          x[u] = q < nparts ? __ldcg(gpart + (size_t)q * E + e) : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+          if (qb + u * NW < nparts) v += (double)x[u];
+      }
+    }
+    s[warp][lane] = v;
+    __syncthreads();
+    if (warp == 0 && e < e1) {
+      double t = 0.0;
+      for (int w = 0; w < NW; ++w) t += s[w][lane];
+      G[e] = t;
+    }
+    __syncthreads();
+  }
+}
+
+// The grid barrier alone (for the diagnostic entry point).
+__global__ void __launch_bounds__(32) grid_barrier_probe_kernel(unsigned* bar, int* err) { grid_barrier(bar, err); }
+
+// n consecutive floats of a 16-byte aligned shared-memory row into v.
+template <int n>
+__device__ __forceinline__ void lds_row(const float* p, float (&v)[n]) {
+  if constexpr (n % 4 == 0) {
+#pragma unroll
+    for (int k = 0; k < n / 4; ++k) {
+      const float4 t = reinterpret_cast<const float4*>(p)[k];
+      v[4 * k] = t.x;
+      v[4 * k + 1] = t.y;
+      v[4 * k + 2] = t.z;
+      v[4 * k + 3] = t.w;
+    }
+  } else if constexpr (n == 2) {
+    const float2 t = *reinterpret_cast<const float2*>(p);
+    v[0] = t.x;
+    v[1] = t.y;
+  } else {
+#pragma unroll
+    for (int k = 0; k < n; ++k) v[k] = p[k];
+  }
+}
 
 template <int TP>
 __global__ void __launch_bounds__(kFGThreads, 1)
 rpca_post_pre_gram_kernel(const RpcaGeom g, const RpcaCoeffs c, const RpcaPlanes P, double* __restrict__ partials,
-                          int nrows, float* __restrict__ gpart) {
-  // Gram blocks of RB x CB entries on an (TP / RB) x (TP / CB) thread grid
-  constexpr int RB = TP >= 64 ? 2 : 1, CB = TP >= 32 ? 4 : 1;
-  constexpr int NCB = TP / CB;
+                          int nrows, float* __restrict__ gpart, double* __restrict__ G, unsigned* __restrict__ bar,
+                          int* __restrict__ err) {
+  // the Gram threads tile TP x TP as a 16 x 8 grid of RB x CB blocks
+  constexpr int CB = TP / 8, RB = TP / 16;
+  static_assert(16 * 8 == kFGGram && RB >= 1, "Gram thread grid");
   constexpr int LDS = TP + 4;       // padded row of the staged tile (16-byte aligned)
-  __shared__ __align__(16) float sLD[kGC][LDS];
+  __shared__ __align__(16) float sLD[2][kGC][LDS];
   float acc[kNumSums] = {};
-  float gacc[RB][CB];
-#pragma unroll
-  for (int r = 0; r < RB; ++r)
-#pragma unroll
-    for (int q = 0; q < CB; ++q) gacc[r][q] = 0.f;
-  const int tid = threadIdx.x, bi = tid / NCB, bj = tid % NCB;
-  const bool gown = bi < TP / RB;   // the whole grid for TP >= 32; half the threads for TP = 16
-  for (int e = tid; e < kGC * LDS; e += kFGThreads) (&sLD[0][0])[e] = 0.f;   // frames T..TP-1 stay zero
+  const int tid = threadIdx.x;
+  for (int e = tid; e < 2 * kGC * LDS; e += kFGThreads) (&sLD[0][0][0])[e] = 0.f;   // frames T..TP-1 stay zero
   __syncthreads();
-  const float rho = c.rho, inv1r = 1.f / (1.f + c.rho);
-  const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
   const long long nch = (g.plane + kGC - 1) / kGC;
-  const int items = g.T * (kGC / 4);
-  for (long long ch = blockIdx.x; ch < nch; ch += gridDim.x) {
-    const long long p0 = ch * kGC;
+  const int nk = blockIdx.x < nch ? (int)((nch - 1 - blockIdx.x) / gridDim.x + 1) : 0;   // chunks of this CTA
+  if (tid < kFGUpd) {
+    const float rho = c.rho, inv1r = 1.f / (1.f + c.rho);
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    const int items = g.T * (kGC / 4);
+    for (int k = 0; k < nk; ++k) {
+      const int b = k & 1;
+      if (k >= 2) named_sync(kBarEmpty + b, kFGThreads);
+      const long long p0 = (blockIdx.x + (long long)k * gridDim.x) * kGC;
 #pragma unroll 2
-    for (int it = tid; it < items; it += kFGThreads) {
-      const int t = it / (kGC / 4), j = it % (kGC / 4);
-      const long long op = p0 + 4 * j;            // offset inside the frame (plane is a multiple of 4)
-      if (op >= g.plane) {
+      for (int it = tid; it < items; it += kFGUpd) {
+        const int t = it / (kGC / 4), j = it % (kGC / 4);
+        const long long op = p0 + 4 * j;            // offset inside the frame (plane is a multiple of 4)
+        if (op >= g.plane) {
 #pragma unroll
-        for (int e = 0; e < 4; ++e) sLD[4 * j + e][t] = 0.f;
-        continue;
-      }
-      const long long o = (long long)t * g.plane + op;
-      const bool hz = t < g.T - 1, hw = t > 0;
-      const long long oz = (long long)t * g.plane + op;
-      const long long ow = (long long)(t - 1) * g.plane + op;
-      const PreConst k = pre_const(g, c, t);
-      const float4 x = ldg4(P.X + o), s = ldg4(P.S + o), l = ldg4(P.L + o), tn = ldg4(P.Tn + o), y = ldg4(P.Y + o);
-      float4 a = ldg4(P.A + o), d = ldg4(P.D + o);
-      const float4 z = hz ? ldg4(P.z + oz) : z4;
-      float4 b = hz ? ldg4(P.Bz + oz) : z4;
-      const float4 w = hw ? ldg4(P.w + ow) : z4;
-      float4 cc = hw ? ldg4(P.Cw + ow) : z4;
-      float4 s4, l4, x4, ld4, p04, p14;
+          for (int e = 0; e < 4; ++e) sLD[b][4 * j + e][t] = 0.f;
+          continue;
+        }
+        const long long o = (long long)t * g.plane + op;
+        const bool hz = t < g.T - 1, hw = t > 0;
+        const long long oz = (long long)t * g.plane + op;
+        const long long ow = (long long)(t - 1) * g.plane + op;
+        const PreConst kc = pre_const(g, c, t);
+        const float4 x = ldg4(P.X + o), s = ldg4(P.S + o), l = ldg4(P.L + o), tn = ldg4(P.Tn + o), y = ldg4(P.Y + o);
+        float4 a = ldg4(P.A + o), d = ldg4(P.D + o);
+        const float4 z = hz ? ldg4(P.z + oz) : z4;
+        float4 bz = hz ? ldg4(P.Bz + oz) : z4;
+        const float4 w = hw ? ldg4(P.w + ow) : z4;
+        float4 cc = hw ? ldg4(P.Cw + ow) : z4;
+        float4 s4, l4, x4, ld4, p04, p14;
 #pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        post_elem<false>(f4c(x, e), f4c(s, e), f4c(l, e), f4c(tn, e), 0.f, f4(a, e), f4(d, e), f4c(z, e), 0.f,
-                         f4(b, e), f4c(w, e), 0.f, f4(cc, e), hz, hw, acc);
-        const PreOut r = pre_elem(f4c(x, e), f4c(l, e), f4c(a, e), f4c(tn, e), f4c(d, e), f4c(y, e), f4c(z, e),
-                                  hz ? f4c(b, e) : 0.f, f4c(w, e), hw ? f4c(cc, e) : 0.f, k.inv_sg, k.thr, rho, inv1r);
-        acc[0] = fmaf(r.dx, r.dx, acc[0]);
-        f4(s4, e) = r.s;
-        f4(l4, e) = r.l;
-        f4(x4, e) = r.x;
-        f4(ld4, e) = r.ld;
-        f4(p04, e) = r.p0;
-        f4(p14, e) = r.p1;
-        sLD[4 * j + e][t] = r.ld;
+        for (int e = 0; e < 4; ++e) {
+          post_elem<false>(f4c(x, e), f4c(s, e), f4c(l, e), f4c(tn, e), 0.f, f4(a, e), f4(d, e), f4c(z, e), 0.f,
+                           f4(bz, e), f4c(w, e), 0.f, f4(cc, e), hz, hw, acc);
+          const PreOut r = pre_elem(f4c(x, e), f4c(l, e), f4c(a, e), f4c(tn, e), f4c(d, e), f4c(y, e), f4c(z, e),
+                                    hz ? f4c(bz, e) : 0.f, f4c(w, e), hw ? f4c(cc, e) : 0.f, kc.inv_sg, kc.thr, rho,
+                                    inv1r);
+          acc[0] = fmaf(r.dx, r.dx, acc[0]);
+          f4(s4, e) = r.s;
+          f4(l4, e) = r.l;
+          f4(x4, e) = r.x;
+          f4(ld4, e) = r.ld;
+          f4(p04, e) = r.p0;
+          f4(p14, e) = r.p1;
+          sLD[b][4 * j + e][t] = r.ld;
+        }
+        stg4v(P.A + o, a);
+        stg4v(P.D + o, d);
+        stg4v(P.S + o, s4);
+        stg4v(P.L + o, l4);
+        stg4v(P.X + o, x4);
+        stg4v(P.LD + o, ld4);
+        if (hz) {
+          stg4v(P.Bz + oz, bz);
+          stg4v(P.p0 + oz, p04);
+          stg4v(P.zprev + oz, z);
+        }
+        if (hw) {
+          stg4v(P.Cw + ow, cc);
+          stg4v(P.p1 + ow, p14);
+          stg4v(P.wprev + ow, w);
+        }
       }
-      stg4v(P.A + o, a);
-      stg4v(P.D + o, d);
-      stg4v(P.S + o, s4);
-      stg4v(P.L + o, l4);
-      stg4v(P.X + o, x4);
-      stg4v(P.LD + o, ld4);
-      if (hz) {
-        stg4v(P.Bz + oz, b);
-        stg4v(P.p0 + oz, p04);
-        stg4v(P.zprev + oz, z);
-      }
-      if (hw) {
-        stg4v(P.Cw + ow, cc);
-        stg4v(P.p1 + ow, p14);
-        stg4v(P.wprev + ow, w);
-      }
+      named_arrive(kBarFull + b, kFGThreads);
     }
-    __syncthreads();
+  } else {
+    const int gt = tid - kFGUpd, bi = gt / 8, bj = gt % 8;
+    float gacc[RB][CB];
+#pragma unroll
+    for (int r = 0; r < RB; ++r)
+#pragma unroll
+      for (int q = 0; q < CB; ++q) gacc[r][q] = 0.f;
+    for (int k = 0; k < nk; ++k) {
+      const int b = k & 1;
+      named_sync(kBarFull + b, kFGThreads);
 #pragma unroll 4
-    for (int p = 0; p < kGC; ++p) {
-      float av[RB], bv[CB];
+      for (int p = 0; p < kGC; ++p) {
+        float av[RB], bv[CB];
+        lds_row<RB>(&sLD[b][p][RB * bi], av);
+        lds_row<CB>(&sLD[b][p][CB * bj], bv);
 #pragma unroll
-      for (int r = 0; r < RB; ++r) av[r] = sLD[p][gown ? RB * bi + r : 0];
+        for (int r = 0; r < RB; ++r)
 #pragma unroll
-      for (int q = 0; q < CB; ++q) bv[q] = sLD[p][CB * bj + q];
-#pragma unroll
-      for (int r = 0; r < RB; ++r)
-#pragma unroll
-        for (int q = 0; q < CB; ++q) gacc[r][q] = fmaf(av[r], bv[q], gacc[r][q]);
+          for (int q = 0; q < CB; ++q) gacc[r][q] = fmaf(av[r], bv[q], gacc[r][q]);
+      }
+      if (k + 2 < nk) named_arrive(kBarEmpty + b, kFGThreads);
     }
-    __syncthreads();
-  }
-  float* out = gpart + (size_t)blockIdx.x * TP * TP;
-  if (gown) {
+    float* out = gpart + (size_t)blockIdx.x * TP * TP;
 #pragma unroll
     for (int r = 0; r < RB; ++r)
 #pragma unroll
@@ -348,6 +474,7 @@ rpca_post_pre_gram_kernel(const RpcaGeom g, const RpcaCoeffs c, const RpcaPlanes
   block_sums_to<kFGThreads>(acc, partials + (size_t)blockIdx.x * kNumSums);
   for (int row = blockIdx.x + gridDim.x; row < nrows; row += gridDim.x)
     if (tid < kNumSums) partials[(size_t)row * kNumSums + tid] = 0.0;
+  if (grid_barrier(bar, err)) gram_slice_reduce<TP>(gpart, G);
 }
 
 // ||Y||^2 (once per input) into partials[block][0].
@@ -388,24 +515,72 @@ cudaError_t rpca_launch_post_pre(const RpcaGeom& g, const RpcaCoeffs& c, const R
 
 // CTAs of the Gram-fused pass = its partial Grams: at most one per SM, one
 // per chunk, and no more than the residual rows it writes (rpca_num_blocks).
+static int device_sms() {
+  int dev = 0, n_sm = 152;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    n_sm = 152;
+  return n_sm;
+}
+
 int rpca_gram_parts(const RpcaGeom& g) {
   long long n = (g.plane + kGC - 1) / kGC;
-  if (n > 152) n = 152;
+  const int n_sm = device_sms();
+  if (n > n_sm) n = n_sm;
   const int nr = rpca_num_blocks(g);
   if (n > nr) n = nr;
   return (int)(n < 1 ? 1 : n);
 }
 
 cudaError_t rpca_launch_post_pre_gram(const RpcaGeom& g, const RpcaCoeffs& c, const RpcaPlanes& P, int TP,
-                                      double* partials, int nrows, float* gpart, cudaStream_t st) {
-  const int grid = rpca_gram_parts(g);
+                                      double* partials, int nrows, float* gpart, double* G, unsigned* bar, int* err,
+                                      cudaStream_t st) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(rpca_gram_parts(g));
+  cfg.blockDim = dim3(kFGThreads);
+  cfg.stream = st;
+  cudaLaunchAttribute coop[1];
+  coop[0].id = cudaLaunchAttributeCooperative;   // the CTAs meet at a grid barrier
+  coop[0].val.cooperative = 1;
+  cfg.attrs = coop;
+  cfg.numAttrs = 1;
   switch (TP) {
-    case 16: rpca_post_pre_gram_kernel<16><<<grid, kFGThreads, 0, st>>>(g, c, P, partials, nrows, gpart); break;
-    case 32: rpca_post_pre_gram_kernel<32><<<grid, kFGThreads, 0, st>>>(g, c, P, partials, nrows, gpart); break;
-    case 64: rpca_post_pre_gram_kernel<64><<<grid, kFGThreads, 0, st>>>(g, c, P, partials, nrows, gpart); break;
+    case 16: return cudaLaunchKernelEx(&cfg, rpca_post_pre_gram_kernel<16>, g, c, P, partials, nrows, gpart, G, bar, err);
+    case 32: return cudaLaunchKernelEx(&cfg, rpca_post_pre_gram_kernel<32>, g, c, P, partials, nrows, gpart, G, bar, err);
+    case 64: return cudaLaunchKernelEx(&cfg, rpca_post_pre_gram_kernel<64>, g, c, P, partials, nrows, gpart, G, bar, err);
     default: return cudaErrorInvalidValue;
   }
-  return cudaGetLastError();
+}
+
+cudaError_t grid_barrier_probe(int ctas, unsigned preset, int* err, unsigned* generation) {
+  if (ctas < 1 || ctas > device_sms()) return cudaErrorInvalidValue;
+  unsigned* bar = nullptr;   // bar[0] count, bar[1] generation, bar[2] error flag
+  cudaStream_t st = nullptr;
+  cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaMalloc(&bar, 4 * sizeof(unsigned));
+  const unsigned init[4] = {preset, 0u, 0u, 0u};
+  unsigned out[4] = {};
+  if (e == cudaSuccess) e = cudaMemcpyAsync(bar, init, sizeof init, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(ctas);
+    cfg.blockDim = dim3(32);
+    cfg.stream = st;
+    cudaLaunchAttribute coop[1];
+    coop[0].id = cudaLaunchAttributeCooperative;
+    coop[0].val.cooperative = 1;
+    cfg.attrs = coop;
+    cfg.numAttrs = 1;
+    e = cudaLaunchKernelEx(&cfg, grid_barrier_probe_kernel, bar, reinterpret_cast<int*>(bar + 2));
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(out, bar, sizeof out, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e == cudaSuccess) {
+    *err = (int)out[2];
+    *generation = out[1];
+  }
+  if (bar) cudaFree(bar);
+  if (st) cudaStreamDestroy(st);
+  return e;
 }
 
 cudaError_t rpca_launch_sumsq(const RpcaGeom& g, const float* Y, double* partials, cudaStream_t st) {

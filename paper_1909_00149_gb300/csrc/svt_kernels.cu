@@ -931,13 +931,6 @@ cudaError_t svt_launch_gram(const float* X, long long ld, long long N, int T, do
   return cudaGetLastError();
 }
 
-cudaError_t svt_launch_gram_reduce(const float* partials, int nparts, int T, double* G, cudaStream_t st) {
-  const int TP = svt_padded_T(T);
-  const int n = TP * TP;
-  gram_reduce_kernel<float><<<(n + 31) / 32, 32 * kRedWarps, 0, st>>>(partials, nparts, n, G);
-  return cudaGetLastError();
-}
-
 cudaError_t svt_launch_eig(const double* G, int T, int warm, float theta, int max_sweeps, float tol, float* V_io,
                            float* Wm, float* sig, int* sweeps, cudaStream_t st) {
   const int TP = svt_padded_T(T);
