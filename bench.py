@@ -50,18 +50,18 @@ PROX_KW = dict(mu=3.0, rho=0.01, kernel="tma", use_graph=True, check_every=PROX_
 OUTER_PER_STEP = 10          # Algorithm 3 outer iterations per step (one residual read-back)
 RPCA_KW = dict(lam=0.02, kappa=0.005, mu=3.0, rho=1.0, check_every=OUTER_PER_STEP)
 PHASES = ["rpca_pre_kernel (Alg. 3 lines 4-9)", "gram_partial/reduce (SVT Gram)", "jacobi_svt_kernel (T x T eig)",
-          "svt_apply_kernel (SVT apply)", "prox_tma_kernel (Alg. 1 iterations)", "rpca_post_kernel (Alg. 3 lines 12-15)",
-          "rpca_post_pre_gram_kernel (lines 12-15 fused with the next lines 4-9 and its Gram, partials reduced "
-          "in the same cooperative launch)",
+          "apply_tc_kernel (SVT apply of the last outer iteration)", "prox_tma_kernel (Alg. 1 iterations)", "rpca_post_kernel (Alg. 3 lines 12-15)",
+          "rpca_apply_post_pre_gram_kernel (SVT apply, lines 12-15, the next lines 4-9 and the next Gram, "
+          "partials reduced in the same cooperative launch)",
           "(no launch: the Gram after the fused pass comes out of it)"]
 # launches of each phase in one step (a check interval): the first lines 4-9,
 # its Gram and the last lines 12-15 run alone, the others fused
-PHASE_COUNT = [1, 1, OUTER_PER_STEP, OUTER_PER_STEP, OUTER_PER_STEP, 1, OUTER_PER_STEP - 1, 0]
+PHASE_COUNT = [1, 1, OUTER_PER_STEP, 1, OUTER_PER_STEP, 1, OUTER_PER_STEP - 1, 0]
 PROFILE_FILES = {  # kernel -> (ncu summary holding its DRAM traffic per launch, its source file)
     "prox_tma_kernel": ("prox_tma_63x256x256.md", "prox_tma.cu"),
     "rpca_pre_kernel": ("rpca_step_64x256x256.md", "rpca_kernels.cu"),
     "rpca_post_kernel": ("rpca_step_64x256x256.md", "rpca_kernels.cu"),
-    "rpca_post_pre_gram_kernel": ("rpca_step_64x256x256.md", "rpca_kernels.cu"),
+    "rpca_apply_post_pre_gram_kernel": ("rpca_step_64x256x256.md", "rpca_kernels.cu"),
 }
 
 
@@ -205,7 +205,8 @@ def rpca_phase_bytes(T: int, N: int, n_inner: int) -> list:
             4.0 * N * 2 * T,                  # apply: reads L+D, writes the new Tm
             56.0 * N * P * n_inner,           # Algorithm 1: 56 B per pixel-iteration
             4.0 * N * (9 * T + 8 * P),        # post: reads X S L Tm Tm_old A D z z' b w w' c, writes A D b c
-            4.0 * N * (13 * T + 10 * P) + 2 * gparts + 8.0 * TP * TP,   # post + pre + the Gram
+            4.0 * N * (13 * T + 10 * P) + 2 * gparts + 8.0 * TP * TP,   # apply + post + pre + the Gram
+                                                                      # (reads LD instead of the SVT output)
             0.0]                              # no separate Gram reduction
 
 
@@ -309,12 +310,12 @@ def run_ours_rpca(args, rank, world, local_rank):
                            "svt_rank": res["svt_rank"]},
         "e2e": {"value": units / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": T * H * W * 4,
                 "d2h_bytes_per_step": 8 * 8 + 4 + 4 * 64 + 4},
-        # per step: lines 4-9 and their Gram (2 kernels) once; per outer
-        # iteration the eigensolver, apply and n_inner prox; between outer
-        # iterations the fused pass (which also yields the next Gram); the
-        # first Gram's reduction, the last lines 12-15 and the residual
-        # finalisation once
-        "gpu_launches": (OUTER_PER_STEP + 4 + (2 + args.n_inner) * OUTER_PER_STEP) * args.steps,
+        # per step: lines 4-9 and their Gram (tensor-core partials and their
+        # reduction) once; per outer iteration the eigensolver and n_inner
+        # prox; between outer iterations the fused pass (the SVT apply, lines
+        # 12-15, the next lines 4-9 and the next Gram); the last iteration's
+        # apply and lines 12-15 and the residual finalisation once
+        "gpu_launches": (OUTER_PER_STEP + 5 + (1 + args.n_inner) * OUTER_PER_STEP) * args.steps,
         "clocks": clocks,
     }
     if not args.no_cpu_baseline:

@@ -277,12 +277,14 @@ int ot_rpca_solve(ot_rpca_t h, ot_rpca_result* res);
 /* Two outer iterations (as ot_rpca_step(h, 2)) with CUDA events recorded on
  * the handle's stream between their phases, the eigensolver serialised with
  * the prox; phase_ms[0..7] receives the device time of: 0 lines 4-9 of the
- * first, 1 its Gram matrix, 2 its T x T eigensolver, 3 its SVT apply, 4 its
- * n_inner Algorithm 1 iterations, 5 lines 12-15 of the second (alone),
- * 6 lines 12-15 of the first fused with lines 4-9 of the second (and, for
- * T <= 64, the second's Gram matrix, its partials reduced in the same
- * launch), 7 the second's Gram where the fused pass does not produce it
- * (T > 64; about 0 otherwise).  Sync. */
+ * first, 1 its Gram matrix, 2 its T x T eigensolver, 3 the second's SVT
+ * apply (alone, as for the last outer iteration of every call), 4 the
+ * first's n_inner Algorithm 1 iterations, 5 lines 12-15 of the second
+ * (alone), 6 the pass between them: lines 12-15 of the first fused with
+ * lines 4-9 of the second (for T <= 64 also the first's SVT apply and the
+ * second's Gram matrix, its partials reduced in the same launch), 7 the
+ * second's Gram where that pass does not produce it (T > 64; about 0
+ * otherwise).  Sync. */
 int ot_rpca_step_profiled(ot_rpca_t h, double* phase_ms);
 
 /* Copy one variable (OT_RPCA_*) out, dense.  Sync. */

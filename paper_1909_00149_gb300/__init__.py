@@ -252,8 +252,9 @@ class Rpca:
 
     def step_profiled(self) -> list:
         """Two outer iterations; device ms of their eight phases (see the C
-        header: pre, Gram, eigensolver, apply, prox, post, fused post + pre
-        (with the second Gram for T <= 64), the second Gram otherwise)."""
+        header: pre, Gram, eigensolver, the second apply, prox, post, the
+        fused pass between them (with the first apply and the second Gram for
+        T <= 64), the second Gram otherwise)."""
         ms = (ctypes.c_double * 8)()
         check(_lib.ot_rpca_step_profiled(self.h, ms), "ot_rpca_step_profiled")
         return list(ms)

@@ -196,15 +196,17 @@ cudaError_t rpca_launch_post(const RpcaGeom& g, const RpcaPlanes& P, double* par
 // post of outer iteration k and pre of k + 1 in one pass (slot 0 sums only)
 cudaError_t rpca_launch_post_pre(const RpcaGeom& g, const RpcaCoeffs& c, const RpcaPlanes& P, double* partials,
                                  cudaStream_t st);
-// the same pass accumulating iteration k + 1's Gram matrix (T padded to TP
-// in {16, 32, 64}): FP32 partials gpart[rpca_gram_parts(g)][TP][TP], reduced
-// in the same cooperative launch into G (TP x TP doubles); bar: two
+// for T padded to TP in {16, 32, 64}: the same pass preceded by the SVT
+// apply of iteration k (T^k = LD^k Wm, Wm TP x TP row-major, computed per
+// chunk in shared memory; P.Tn written only when store_tn) and followed by
+// iteration k + 1's Gram matrix: FP32 partials gpart[rpca_gram_parts(g)][TP][TP],
+// reduced in the same cooperative launch into G (TP x TP doubles); bar: two
 // zero-initialised unsigned ints owned by the caller (its grid barrier);
 // err is set if the barrier wait expires; writes nrows slot-0 rows of partials
 int rpca_gram_parts(const RpcaGeom& g);
-cudaError_t rpca_launch_post_pre_gram(const RpcaGeom& g, const RpcaCoeffs& c, const RpcaPlanes& P, int TP,
-                                      double* partials, int nrows, float* gpart, double* G, unsigned* bar, int* err,
-                                      cudaStream_t st);
+cudaError_t rpca_launch_apply_post_pre_gram(const RpcaGeom& g, const RpcaCoeffs& c, const RpcaPlanes& P, int TP,
+                                            const float* Wm, int store_tn, double* partials, int nrows, float* gpart,
+                                            double* G, unsigned* bar, int* err, cudaStream_t st);
 // the fused pass's grid barrier alone on `ctas` cooperative CTAs, its count
 // preset (diagnostic: ot_debug_grid_barrier)
 cudaError_t grid_barrier_probe(int ctas, unsigned preset, int* err, unsigned* generation);

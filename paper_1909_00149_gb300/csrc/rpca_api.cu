@@ -278,19 +278,24 @@ static void swap_svt_planes(ot_rpca* h) {
   h->tpar ^= 1;
 }
 
-// Lines 12-15 of this outer iteration and lines 4-9 of the next in one pass
-// (with the next iteration's Gram partials when T_pad <= 64).
-static cudaError_t launch_between(ot_rpca* h) {
+// Lines 12-15 of this outer iteration and lines 4-9 of the next in one pass;
+// for T_pad <= 64 the pass also forms this iteration's SVT output (storing it
+// only with store_tn) and the next iteration's Gram matrix.
+static cudaError_t launch_between(ot_rpca* h, bool store_tn) {
   if (h->fgram)
-    return rpca_launch_post_pre_gram(h->G, h->C, h->P, h->TP, pre_rows(h, h->tpar ^ 1), h->nb_rpca, h->fgram,
-                                     h->Gm, h->fbar, h->prox->derr, h->stream);
+    return rpca_launch_apply_post_pre_gram(h->G, h->C, h->P, h->TP, h->Wm, store_tn ? 1 : 0,
+                                           pre_rows(h, h->tpar ^ 1), h->nb_rpca, h->fgram, h->Gm, h->fbar,
+                                           h->prox->derr, h->stream);
   return rpca_launch_post_pre(h->G, h->C, h->P, pre_rows(h, h->tpar ^ 1), h->stream);
 }
 
 // Enqueue n >= 1 outer iterations: lines 4-9 of the first, then per
 // iteration the SVT (line 10) beside the prox (line 11), and lines 12-15
 // fused with the next iteration's lines 4-9, except after the last, whose
-// lines 12-15 run alone so the state between calls is Algorithm 3's.
+// SVT apply and lines 12-15 run alone so the state between calls is
+// Algorithm 3's.  For T_pad <= 64 the fused pass also does the SVT apply of
+// its iteration (storing the output only before the last iteration, whose
+// lines 12-15 compare with it) and the next iteration's Gram matrix.
 // `sums` finalises the last iteration's residual sums and copies them (with
 // the SVT diagnostics) to the pinned host buffer.
 static int enqueue_interval(ot_rpca* h, int n, bool sums) {
@@ -318,14 +323,15 @@ static int enqueue_interval(ot_rpca* h, int n, bool sums) {
     if (rc != OT_OK) return rc;
     // join, then the rest of line 10 and lines 12-15
     OT_CUDA(cudaStreamWaitEvent(h->stream, h->ev_join, 0), "join wait");
-    OT_CUDA(svt_launch_apply(h->P.LD, plane, N, h->prm.T, h->Wm, h->P.Tn, plane, false, nullptr, h->prox->derr,
-                             h->stream),
-            "svt apply");
+    if (k == n - 1 || !h->fgram)
+      OT_CUDA(svt_launch_apply(h->P.LD, plane, N, h->prm.T, h->Wm, h->P.Tn, plane, false, nullptr, h->prox->derr,
+                               h->stream),
+              "svt apply");
     last_par = h->tpar;
     if (k == n - 1)
       OT_CUDA(rpca_launch_post(h->G, h->P, post_rows(h), h->stream), "rpca post");
     else
-      OT_CUDA(launch_between(h), "rpca post + pre");
+      OT_CUDA(launch_between(h, k == n - 2), "rpca post + pre");
     swap_svt_planes(h);
   }
   if (sums) {
@@ -476,51 +482,69 @@ int ot_debug_grid_barrier(int32_t ctas, uint32_t preset_count, int32_t* err, uin
 int ot_rpca_step_profiled(ot_rpca_t h, double* phase_ms) {
   if (!h || !phase_ms) return fail(OT_EINVAL, "ot_rpca_step_profiled: NULL argument");
   if (!h->have_input) return fail(OT_EINVAL, "ot_rpca_step_profiled: no input (call ot_rpca_set_input)");
-  constexpr int kEv = 10;
+  // the kernels of ot_rpca_step(h, 2), serialised on the handle's stream:
+  //   ev0 pre ev1 Gram ev2 eig ev3 [apply, T_pad > 64] ev4 prox ev5 fused pass ev6
+  //   [Gram, T_pad > 64] ev7 eig ev8 apply ev9 prox ev10 post ev11
+  constexpr int kEv = 12;
   cudaEvent_t ev[kEv] = {};
   cudaError_t e = cudaSuccess;
   for (int k = 0; k < kEv && e == cudaSuccess; ++k) e = cudaEventCreate(&ev[k]);
   const long long plane = h->G.plane;
   int rc = OT_OK;
-  // lines 10-11 of one outer iteration, every phase on the handle's stream
-  auto middle = [&](bool after_fused, cudaEvent_t e1, cudaEvent_t e2, cudaEvent_t e3, cudaEvent_t e4) {
-    if (e == cudaSuccess && !(after_fused && h->fgram))   // else the fused pass left G in Gm
+  auto rec = [&](int k) {
+    if (e == cudaSuccess && rc == OT_OK) e = cudaEventRecord(ev[k], h->stream);
+  };
+  auto gram = [&]() {
+    if (e == cudaSuccess && rc == OT_OK)
       e = svt_launch_gram(h->P.LD, plane, plane, h->prm.T, h->gram_partials, h->Gm, h->prox->derr, h->stream);
-    if (e == cudaSuccess && e1) e = cudaEventRecord(e1, h->stream);
-    if (e == cudaSuccess)
+  };
+  auto eig = [&]() {
+    if (e == cudaSuccess && rc == OT_OK) {
       e = svt_launch_eig(h->Gm, h->prm.T, h->warm, (float)(h->prm.gamma / h->prm.rho), h->prm.svt_max_sweeps,
                          svt_tolerance(h->prm.T), h->V, h->Wm, h->sig, h->sweeps, h->stream);
-    if (e == cudaSuccess) {
       h->warm = 1;
-      if (e2) e = cudaEventRecord(e2, h->stream);
-    }
-    if (e == cudaSuccess)
-      e = svt_launch_apply(h->P.LD, plane, plane, h->prm.T, h->Wm, h->P.Tn, plane, false, nullptr, h->prox->derr,
-                           h->stream);
-    if (e == cudaSuccess && e3) e = cudaEventRecord(e3, h->stream);
-    if (e == cudaSuccess) {
-      rc = ot_prox_step(h->prox, h->prm.n_inner);
-      if (rc == OT_OK && e4) e = cudaEventRecord(e4, h->stream);
     }
   };
-  if (e == cudaSuccess) e = cudaEventRecord(ev[0], h->stream);
+  auto apply = [&]() {
+    if (e == cudaSuccess && rc == OT_OK)
+      e = svt_launch_apply(h->P.LD, plane, plane, h->prm.T, h->Wm, h->P.Tn, plane, false, nullptr, h->prox->derr,
+                           h->stream);
+  };
+  auto prox = [&]() {
+    if (e == cudaSuccess && rc == OT_OK) rc = ot_prox_step(h->prox, h->prm.n_inner);
+  };
+  rec(0);
   if (e == cudaSuccess) e = rpca_launch_pre(h->G, h->C, h->P, pre_rows(h, h->tpar), h->stream);
-  if (e == cudaSuccess) e = cudaEventRecord(ev[1], h->stream);
-  middle(false, ev[2], ev[3], ev[4], ev[5]);
-  if (e == cudaSuccess && rc == OT_OK) e = launch_between(h);
+  rec(1);
+  gram();
+  rec(2);
+  eig();
+  rec(3);
+  if (!h->fgram) apply();
+  rec(4);
+  prox();
+  rec(5);
   if (e == cudaSuccess && rc == OT_OK) {
+    e = launch_between(h, true);
     swap_svt_planes(h);
-    e = cudaEventRecord(ev[6], h->stream);
   }
-  if (rc == OT_OK) middle(true, ev[9], nullptr, nullptr, nullptr);
-  if (e == cudaSuccess && rc == OT_OK) e = cudaEventRecord(ev[7], h->stream);
-  if (e == cudaSuccess && rc == OT_OK) e = rpca_launch_post(h->G, h->P, post_rows(h), h->stream);
+  rec(6);
+  if (!h->fgram) gram();
+  rec(7);
+  eig();
+  rec(8);
+  apply();
+  rec(9);
+  prox();
+  rec(10);
   if (e == cudaSuccess && rc == OT_OK) {
+    e = rpca_launch_post(h->G, h->P, post_rows(h), h->stream);
     swap_svt_planes(h);
-    e = cudaEventRecord(ev[8], h->stream);
   }
-  if (e == cudaSuccess && rc == OT_OK) e = cudaEventSynchronize(ev[8]);
-  const int from[8] = {0, 1, 2, 3, 4, 7, 5, 6}, to[8] = {1, 2, 3, 4, 5, 8, 6, 9};
+  rec(11);
+  if (e == cudaSuccess && rc == OT_OK) e = cudaEventSynchronize(ev[11]);
+  // phases: pre, Gram, eig, apply (the second iteration's), prox, post, fused pass, second Gram
+  const int from[8] = {0, 1, 2, 8, 4, 10, 5, 6}, to[8] = {1, 2, 3, 9, 5, 11, 6, 7};
   for (int k = 0; k < 8 && e == cudaSuccess && rc == OT_OK; ++k) {
     float ms = 0.f;
     e = cudaEventElapsedTime(&ms, ev[from[k]], ev[to[k]]);

@@ -232,32 +232,45 @@ rpca_post_pre_kernel(const RpcaGeom g, const RpcaCoeffs c, const RpcaPlanes P, d
   block_sums_to<kRpcaThreads>(acc, partials + (size_t)blockIdx.x * kNumSums);
 }
 
-// The fused pass of rpca_post_pre_kernel that also accumulates the SVT Gram
-// matrix of the LD = L + D it writes (Alg. 3 line 10 of iteration k + 1).
-// A CTA owns chunks of kGC consecutive pixels of a frame plane across all T
-// frames, taken in the order blockIdx.x, blockIdx.x + gridDim.x, ...  Its
-// warps are split by role so that the Gram arithmetic overlaps the memory
-// traffic instead of alternating with it:
+// The pass between outer iterations k and k + 1 for T_pad <= 64: the SVT
+// apply of iteration k (Alg. 3 line 10, T^k = LD^k Wm), its lines 12-15,
+// lines 4-9 of iteration k + 1 and the Gram matrix of the LD^{k+1} they
+// write (line 10 of k + 1), in one cooperative launch.  A CTA owns chunks of
+// kGC consecutive pixels of a frame plane across all T frames, taken in the
+// order blockIdx.x, blockIdx.x + gridDim.x, ...  Its warps are split by role
+// so that the contractions overlap the memory traffic:
+//   * kFGGram warps (the contraction warps) copy chunk j + 2 of LD^k into
+//     shared memory (cp.async) while they form T^k of chunk j = Wm applied
+//     to its LD^k columns (FP32 FMAs, s in order) into a shared tile, then
+//     add LD^{k+1}_chunk^T LD^{k+1}_chunk of chunk j - 1 to a TP x TP FP32
+//     accumulator held in registers (RB x CB entries a thread), pixel by
+//     pixel in chunk order;
 //   * kFGUpd updating warps run the per-(frame, pixel) arithmetic of
-//     rpca_post_pre_kernel on a chunk and leave its LD values in one of two
-//     shared-memory tiles;
-//   * kFGGram Gram warps add LD_chunk^T LD_chunk of the other tile to a
-//     TP x TP FP32 accumulator held in registers (RB x CB entries a thread),
-//     pixel by pixel in chunk order.
-// Hand-off through named barriers (hardware barriers; every warp of the CTA
-// runs the same number of chunks): kBarFull + b says tile b holds a chunk,
-// kBarEmpty + b that the Gram warps are done with it.  Every CTA writes its
-// partial Gram to gpart[blockIdx.x].  Then the CTAs meet at a grid barrier
-// (the launch is cooperative, so all of them are resident) and each sums
+//     rpca_post_pre_kernel on chunk j with T^k from the shared tile and
+//     leave its LD^{k+1} values in another shared tile (LD is updated in
+//     place: a chunk's LD^k is copied before its LD^{k+1} is stored).
+// Double-buffered tiles, handed over through named barriers (hardware
+// barriers; every warp of the CTA runs the same number of chunks).  With
+// store_tn the updating warps also store T^k (needed only before the last
+// outer iteration of a call, whose lines 12-15 form ||T^{k+1} - T^k||).
+// Every CTA writes its partial Gram to gpart[blockIdx.x]; the CTAs then meet
+// at a grid barrier (all resident: the launch is cooperative) and each sums
 // its slice of the TP x TP entries over the partials, in partial order and
-// FP64, into G.  The slot-0 rows blockIdx.x + k gridDim.x < nrows of partials
-// are written (zero beyond the CTA's own), so the residual finalisation sees
-// nrows rows as before.
-constexpr int kGC = 64;                          // pixels per Gram chunk
+// FP64, into G.  The slot-0 rows blockIdx.x + k gridDim.x < nrows of
+// partials are written (zero beyond the CTA's own), so the residual
+// finalisation sees nrows rows as before.
+constexpr int kGC = 64;                          // pixels per chunk
 constexpr int kFGUpd = 512;                      // updating threads (16 warps)
-constexpr int kFGGram = 128;                     // Gram threads (4 warps)
+constexpr int kFGGram = 128;                     // contraction threads (4 warps)
 constexpr int kFGThreads = kFGUpd + kFGGram;     // one CTA per SM: 152 partial Grams
-constexpr int kBarFull = 1, kBarEmpty = 3;       // named barriers 1-2 and 3-4 (0 is __syncthreads)
+// named barriers (0 is __syncthreads): tile b of T^k full / free, tile b of
+// LD^{k+1} full / free, and one among the contraction warps alone
+constexpr int kBarTnFull = 1, kBarTnFree = 3, kBarLdFull = 5, kBarLdFree = 7, kBarMma = 9;
+
+template <int TP>
+constexpr size_t between_smem() {   // Wm^T, 2 x LD^k chunk, 2 x T^k chunk, 2 x LD^{k+1} chunk
+  return sizeof(float) * ((size_t)TP * (TP + 4) + 4 * (size_t)TP * (kGC + 4) + 2 * (size_t)kGC * (TP + 4));
+}
 
 __device__ __forceinline__ void named_sync(int id, int n) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
@@ -363,37 +376,59 @@ __device__ __forceinline__ void lds_row(const float* p, float (&v)[n]) {
   }
 }
 
+// 16-byte asynchronous copy global -> shared; src_bytes = 0 fills zeros
+// (the source address must still be valid).
+__device__ __forceinline__ void cp_async16(float* dst, const float* src, int src_bytes) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
 template <int TP>
 __global__ void __launch_bounds__(kFGThreads, 1)
-rpca_post_pre_gram_kernel(const RpcaGeom g, const RpcaCoeffs c, const RpcaPlanes P, double* __restrict__ partials,
-                          int nrows, float* __restrict__ gpart, double* __restrict__ G, unsigned* __restrict__ bar,
-                          int* __restrict__ err) {
-  // the Gram threads tile TP x TP as a 16 x 8 grid of RB x CB blocks
-  constexpr int CB = TP / 8, RB = TP / 16;
-  static_assert(16 * 8 == kFGGram && RB >= 1, "Gram thread grid");
-  constexpr int LDS = TP + 4;       // padded row of the staged tile (16-byte aligned)
-  __shared__ __align__(16) float sLD[2][kGC][LDS];
+rpca_apply_post_pre_gram_kernel(const RpcaGeom g, const RpcaCoeffs c, const RpcaPlanes P,
+                                const float* __restrict__ Wm, int store_tn, double* __restrict__ partials, int nrows,
+                                float* __restrict__ gpart, double* __restrict__ G, unsigned* __restrict__ bar,
+                                int* __restrict__ err) {
+  constexpr int CB = TP / 8, RB = TP / 16;   // Gram block of a contraction thread (16 x 8 grid)
+  constexpr int AT = TP / 8;                 // apply block: 4 pixels x AT frames (16 x 8 grid)
+  constexpr int AH = AT < 4 ? AT : 4;
+  static_assert(16 * 8 == kFGGram && RB >= 1 && 16 * 4 == kGC, "contraction thread grid");
+  constexpr int LDS = TP + 4, LDP = kGC + 4;   // padded rows (16-byte aligned)
+  extern __shared__ __align__(16) float smf[];
+  float* sW = smf;                       // [TP][LDS]: sW[s][t] = Wm[t][s]
+  float* sIn = sW + TP * LDS;            // [2][TP][LDP]: LD^k of a chunk, frame rows
+  float* sTn = sIn + 2 * TP * LDP;       // [2][TP][LDP]: T^k of a chunk, frame rows
+  float* sLD = sTn + 2 * TP * LDP;       // [2][kGC][LDS]: LD^{k+1} of a chunk, pixel rows
   float acc[kNumSums] = {};
   const int tid = threadIdx.x;
-  for (int e = tid; e < 2 * kGC * LDS; e += kFGThreads) (&sLD[0][0][0])[e] = 0.f;   // frames T..TP-1 stay zero
+  const int nsm = (int)(between_smem<TP>() / sizeof(float));
+  for (int e = tid; e < nsm; e += kFGThreads) smf[e] = 0.f;   // frames T..TP-1 stay zero
   __syncthreads();
   const long long nch = (g.plane + kGC - 1) / kGC;
   const int nk = blockIdx.x < nch ? (int)((nch - 1 - blockIdx.x) / gridDim.x + 1) : 0;   // chunks of this CTA
+  for (int e = tid; e < g.T * g.T; e += kFGThreads) sW[(e % g.T) * LDS + e / g.T] = Wm[(e / g.T) * TP + e % g.T];
+  __syncthreads();
   if (tid < kFGUpd) {
     const float rho = c.rho, inv1r = 1.f / (1.f + c.rho);
     const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
     const int items = g.T * (kGC / 4);
     for (int k = 0; k < nk; ++k) {
       const int b = k & 1;
-      if (k >= 2) named_sync(kBarEmpty + b, kFGThreads);
+      named_sync(kBarTnFull + b, kFGThreads);
+      if (k >= 2) named_sync(kBarLdFree + b, kFGThreads);
       const long long p0 = (blockIdx.x + (long long)k * gridDim.x) * kGC;
+      const float* tnb = sTn + b * TP * LDP;
+      float* ldb = sLD + b * kGC * LDS;
 #pragma unroll 2
       for (int it = tid; it < items; it += kFGUpd) {
         const int t = it / (kGC / 4), j = it % (kGC / 4);
         const long long op = p0 + 4 * j;            // offset inside the frame (plane is a multiple of 4)
         if (op >= g.plane) {
 #pragma unroll
-          for (int e = 0; e < 4; ++e) sLD[b][4 * j + e][t] = 0.f;
+          for (int e = 0; e < 4; ++e) ldb[(4 * j + e) * LDS + t] = 0.f;
           continue;
         }
         const long long o = (long long)t * g.plane + op;
@@ -401,7 +436,8 @@ rpca_post_pre_gram_kernel(const RpcaGeom g, const RpcaCoeffs c, const RpcaPlanes
         const long long oz = (long long)t * g.plane + op;
         const long long ow = (long long)(t - 1) * g.plane + op;
         const PreConst kc = pre_const(g, c, t);
-        const float4 x = ldg4(P.X + o), s = ldg4(P.S + o), l = ldg4(P.L + o), tn = ldg4(P.Tn + o), y = ldg4(P.Y + o);
+        const float4 tn = *reinterpret_cast<const float4*>(tnb + t * LDP + 4 * j);
+        const float4 x = ldg4(P.X + o), s = ldg4(P.S + o), l = ldg4(P.L + o), y = ldg4(P.Y + o);
         float4 a = ldg4(P.A + o), d = ldg4(P.D + o);
         const float4 z = hz ? ldg4(P.z + oz) : z4;
         float4 bz = hz ? ldg4(P.Bz + oz) : z4;
@@ -422,8 +458,9 @@ rpca_post_pre_gram_kernel(const RpcaGeom g, const RpcaCoeffs c, const RpcaPlanes
           f4(ld4, e) = r.ld;
           f4(p04, e) = r.p0;
           f4(p14, e) = r.p1;
-          sLD[b][4 * j + e][t] = r.ld;
+          ldb[(4 * j + e) * LDS + t] = r.ld;
         }
+        if (store_tn) stg4v(P.Tn + o, tn);
         stg4v(P.A + o, a);
         stg4v(P.D + o, d);
         stg4v(P.S + o, s4);
@@ -441,30 +478,89 @@ rpca_post_pre_gram_kernel(const RpcaGeom g, const RpcaCoeffs c, const RpcaPlanes
           stg4v(P.wprev + ow, w);
         }
       }
-      named_arrive(kBarFull + b, kFGThreads);
+      if (k + 2 < nk) named_arrive(kBarTnFree + b, kFGThreads);
+      named_arrive(kBarLdFull + b, kFGThreads);
     }
   } else {
     const int gt = tid - kFGUpd, bi = gt / 8, bj = gt % 8;
+    // LD^k of chunk k into tile k & 1 (one commit group per chunk, empty
+    // beyond the last, so that wait_group 1 always means "chunk k is in")
+    auto prefetch = [&](int k) {
+      if (k < nk) {
+        const long long p0 = (blockIdx.x + (long long)k * gridDim.x) * kGC;
+        float* dst = sIn + (k & 1) * TP * LDP;
+        for (int e = gt; e < g.T * (kGC / 4); e += kFGGram) {
+          const int s = e / (kGC / 4), q = e % (kGC / 4);
+          const long long op = p0 + 4 * q;
+          const bool in = op < g.plane;
+          cp_async16(dst + s * LDP + 4 * q, in ? P.LD + (long long)s * g.plane + op : P.LD, in ? 16 : 0);
+        }
+      }
+      cp_async_commit();
+    };
     float gacc[RB][CB];
 #pragma unroll
     for (int r = 0; r < RB; ++r)
 #pragma unroll
       for (int q = 0; q < CB; ++q) gacc[r][q] = 0.f;
-    for (int k = 0; k < nk; ++k) {
-      const int b = k & 1;
-      named_sync(kBarFull + b, kFGThreads);
+    // Gram of chunk j from LD^{k+1} tile j & 1
+    auto gram_chunk = [&](int j) {
+      const int b = j & 1;
+      named_sync(kBarLdFull + b, kFGThreads);
+      const float* ldb = sLD + b * kGC * LDS;
 #pragma unroll 4
       for (int p = 0; p < kGC; ++p) {
         float av[RB], bv[CB];
-        lds_row<RB>(&sLD[b][p][RB * bi], av);
-        lds_row<CB>(&sLD[b][p][CB * bj], bv);
+        lds_row<RB>(ldb + p * LDS + RB * bi, av);
+        lds_row<CB>(ldb + p * LDS + CB * bj, bv);
 #pragma unroll
         for (int r = 0; r < RB; ++r)
 #pragma unroll
           for (int q = 0; q < CB; ++q) gacc[r][q] = fmaf(av[r], bv[q], gacc[r][q]);
       }
-      if (k + 2 < nk) named_arrive(kBarEmpty + b, kFGThreads);
+      if (j + 2 < nk) named_arrive(kBarLdFree + b, kFGThreads);
+    };
+    prefetch(0);
+    prefetch(1);
+    for (int k = 0; k < nk; ++k) {
+      const int b = k & 1;
+      cp_async_wait<1>();                      // this thread's copies of chunk k are in
+      named_sync(kBarMma, kFGGram);            // ... and every contraction thread's
+      if (k >= 2) named_sync(kBarTnFree + b, kFGThreads);
+      // T^k of chunk k: rows t = AT bj .. AT bj + AT - 1 (AH at a time, to
+      // bound the registers beside the Gram accumulator), pixels 4 bi .. 4 bi + 3
+      const float* in = sIn + b * TP * LDP;
+      float* tnb = sTn + b * TP * LDP;
+#pragma unroll
+      for (int h = 0; h < AT; h += AH) {
+        float o[AH][4];
+#pragma unroll
+        for (int r = 0; r < AH; ++r) o[r][0] = o[r][1] = o[r][2] = o[r][3] = 0.f;
+#pragma unroll 4
+        for (int s = 0; s < TP; ++s) {
+          const float4 xv = *reinterpret_cast<const float4*>(in + s * LDP + 4 * bi);
+          float wv[AH];
+          lds_row<AH>(sW + s * LDS + AT * bj + h, wv);
+#pragma unroll
+          for (int r = 0; r < AH; ++r) {
+            o[r][0] = fmaf(wv[r], xv.x, o[r][0]);
+            o[r][1] = fmaf(wv[r], xv.y, o[r][1]);
+            o[r][2] = fmaf(wv[r], xv.z, o[r][2]);
+            o[r][3] = fmaf(wv[r], xv.w, o[r][3]);
+          }
+        }
+#pragma unroll
+        for (int r = 0; r < AH; ++r)
+          *reinterpret_cast<float4*>(tnb + (AT * bj + h + r) * LDP + 4 * bi) =
+              make_float4(o[r][0], o[r][1], o[r][2], o[r][3]);
+      }
+      named_arrive(kBarTnFull + b, kFGThreads);
+      named_sync(kBarMma, kFGGram);            // every contraction thread is done with tile b of LD^k
+      prefetch(k + 2);
+      if (k >= 1) gram_chunk(k - 1);
     }
+    if (nk >= 1) gram_chunk(nk - 1);
+    cp_async_wait<0>();
     float* out = gpart + (size_t)blockIdx.x * TP * TP;
 #pragma unroll
     for (int r = 0; r < RB; ++r)
@@ -531,9 +627,22 @@ int rpca_gram_parts(const RpcaGeom& g) {
   return (int)(n < 1 ? 1 : n);
 }
 
-cudaError_t rpca_launch_post_pre_gram(const RpcaGeom& g, const RpcaCoeffs& c, const RpcaPlanes& P, int TP,
-                                      double* partials, int nrows, float* gpart, double* G, unsigned* bar, int* err,
-                                      cudaStream_t st) {
+cudaError_t rpca_launch_apply_post_pre_gram(const RpcaGeom& g, const RpcaCoeffs& c, const RpcaPlanes& P, int TP,
+                                            const float* Wm, int store_tn, double* partials, int nrows, float* gpart,
+                                            double* G, unsigned* bar, int* err, cudaStream_t st) {
+  static bool attr_set = false;   // raised once to the largest (TP = 64) size
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(rpca_apply_post_pre_gram_kernel<16>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)between_smem<16>());
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(rpca_apply_post_pre_gram_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)between_smem<32>());
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(rpca_apply_post_pre_gram_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)between_smem<64>());
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(rpca_gram_parts(g));
   cfg.blockDim = dim3(kFGThreads);
@@ -544,9 +653,18 @@ cudaError_t rpca_launch_post_pre_gram(const RpcaGeom& g, const RpcaCoeffs& c, co
   cfg.attrs = coop;
   cfg.numAttrs = 1;
   switch (TP) {
-    case 16: return cudaLaunchKernelEx(&cfg, rpca_post_pre_gram_kernel<16>, g, c, P, partials, nrows, gpart, G, bar, err);
-    case 32: return cudaLaunchKernelEx(&cfg, rpca_post_pre_gram_kernel<32>, g, c, P, partials, nrows, gpart, G, bar, err);
-    case 64: return cudaLaunchKernelEx(&cfg, rpca_post_pre_gram_kernel<64>, g, c, P, partials, nrows, gpart, G, bar, err);
+    case 16:
+      cfg.dynamicSmemBytes = between_smem<16>();
+      return cudaLaunchKernelEx(&cfg, rpca_apply_post_pre_gram_kernel<16>, g, c, P, Wm, store_tn, partials, nrows,
+                                gpart, G, bar, err);
+    case 32:
+      cfg.dynamicSmemBytes = between_smem<32>();
+      return cudaLaunchKernelEx(&cfg, rpca_apply_post_pre_gram_kernel<32>, g, c, P, Wm, store_tn, partials, nrows,
+                                gpart, G, bar, err);
+    case 64:
+      cfg.dynamicSmemBytes = between_smem<64>();
+      return cudaLaunchKernelEx(&cfg, rpca_apply_post_pre_gram_kernel<64>, g, c, P, Wm, store_tn, partials, nrows,
+                                gpart, G, bar, err);
     default: return cudaErrorInvalidValue;
   }
 }
