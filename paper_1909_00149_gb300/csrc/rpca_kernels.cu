@@ -269,7 +269,17 @@ constexpr int kBarTnFull = 1, kBarTnFree = 3, kBarLdFull = 5, kBarLdFree = 7, kB
 
 template <int TP>
 constexpr size_t between_smem() {   // Wm^T, 2 x LD^k chunk, 2 x T^k chunk, 2 x LD^{k+1} chunk
-  return sizeof(float) * ((size_t)TP * (TP + 4) + 4 * (size_t)TP * (kGC + 4) + 2 * (size_t)kGC * (TP + 4));
+  return sizeof(float) * ((size_t)TP * (TP + 4) + 4 * (size_t)TP * (kGC + 4) + 2 * (size_t)kGC * TP);
+}
+
+// Column of frame t in pixel row p of an LD^{k+1} tile (rows of TP floats):
+// groups of 4 frames are permuted by an XOR with p / 4, so that the
+// updating warps' stores (lanes on pixels 4 apart) spread over the banks
+// while every 4-frame group stays contiguous for the Gram's vector reads.
+template <int TP>
+__device__ __forceinline__ int ld_col(int p, int t) {
+  constexpr int mask = (TP / 4 < 8 ? TP / 4 : 8) - 1;
+  return 4 * ((t >> 2) ^ ((p >> 2) & mask)) + (t & 3);
 }
 
 __device__ __forceinline__ void named_sync(int id, int n) {
@@ -401,7 +411,7 @@ rpca_apply_post_pre_gram_kernel(const RpcaGeom g, const RpcaCoeffs c, const Rpca
   float* sW = smf;                       // [TP][LDS]: sW[s][t] = Wm[t][s]
   float* sIn = sW + TP * LDS;            // [2][TP][LDP]: LD^k of a chunk, frame rows
   float* sTn = sIn + 2 * TP * LDP;       // [2][TP][LDP]: T^k of a chunk, frame rows
-  float* sLD = sTn + 2 * TP * LDP;       // [2][kGC][LDS]: LD^{k+1} of a chunk, pixel rows
+  float* sLD = sTn + 2 * TP * LDP;       // [2][kGC][TP]: LD^{k+1} of a chunk, pixel rows (ld_col)
   float acc[kNumSums] = {};
   const int tid = threadIdx.x;
   const int nsm = (int)(between_smem<TP>() / sizeof(float));
@@ -421,14 +431,14 @@ rpca_apply_post_pre_gram_kernel(const RpcaGeom g, const RpcaCoeffs c, const Rpca
       if (k >= 2) named_sync(kBarLdFree + b, kFGThreads);
       const long long p0 = (blockIdx.x + (long long)k * gridDim.x) * kGC;
       const float* tnb = sTn + b * TP * LDP;
-      float* ldb = sLD + b * kGC * LDS;
+      float* ldb = sLD + b * kGC * TP;
 #pragma unroll 2
       for (int it = tid; it < items; it += kFGUpd) {
         const int t = it / (kGC / 4), j = it % (kGC / 4);
         const long long op = p0 + 4 * j;            // offset inside the frame (plane is a multiple of 4)
         if (op >= g.plane) {
 #pragma unroll
-          for (int e = 0; e < 4; ++e) ldb[(4 * j + e) * LDS + t] = 0.f;
+          for (int e = 0; e < 4; ++e) ldb[(4 * j + e) * TP + ld_col<TP>(4 * j + e, t)] = 0.f;
           continue;
         }
         const long long o = (long long)t * g.plane + op;
@@ -458,7 +468,7 @@ rpca_apply_post_pre_gram_kernel(const RpcaGeom g, const RpcaCoeffs c, const Rpca
           f4(ld4, e) = r.ld;
           f4(p04, e) = r.p0;
           f4(p14, e) = r.p1;
-          ldb[(4 * j + e) * LDS + t] = r.ld;
+          ldb[(4 * j + e) * TP + ld_col<TP>(4 * j + e, t)] = r.ld;
         }
         if (store_tn) stg4v(P.Tn + o, tn);
         stg4v(P.A + o, a);
@@ -507,12 +517,23 @@ rpca_apply_post_pre_gram_kernel(const RpcaGeom g, const RpcaCoeffs c, const Rpca
     auto gram_chunk = [&](int j) {
       const int b = j & 1;
       named_sync(kBarLdFull + b, kFGThreads);
-      const float* ldb = sLD + b * kGC * LDS;
+      const float* ldb = sLD + b * kGC * TP;
 #pragma unroll 4
       for (int p = 0; p < kGC; ++p) {
         float av[RB], bv[CB];
-        lds_row<RB>(ldb + p * LDS + RB * bi, av);
-        lds_row<CB>(ldb + p * LDS + CB * bj, bv);
+        lds_row<RB>(ldb + p * TP + ld_col<TP>(p, RB * bi), av);   // RB <= 4: inside one group
+        if constexpr (CB == 8) {
+          float b0[4], b1[4];
+          lds_row<4>(ldb + p * TP + ld_col<TP>(p, 8 * bj), b0);
+          lds_row<4>(ldb + p * TP + ld_col<TP>(p, 8 * bj + 4), b1);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            bv[q] = b0[q];
+            bv[4 + q] = b1[q];
+          }
+        } else {
+          lds_row<CB>(ldb + p * TP + ld_col<TP>(p, CB * bj), bv);
+        }
 #pragma unroll
         for (int r = 0; r < RB; ++r)
 #pragma unroll
@@ -527,8 +548,10 @@ rpca_apply_post_pre_gram_kernel(const RpcaGeom g, const RpcaCoeffs c, const Rpca
       cp_async_wait<1>();                      // this thread's copies of chunk k are in
       named_sync(kBarMma, kFGGram);            // ... and every contraction thread's
       if (k >= 2) named_sync(kBarTnFree + b, kFGThreads);
-      // T^k of chunk k: rows t = AT bj .. AT bj + AT - 1 (AH at a time, to
-      // bound the registers beside the Gram accumulator), pixels 4 bi .. 4 bi + 3
+      // T^k of chunk k, pixels 4 bi .. 4 bi + 3: AT rows t in runs of AH,
+      // the run starting at h = 0, AH, ... covering t = 8 h + AH bj .. + AH - 1
+      // (the 8 threads of a pixel group read consecutive Wm runs), one run at
+      // a time to bound the registers beside the Gram accumulator
       const float* in = sIn + b * TP * LDP;
       float* tnb = sTn + b * TP * LDP;
 #pragma unroll
@@ -540,7 +563,7 @@ rpca_apply_post_pre_gram_kernel(const RpcaGeom g, const RpcaCoeffs c, const Rpca
         for (int s = 0; s < TP; ++s) {
           const float4 xv = *reinterpret_cast<const float4*>(in + s * LDP + 4 * bi);
           float wv[AH];
-          lds_row<AH>(sW + s * LDS + AT * bj + h, wv);
+          lds_row<AH>(sW + s * LDS + 8 * h + AH * bj, wv);
 #pragma unroll
           for (int r = 0; r < AH; ++r) {
             o[r][0] = fmaf(wv[r], xv.x, o[r][0]);
@@ -551,7 +574,7 @@ rpca_apply_post_pre_gram_kernel(const RpcaGeom g, const RpcaCoeffs c, const Rpca
         }
 #pragma unroll
         for (int r = 0; r < AH; ++r)
-          *reinterpret_cast<float4*>(tnb + (AT * bj + h + r) * LDP + 4 * bi) =
+          *reinterpret_cast<float4*>(tnb + (8 * h + AH * bj + r) * LDP + 4 * bi) =
               make_float4(o[r][0], o[r][1], o[r][2], o[r][3]);
       }
       named_arrive(kBarTnFull + b, kFGThreads);
