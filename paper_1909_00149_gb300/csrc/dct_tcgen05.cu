@@ -250,12 +250,12 @@ struct TcPlan {
 
 template <int NT, bool TRANS, bool SCALE, bool OUT_BF16>
 cudaError_t launch_tc(const TcMaps& maps, const TcEpi& ep, int* err, cudaStream_t st) {
-  static bool attr_set = false;
-  if (!attr_set) {
+  static unsigned long long attr_set = 0;
+  if (needs_setup(attr_set)) {
     const cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<NT, TRANS, SCALE, OUT_BF16>,
                                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem<NT>());
     if (e != cudaSuccess) return e;
-    attr_set = true;
+    mark_setup(attr_set);
   }
   const dim3 grid((ep.M + kTM - 1) / kTM, (ep.N + NT - 1) / NT);
   tc_gemm_kernel<NT, TRANS, SCALE, OUT_BF16><<<grid, 128, tc_smem<NT>(), st>>>(maps, ep, err);

@@ -8,6 +8,19 @@
 
 namespace otp {
 
+// One-time setup per device (a kernel's attributes belong to the context of
+// the device it runs on): needs_setup is true until mark_setup has recorded
+// the current device in `done` (devices 0-63; others always set up).
+inline bool needs_setup(unsigned long long done) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return true;
+  return !(done & (1ull << dev));
+}
+inline void mark_setup(unsigned long long& done) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < 64) done |= 1ull << dev;
+}
+
 // ----------------------------------------------------------------- tiling
 // Tiled Algorithm 1 iteration: a CTA owns kTH rows x kTW columns of one
 // problem; 32 x 8 threads, each thread a float4 column group on kRPT rows.

@@ -653,8 +653,8 @@ int rpca_gram_parts(const RpcaGeom& g) {
 cudaError_t rpca_launch_apply_post_pre_gram(const RpcaGeom& g, const RpcaCoeffs& c, const RpcaPlanes& P, int TP,
                                             const float* Wm, int store_tn, double* partials, int nrows, float* gpart,
                                             double* G, unsigned* bar, int* err, cudaStream_t st) {
-  static bool attr_set = false;   // raised once to the largest (TP = 64) size
-  if (!attr_set) {
+  static unsigned long long attr_set = 0;   // raised once to the largest (TP = 64) size
+  if (needs_setup(attr_set)) {
     cudaError_t e = cudaFuncSetAttribute(rpca_apply_post_pre_gram_kernel<16>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)between_smem<16>());
     if (e == cudaSuccess)
@@ -664,7 +664,7 @@ cudaError_t rpca_launch_apply_post_pre_gram(const RpcaGeom& g, const RpcaCoeffs&
       e = cudaFuncSetAttribute(rpca_apply_post_pre_gram_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)between_smem<64>());
     if (e != cudaSuccess) return e;
-    attr_set = true;
+    mark_setup(attr_set);
   }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(rpca_gram_parts(g));

@@ -222,12 +222,12 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap xmap, int T, int nchunks, flo
 template <int TP>
 cudaError_t launch_gram_tc(const CUtensorMap& m, int T, int nchunks, int grid, float* partials, int* err,
                            cudaStream_t st) {
-  static bool attr = false;
-  if (!attr) {
+  static unsigned long long attr = 0;
+  if (needs_setup(attr)) {
     const cudaError_t e =
         cudaFuncSetAttribute(gram_tc_kernel<TP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gram_tc_smem<TP>());
     if (e != cudaSuccess) return e;
-    attr = true;
+    mark_setup(attr);
   }
   gram_tc_kernel<TP><<<grid, kGThreads, gram_tc_smem<TP>(), st>>>(m, T, nchunks, partials, err);
   return cudaGetLastError();
@@ -454,12 +454,12 @@ apply_tc_kernel(const __grid_constant__ CUtensorMap xmap, const __grid_constant_
 template <int TP>
 cudaError_t launch_apply_tc(const CUtensorMap& xm, const CUtensorMap& ym, const float* Wm, int T, long long N,
                             int ntiles, int grid, int* err, cudaStream_t st) {
-  static bool attr = false;
-  if (!attr) {
+  static unsigned long long attr = 0;
+  if (needs_setup(attr)) {
     const cudaError_t e = cudaFuncSetAttribute(apply_tc_kernel<TP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                (int)apply_tc_smem<TP>());
     if (e != cudaSuccess) return e;
-    attr = true;
+    mark_setup(attr);
   }
   apply_tc_kernel<TP><<<grid, kAThreads, apply_tc_smem<TP>(), st>>>(xm, ym, Wm, T, N, ntiles, err);
   return cudaGetLastError();

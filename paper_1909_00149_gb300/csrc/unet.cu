@@ -718,12 +718,12 @@ uint32_t conv_smem(int n_out, int* stages) {
 cudaError_t conv_tc(ot_unet* h, const Act& inA, const Act* inB, const CUtensorMap& wmap, int co_total, int n_out,
                     const Act& outA, const Act* outB, int split, int n, const float* bias, bool relu, const Act* maskA,
                     const Act* maskB) {
-  static bool attr = false;
-  if (!attr) {
+  static unsigned long long attr = 0;
+  if (needs_setup(attr)) {
     const cudaError_t e =
         cudaFuncSetAttribute(conv3x3_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 224 * 1024);
     if (e != cudaSuccess) return e;
-    attr = true;
+    mark_setup(attr);
   }
   ConvMaps M;
   M.inA = inA.ld;
