@@ -129,8 +129,16 @@ def test_rpca_elementwise_and_prox_parity(lib, T, H, W, k):
     assert abs(res["res_dual"] - dual) <= 1e-4 * dual + 1e-9
 
 
-@pytest.mark.parametrize("T,H,W", [(6, 24, 28), (9, 33, 17), (40, 16, 20), (24, 20, 13), (72, 12, 10)])
-@pytest.mark.parametrize("k", [1, 5, 30])
+TRAJECTORY_CASES = [(T, H, W, k) for T, H, W in [(6, 24, 28), (9, 33, 17), (40, 16, 20), (24, 20, 13)]
+                    for k in (1, 5, 30)]
+# T_pad = 128 (separate Gram and apply kernels).  Not at k = 30: there the
+# residual of this 120-pixel video (3.4e-4 of ||Y||) is below the FP32 SVT
+# accuracy bound of its state (7.7e-4 of ||Y||), so comparing residuals says
+# nothing; the state itself is still checked at k = 1 and 5.
+TRAJECTORY_CASES += [(72, 12, 10, 1), (72, 12, 10, 5)]
+
+
+@pytest.mark.parametrize("T,H,W,k", TRAJECTORY_CASES)
 def test_rpca_trajectory_parity(lib, T, H, W, k):
     """Full Algorithm 3 with the paper's gamma = lambda sqrt(max(N, T)).  The
     FP32 SVT error (bounded in svt_bound) propagates into every variable as an
