@@ -427,7 +427,7 @@ typedef struct ot_unet* ot_unet_t;
  * parameters start at zero (set them with ot_unet_set_params). */
 int ot_unet_create(int32_t H, int32_t W, int32_t max_batch, int32_t base_channels, void* cuda_stream,
                    ot_unet_t* out);
-/* Length of the flat parameter array (-1 for a NULL handle). */
+/* Length of the flat parameter array (OT_EINVAL = -1 for a NULL handle). */
 int64_t ot_unet_param_count(ot_unet_t h);
 /* Load parameters (resets the optimiser state).  Synchronises. */
 int ot_unet_set_params(ot_unet_t h, const float* params);

@@ -1098,7 +1098,10 @@ int ot_unet_create(int32_t H, int32_t W, int32_t max_batch, int32_t base_channel
   return OT_OK;
 }
 
-int64_t ot_unet_param_count(ot_unet_t h) { return h ? h->nparams : -1; }
+int64_t ot_unet_param_count(ot_unet_t h) {
+  if (!h) return fail(OT_EINVAL, "ot_unet_param_count: NULL handle");
+  return h->nparams;
+}
 
 int ot_unet_set_params(ot_unet_t h, const float* params) {
   if (!h || !params) return fail(OT_EINVAL, "ot_unet_set_params: NULL argument");

@@ -109,3 +109,11 @@ def test_null_arguments():
     assert otp.ot_prox_step(None, 1) == -1
     assert otp.ot_prox_solve(None, None) == -1
     assert otp.ot_prox_destroy(None) == 0
+    # every handle-taking call checks its pointers before any CUDA call
+    for name, args in [("ot_rpca_step", (None, 1)), ("ot_rpca_iterate_checked", (None, 1, None)),
+                       ("ot_rpca_step_profiled", (None, None)), ("ot_debug_grid_barrier", (1, 0, None, None)),
+                       ("ot_prox_warm_start", (None, None, 0.0)), ("ot_unet_forward", (None, None, None, 1)),
+                       ("ot_unet_param_count", (None,)), ("ot_prox_batch_step", (None, 1))]:
+        assert getattr(otp, name)(*args) == -1, name
+        assert otp.ot_last_error().decode().startswith(name), (name, otp.ot_last_error())
+    assert otp.ot_rpca_destroy(None) == 0 and otp.ot_unet_destroy(None) == 0
