@@ -47,7 +47,9 @@ extern "C" {
 #define OT_ECUDA      -3  /* a CUDA runtime call failed (message has the name)  */
 #define OT_ENOTCONV   -4  /* max_iter reached before the tolerance; outputs valid */
 #define OT_ENONFINITE -5  /* a NaN/Inf appeared in the iterates                 */
-#define OT_ETIMEOUT   -6  /* a bounded device wait gave up                      */
+#define OT_ETIMEOUT   -6  /* a bounded device wait gave up (the kernel returned
+                             early, the context stays usable); the handle's
+                             state is then undefined: destroy and recreate it */
 
 /* ------------------------------------------------------------ enumerations */
 /* Which arguments of V_mu are variables (Sec. III-B):
@@ -269,10 +271,12 @@ int ot_rpca_create(const ot_rpca_params* params, void* cuda_stream, ot_rpca_t* o
 int ot_rpca_set_input(ot_rpca_t h, const float* Y);
 /* n_outer >= 0 outer iterations, no residual read.  Async. */
 int ot_rpca_step(ot_rpca_t h, int32_t n_outer);
-/* n_outer >= 1 outer iterations; the residuals of the last one.  Sync. */
+/* n_outer >= 1 outer iterations; the residuals of the last one.  Sync.
+ * OT_ETIMEOUT if a bounded device wait expired in the prox kernel, a
+ * tensor-core kernel or the grid barrier of the pass between iterations. */
 int ot_rpca_iterate_checked(ot_rpca_t h, int32_t n_outer, ot_rpca_result* res);
 /* Iterate until both residuals <= tol or max_iter.  Returns OT_OK,
- * OT_ENOTCONV (state still valid) or OT_ENONFINITE.  Sync. */
+ * OT_ENOTCONV (state still valid), OT_ENONFINITE or OT_ETIMEOUT.  Sync. */
 int ot_rpca_solve(ot_rpca_t h, ot_rpca_result* res);
 /* Two outer iterations (as ot_rpca_step(h, 2)) with CUDA events recorded on
  * the handle's stream between their phases, the eigensolver serialised with
