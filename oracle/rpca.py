@@ -38,6 +38,7 @@ class RpcaParams:
     n_inner: int = 1
     tol: float = 1e-5
     max_iter: int = 5000
+    norm: str = "iso"           # flux norm of the inner prox ("aniso" for the LP/QP pins)
 
 
 @dataclass
@@ -61,10 +62,46 @@ def zero_state(T: int, H: int, W: int) -> RpcaState:
                      P.ProxState(g.copy(), g.copy(), g.copy(), g.copy(), g.copy(), g.copy()))
 
 
+def line7_s(k: np.ndarray, sigma: np.ndarray, lam: float, rho: float) -> np.ndarray:
+    """Line 7: s_t minimises lambda sum(s) + (rho sigma_t / 2) ||s - k_t / sigma_t||^2
+    over s >= 0 (the sigma_t augmented terms that contain s_t, collected)."""
+    return np.maximum(k / sigma - lam / (rho * sigma), 0.0)
+
+
+def line8_l(Tm: np.ndarray, D: np.ndarray, X: np.ndarray, S: np.ndarray, A: np.ndarray) -> np.ndarray:
+    """Line 8: L minimises rho/2 ||X - S - L + A||^2 + rho/2 ||L - Tm + D||^2
+    over L >= 0 (the 1/2 outside or inside Pi_+ is the same)."""
+    return 0.5 * np.maximum(Tm - D + X - S + A, 0.0)
+
+
+def line9_x(Y: np.ndarray, S: np.ndarray, L: np.ndarray, A: np.ndarray, rho: float) -> np.ndarray:
+    """Line 9 with Phi = I: X minimises 1/2 ||Y - X||^2 + rho/2 ||X - S - L + A||^2."""
+    return (Y + rho * (S + L - A)) / (1.0 + rho)
+
+
+def line10_theta(prm: RpcaParams) -> float:
+    """Line 10: Tm minimises gamma ||Tm||_* + rho/2 ||L + D - Tm||^2, i.e. the
+    SVT of L + D at gamma / rho."""
+    return prm.gamma / prm.rho
+
+
+def line11_weight(prm: RpcaParams) -> float:
+    """Line 11: (z_t, w_{t+1}) minimise kappa V_mu(z, w) + rho/2 ||z - s_t + b_t||^2
+    + rho/2 ||w - s_{t+1} + c_{t+1}||^2, the prox of eq. (Prox_UOT) with
+    weight kappa / rho."""
+    return prm.kappa / prm.rho
+
+
+def line12_a(A: np.ndarray, X: np.ndarray, S: np.ndarray, L: np.ndarray) -> np.ndarray:
+    """Line 12: dual ascent on the constraint X - S - L = 0 of the augmented
+    term ||X - S - L + A||^2 (the printed "+ L" is a sign slip)."""
+    return A + X - S - L
+
+
 def prox_params(prm: RpcaParams, H: int, W: int) -> P.ProxParams:
     """Line 11 evaluates prox^mu_{kappa/rho V}: the prox weight of eq.
     (Prox_UOT) is kappa / rho."""
-    return P.default_steps(H, W, P.ProxParams(mu=prm.mu, rho=prm.kappa / prm.rho, mode="prox"))
+    return P.default_steps(H, W, P.ProxParams(mu=prm.mu, rho=line11_weight(prm), mode="prox", norm=prm.norm))
 
 
 def outer_iteration(st: RpcaState, Y: np.ndarray, prm: RpcaParams) -> tuple[RpcaState, float, float]:
@@ -78,14 +115,14 @@ def outer_iteration(st: RpcaState, Y: np.ndarray, prm: RpcaParams) -> tuple[Rpca
     wc = np.concatenate([np.zeros((1, H, W)), w + st.C], axis=0)     # w_t + c_t, t = 2..T
     k = (st.X - st.L + st.A) + om_z * zb + om_w * wc
     sigma = 1.0 + om_z + om_w
-    S = np.maximum(k / sigma - lam / (rho * sigma), 0.0)
+    S = line7_s(k, sigma, lam, rho)
     # line 8
-    L = 0.5 * np.maximum(st.Tm - st.D + st.X - S + st.A, 0.0)
+    L = line8_l(st.Tm, st.D, st.X, S, st.A)
     # line 9 (Phi = I)
-    X = (Y + rho * (S + L - st.A)) / (1.0 + rho)
+    X = line9_x(Y, S, L, st.A, rho)
     # line 10
     N = H * W
-    Tm = SV.svt((L + st.D).reshape(T, N).T, prm.gamma / rho).T.reshape(T, H, W)
+    Tm = SV.svt((L + st.D).reshape(T, N).T, line10_theta(prm)).T.reshape(T, H, W)
     # line 11: warm-started, n_inner Algorithm 1 iterations on the T-1 pairs
     pp = prox_params(prm, H, W)
     c0 = S[:-1] - st.B
@@ -93,7 +130,7 @@ def outer_iteration(st: RpcaState, Y: np.ndarray, prm: RpcaParams) -> tuple[Rpca
     pst = P.iterate(c0, c1, pp, prm.n_inner, state=st.prox)
     z_new, w_new = pst.x0, pst.x1
     # lines 12-15
-    A = st.A + X - S - L
+    A = line12_a(st.A, X, S, L)
     D = st.D + L - Tm
     Bn = st.B + z_new - S[:-1]
     Cn = st.C + w_new - S[1:]

@@ -66,9 +66,15 @@ class UotdfState:
         return self.prox.x1
 
 
+def line6_weight(prm: UotdfParams) -> float:
+    """Line 6: z minimises kappa V_mu(s0, z) + rho/2 ||z - (s - b)||^2, the prox
+    of eq. (Prox_UOT_specialcase) with weight kappa / rho."""
+    return prm.kappa / prm.rho
+
+
 def prox_params(prm: UotdfParams, H: int, W: int) -> P.ProxParams:
     """Line 6: prox of (kappa/rho) V_mu(., s0), the fixed-first form."""
-    return P.default_steps(H, W, P.ProxParams(mu=prm.mu, rho=prm.kappa / prm.rho, mode="fixed_first",
+    return P.default_steps(H, W, P.ProxParams(mu=prm.mu, rho=line6_weight(prm), mode="fixed_first",
                                               norm=prm.norm, p_exp=prm.p_exp))
 
 
@@ -84,6 +90,11 @@ def prox_R(q: np.ndarray, prm: UotdfParams) -> np.ndarray:
     return np.maximum(q - prm.lam / (2.0 * prm.rho), 0.0) if prm.lam > 0 else np.maximum(q, 0.0)
 
 
+def line5_x(y: np.ndarray, s: np.ndarray, a: np.ndarray, rho: float) -> np.ndarray:
+    """Line 5 with Phi = I: x minimises 1/2 ||y - x||^2 + rho/2 ||x - s + a||^2."""
+    return (y + rho * (s - a)) / (1.0 + rho)
+
+
 def iteration(st: UotdfState, y: np.ndarray, s0: np.ndarray, prm: UotdfParams) -> tuple[UotdfState, float, float]:
     """One pass of Algorithm 2's loop body; returns the new state and the
     residuals (relative to ||y||)."""
@@ -92,7 +103,7 @@ def iteration(st: UotdfState, y: np.ndarray, s0: np.ndarray, prm: UotdfParams) -
     H, W = y.shape[-2:]
     rho = prm.rho
     s = prox_R(0.5 * (st.x + st.a + st.prox.x1 + st.b), prm)   # line 4
-    x = (y + rho * (s - st.a)) / (1.0 + rho)           # line 5, Phi = I
+    x = line5_x(y, s, st.a, rho)                       # line 5, Phi = I
     pp = prox_params(prm, H, W)
     pst = P.iterate(s0, s - st.b, pp, prm.n_inner, state=st.prox)   # line 6
     z_old = st.prox.x1

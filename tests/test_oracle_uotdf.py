@@ -12,6 +12,7 @@ import pytest
 from scipy.optimize import Bounds, LinearConstraint, minimize
 
 from oracle import uotdf as U
+from qp_pins import qp_prox_pairs
 
 
 def qp_uotdf(y, s0, kappa, mu, lam):
@@ -52,14 +53,18 @@ def qp_uotdf(y, s0, kappa, mu, lam):
     return res.x[:n].reshape(H, W)
 
 
-@pytest.mark.parametrize("lam,seed", [(0.0, 0), (0.1, 0), (0.0, 3)])
-def test_admm_matches_independent_qp(lam, seed):
+@pytest.mark.parametrize("lam,seed,rho", [(0.0, 0, 1.0), (0.1, 0, 1.0), (0.0, 3, 1.0),
+                                          (0.1, 0, 0.4), (0.1, 0, 2.5), (0.0, 3, 0.4), (0.0, 3, 2.5)])
+def test_admm_matches_independent_qp(lam, seed, rho):
+    """At rho = 1 a misplaced rho (lambda / (2 rho) of line 4, the rho of
+    line 5, the prox weight kappa / rho of line 6) would not show; the fixed
+    point does not depend on rho, so the same QP pins rho = 0.4 and 2.5."""
     rng = np.random.default_rng(seed)
     H, W = 3, 3
     s0 = rng.uniform(0, 1, (H, W)) * (rng.uniform(size=(H, W)) < 0.6)
     y = np.roll(s0, 1, axis=1) * 1.2 + 0.05 * rng.normal(size=(H, W))
     s_qp = qp_uotdf(y, s0, 0.5, 1.0, lam)
-    prm = U.UotdfParams(kappa=0.5, mu=1.0, rho=1.0, lam=lam, n_inner=20, norm="aniso", tol=1e-10, max_iter=50000)
+    prm = U.UotdfParams(kappa=0.5, mu=1.0, rho=rho, lam=lam, n_inner=20, norm="aniso", tol=1e-10, max_iter=50000)
     st, info = U.solve(y[None], s0[None], prm)
     assert info["converged"]
     assert np.max(np.abs(st.s[0] - s_qp)) <= 1e-5
@@ -98,3 +103,61 @@ def test_printed_s_update_would_ignore_the_transport_term():
     y = np.roll(s0, 1, axis=1) * 1.2 + 0.05 * rng.normal(size=(H, W))
     s_qp = qp_uotdf(y, s0, 0.5, 1.0, 0.0)
     assert np.max(np.abs(s_qp - np.maximum(y, 0.0))) > 0.1
+
+
+def uotdf_block_violations(rho, seed=6, n_inner=6000):
+    """One iteration of Algorithm 2 from a random, unconverged state; returns
+    the blocks whose output does not minimise its subproblem of the augmented
+    Lagrangian lam sum s + i_+(s) + 1/2 ||y - x||^2 + kappa V(s0, z)
+    + rho/2 ||x - s + a||^2 + rho/2 ||z - s + b||^2 (written out here)."""
+    rng = np.random.default_rng(seed)
+    B, H, W = 2, 2, 3
+    s0 = rng.uniform(0, 1, (B, H, W)) * (rng.uniform(size=(B, H, W)) < 0.7)
+    y = rng.uniform(0, 1.2, (B, H, W))
+    st = U.zero_state(s0)
+    st.x = rng.uniform(0, 1, (B, H, W))
+    st.a = rng.normal(0, 0.3, (B, H, W))
+    st.b = rng.normal(0, 0.3, (B, H, W))
+    st.prox.x1[...] = rng.uniform(0, 1, (B, H, W))
+    x_old, a_old, b_old, z_old = st.x.copy(), st.a.copy(), st.b.copy(), st.prox.x1.copy()
+    prm = U.UotdfParams(kappa=0.5, mu=1.0, rho=rho, lam=0.1, n_inner=n_inner, norm="aniso")
+    new, _, _ = U.iteration(st, y, s0, prm)
+    fails = []
+    # line 4: lam sum s + rho/2 ||x - s + a||^2 + rho/2 ||z - s + b||^2 over s >= 0
+    s = new.s
+    g = prm.lam - rho * (x_old - s + a_old) - rho * (z_old - s + b_old)
+    if s.min() < 0 or np.max(np.abs(g[s > 0]), initial=0.0) > 1e-10 or np.min(g[s == 0], initial=np.inf) < -1e-10:
+        fails.append("line 4 (s)")
+    # line 5: 1/2 ||y - x||^2 + rho/2 ||x - s + a||^2
+    if np.max(np.abs((new.x - y) + rho * (new.x - s + a_old))) > 1e-10:
+        fails.append("line 5 (x)")
+    # line 6: kappa V(s0, z) + rho/2 ||z - (s - b)||^2 over z >= 0, by the QP
+    _, z_qp = qp_prox_pairs(None, s - b_old, prm.kappa, prm.mu, rho, s0=s0)
+    if np.max(np.abs(new.z - z_qp)) > 1e-6:
+        fails.append("line 6 (z)")
+    active = (s > 0).any() and (s == 0).any()
+    return fails, active
+
+
+@pytest.mark.parametrize("rho", [1.0, 0.4, 2.5])
+def test_blocks_minimise_the_augmented_lagrangian(rho):
+    fails, active = uotdf_block_violations(rho)
+    assert fails == [] and active
+
+
+UOTDF_MUTANTS = {
+    "line 4: lambda / 2": ("prox_R", lambda q, prm: np.maximum(q - prm.lam / 2.0, 0.0)),
+    "line 4: printed rho / lambda": ("prox_R", lambda q, prm: np.maximum(q - prm.rho / prm.lam, 0.0)),
+    "line 5: without rho": ("line5_x", lambda y, s, a, rho: (y + s - a) / (1.0 + rho)),
+    "line 6: kappa": ("line6_weight", lambda prm: prm.kappa),
+}
+
+
+@pytest.mark.parametrize("name", list(UOTDF_MUTANTS))
+def test_planted_mistakes_are_rejected(monkeypatch, name):
+    """Each mistake is planted in the oracle (on the CPU); the block checks at
+    rho = 2.5 must reject it."""
+    attr, mutant = UOTDF_MUTANTS[name]
+    monkeypatch.setattr(U, attr, mutant)
+    fails, _ = uotdf_block_violations(2.5, n_inner=3000)
+    assert fails, name
