@@ -2,14 +2,15 @@
 Phi = I) against the FP64 oracle (one-sided Jacobi SVD, NumPy Algorithm 3).
 
 Tolerances.  Elementwise steps are exact to FP32 rounding.  The SVT goes
-through X^T X: its T x T eigenproblem is solved in FP32, so eigenvalue errors
-are about u ||X||_2^2 in absolute terms and a singular value sigma moves by
-about u ||X||_2^2 / (2 sigma).  Components near the threshold theta are the
-sensitive ones, and their weight max(sigma - theta, 0) is small, so the
-output error relative to ||shrink*(X)|| is about u (sigma_max / theta) (plus
-the u sqrt(T) of the final product).  The tests derive the bound from that
-estimate with a factor of 8 margin, floored at the 1e-5 stated for the FP32
-form.
+through X^T X and an FP32 Jacobi eigensolver whose stopping test bounds the
+first-order change of the SVT output relative to the output (4 u sqrt(T_pad),
+about 2e-6); the warm start deflates the dominant eigenpairs in FP64 before
+rounding, and the eigenvectors carried between outer iterations are
+re-orthonormalised, so that the error stays at that level along a trajectory
+(the oracle's own trajectory moves by about 1e-8 when its state is rounded to
+FP32 once, so no amplification hides behind the tolerance).  The tests hold
+every variable to the stated 1e-5 of ||Y||, with no growth in k, and the SVT
+alone to 1e-5 of its output's norm.
 """
 import numpy as np
 import pytest
@@ -21,12 +22,7 @@ from synth import rng_for, rpca_video
 
 pytestmark = pytest.mark.gpu
 
-U32 = 2.0 ** -24
-
-
-def svt_bound(X, theta):
-    s = np.linalg.svd(X, compute_uv=False)
-    return max(1e-5, 8 * U32 * (s[0] / max(theta, 1e-30) + np.sqrt(X.shape[1])))
+TOL = 1e-5          # the stated relative error of the FP32 form
 
 
 @pytest.mark.parametrize("N,T,rank", [(3000, 8, 2), (4096, 33, 3), (20000, 64, 3), (5000, 100, 4), (999, 5, 1),
@@ -41,7 +37,7 @@ def test_svt_matches_oracle(lib, N, T, rank):
     Xg = torch.from_numpy(np.ascontiguousarray(Xm.T)).cuda()               # T columns of N
     Yg = lib.svt(Xg, theta).cpu().numpy().T.astype(np.float64)
     err = np.linalg.norm(Yg - ref) / np.linalg.norm(ref)
-    assert err <= svt_bound(Xm.astype(np.float64), theta), err
+    assert err <= TOL, err
     # the rank kept equals the oracle's count of singular values above theta
     s_ref = np.linalg.svd(ref, compute_uv=False)
     assert np.sum(np.linalg.svd(Yg, compute_uv=False) > 1e-3 * s_ref[0]) == np.sum(s_ref > 1e-3 * s_ref[0])
@@ -63,10 +59,17 @@ def test_svt_large_threshold_is_zero(lib):
 
 
 RP = dict(lam=0.02, kappa=0.005, mu=3.0, rho=1.0)
+# At rho = 1 a rho in the wrong place (lambda/(rho sigma), gamma/rho,
+# kappa/rho, the rho of the x-update) would not show on either side.
+RHOS = [1.0, 0.4, 2.5]
 
 
-def oracle_rpca(Y, k, gamma, n_inner=1):
-    prm = R.RpcaParams(lam=RP["lam"], gamma=gamma, kappa=RP["kappa"], mu=RP["mu"], rho=RP["rho"], n_inner=n_inner)
+def rp(rho):
+    return dict(RP, rho=rho)
+
+
+def oracle_rpca(Y, k, gamma, n_inner=1, rho=RP["rho"]):
+    prm = R.RpcaParams(lam=RP["lam"], gamma=gamma, kappa=RP["kappa"], mu=RP["mu"], rho=rho, n_inner=n_inner)
     st = R.zero_state(*Y.shape)
     Yd = Y.astype(np.float64)
     res = None
@@ -82,8 +85,10 @@ PROX_VARS = [("Z", "x0"), ("W", "x1"), ("Mx", "Mx"), ("My", "My"), ("r", "r"), (
 
 # The dual accumulators sum differences of nearly equal operands (A += X - S - L,
 # D += L - Tm, b += z - s, c += w - s): their rounding error is relative to
-# those operands, not to their own (small) norm.
-OPERANDS = {"A": ("X",), "D": ("L", "Tm"), "B": ("S",), "C": ("S",)}
+# those operands, not to their own (small) norm.  So is L's: it is half the
+# positive part of Tm - D + X - S + A, which the ADMM drives towards 0 when the
+# SVT output Tm is 0 (gamma large), a sum of much larger terms that cancel.
+OPERANDS = {"A": ("X",), "D": ("L", "Tm"), "B": ("S",), "C": ("S",), "L": ("X", "S", "A", "D")}
 
 
 def rpca_errors(rp, st, scale=None):
@@ -111,20 +116,21 @@ def rp_Y(st):
 
 @pytest.mark.parametrize("T,H,W", [(6, 24, 28), (9, 33, 17)])
 @pytest.mark.parametrize("k", [1, 5, 30])
-def test_rpca_elementwise_and_prox_parity(lib, T, H, W, k):
+@pytest.mark.parametrize("rho", RHOS)
+def test_rpca_elementwise_and_prox_parity(lib, T, H, W, k, rho):
     """gamma above ||L + D||_2 makes the SVT output exactly zero on both sides,
     so this isolates the fused elementwise passes and the inner prox: every
     variable within 1e-5 of the oracle, relative to its own norm."""
     Y, _, _ = rpca_video(rng_for(1, 40 + T), T=T, H=H, W=W, n_blobs=3)
     gamma = 1e6
-    with lib.Rpca(T, H, W, gamma=gamma, **RP) as rp:
-        rp.set_input(Y)
-        res = rp.iterate_checked(k)
-        st, (pri, dual) = oracle_rpca(Y, k, gamma)
-        assert np.max(np.abs(rp.get("T").cpu().numpy())) == 0.0
-        err = rpca_errors(rp, st)
+    with lib.Rpca(T, H, W, gamma=gamma, **rp(rho)) as rp_:
+        rp_.set_input(Y)
+        res = rp_.iterate_checked(k)
+        st, (pri, dual) = oracle_rpca(Y, k, gamma, rho=rho)
+        assert np.max(np.abs(rp_.get("T").cpu().numpy())) == 0.0
+        err = rpca_errors(rp_, st)
     for name, e in err.items():
-        assert e <= 1e-5 * max(1, k / 10), (name, e)
+        assert e <= TOL, (name, e)
     assert abs(res["res_pri"] - pri) <= 1e-4 * pri + 1e-9
     assert abs(res["res_dual"] - dual) <= 1e-4 * dual + 1e-9
 
@@ -139,67 +145,72 @@ TRAJECTORY_CASES += [(72, 12, 10, 1), (72, 12, 10, 5)]
 
 
 @pytest.mark.parametrize("T,H,W,k", TRAJECTORY_CASES)
-def test_rpca_trajectory_parity(lib, T, H, W, k):
+@pytest.mark.parametrize("rho", RHOS)
+def test_rpca_trajectory_parity(lib, T, H, W, k, rho):
     """Full Algorithm 3 with the paper's gamma = lambda sqrt(max(N, T)).  The
-    FP32 SVT error (bounded in svt_bound) propagates into every variable as an
-    absolute error of that size relative to the data, so all variables are
-    measured against ||Y||; the SVT output itself against its own norm."""
+    FP32 SVT error propagates into every variable as an absolute error of
+    that size relative to the data, so all variables are measured against
+    ||Y||; the SVT output itself against its own norm."""
     Y, _, _ = rpca_video(rng_for(1, 40 + T), T=T, H=H, W=W, n_blobs=3)
     gamma = RP["lam"] * np.sqrt(max(H * W, T))
-    with lib.Rpca(T, H, W, **RP) as rp:
-        rp.set_input(Y)
-        res = rp.iterate_checked(k)
-        st, (pri, dual) = oracle_rpca(Y, k, gamma)
-        tol = svt_bound((st.L + st.D).reshape(T, -1).T, gamma / RP["rho"]) * max(1, k / 5)
-        err = rpca_errors(rp, st, scale=np.linalg.norm(Y.astype(np.float64)))
-        tm = rpca_errors(rp, st)["T"]
+    with lib.Rpca(T, H, W, **rp(rho)) as rp_:
+        rp_.set_input(Y)
+        res = rp_.iterate_checked(k)
+        st, (pri, dual) = oracle_rpca(Y, k, gamma, rho=rho)
+        err = rpca_errors(rp_, st, scale=np.linalg.norm(Y.astype(np.float64)))
+        tm = rpca_errors(rp_, st)["T"]
     for name, e in err.items():
-        assert e <= tol, (name, e, tol)
-    assert tm <= tol or np.linalg.norm(st.Tm) == 0
-    assert abs(res["res_pri"] - pri) <= 1e-2 * pri + 1e-9
-    assert abs(res["res_dual"] - dual) <= 1e-2 * dual + 1e-9
+        assert e <= TOL, (name, e)
+    assert tm <= 3 * TOL or np.linalg.norm(st.Tm) == 0, tm
+    assert abs(res["res_pri"] - pri) <= 2e-3 * pri + 1e-9
+    assert abs(res["res_dual"] - dual) <= 2e-3 * dual + 1e-9
 
 
-def test_rpca_solve_converges_and_matches_oracle(lib):
+@pytest.mark.parametrize("rho", [1.0, 2.5])
+def test_rpca_solve_converges_and_matches_oracle(lib, rho):
     T, H, W = 6, 20, 20
     Y, _, _ = rpca_video(rng_for(1, 50), T=T, H=H, W=W, n_blobs=2)
     gamma = RP["lam"] * np.sqrt(max(H * W, T))
-    with lib.Rpca(T, H, W, tol=1e-6, max_iter=20000, **RP) as rp:
-        rp.set_input(Y)
-        res = rp.solve()
-        S = rp.get("S").double().cpu().numpy()
-        L = rp.get("L").double().cpu().numpy()
+    with lib.Rpca(T, H, W, tol=1e-6, max_iter=20000, **rp(rho)) as rp_:
+        rp_.set_input(Y)
+        res = rp_.solve()
+        S = rp_.get("S").double().cpu().numpy()
+        L = rp_.get("L").double().cpu().numpy()
     assert res["status"] == 0, res
-    prm = R.RpcaParams(lam=RP["lam"], gamma=gamma, kappa=RP["kappa"], mu=RP["mu"], rho=RP["rho"], tol=1e-6,
+    prm = R.RpcaParams(lam=RP["lam"], gamma=gamma, kappa=RP["kappa"], mu=RP["mu"], rho=rho, tol=1e-6,
                        max_iter=20000)
     st, info = R.solve(Y, prm)
     assert info["converged"]
-    # both are within ~tol of the same fixed point
+    # the same iteration on both sides, stopped by the same rule: the two
+    # stopping points agree to FP32 accuracy (measured 2e-6 and 2e-5 of ||Y||
+    # at rho = 1 and 2.5), though each lies about 5e-4 of ||Y|| from the limit
     ny = np.linalg.norm(Y)
-    assert np.linalg.norm(S - st.S) <= 1e-3 * ny
-    assert np.linalg.norm(L - st.L) <= 1e-3 * ny
+    assert np.linalg.norm(S - st.S) <= 1e-4 * ny
+    assert np.linalg.norm(L - st.L) <= 1e-4 * ny
     assert np.min(S) >= 0 and np.min(L) >= 0
 
 
-def test_rpca_full_size_two_iterations(lib):
-    """The 64-frame 256x256 video (rank-3 clutter, 8 blobs, noise 0.02): two
-    outer iterations of the benchmark's step against the oracle."""
+@pytest.mark.parametrize("k", [2, 10])
+def test_rpca_full_size_trajectory(lib, k):
+    """The 64-frame 256x256 video (rank-3 clutter, 8 blobs, noise 0.02): k
+    outer iterations of the benchmark's step (the fused passes between
+    iterations, the interval graph) against the oracle, every variable within
+    1e-5 of ||Y||."""
     from synth import rpca_video_64x256x256
     Y, _, _ = rpca_video_64x256x256()
     T, H, W = Y.shape
     gamma = RP["lam"] * np.sqrt(max(H * W, T))
-    with lib.Rpca(T, H, W, **RP) as rp:
-        rp.set_input(torch.from_numpy(Y).cuda())
-        res = rp.iterate_checked(2)
-        st, (pri, dual) = oracle_rpca(Y, 2, gamma)
-        tol = svt_bound((st.L + st.D).reshape(T, -1).T, gamma / RP["rho"])
-        err = rpca_errors(rp, st, scale=np.linalg.norm(Y.astype(np.float64)))
-        tm = rpca_errors(rp, st)["T"]
+    with lib.Rpca(T, H, W, check_every=k, **RP) as rp_:
+        rp_.set_input(torch.from_numpy(Y).cuda())
+        res = rp_.iterate_checked(k)
+        st, (pri, dual) = oracle_rpca(Y, k, gamma)
+        err = rpca_errors(rp_, st, scale=np.linalg.norm(Y.astype(np.float64)))
+        tm = rpca_errors(rp_, st)["T"]
     for name, e in err.items():
-        assert e <= tol, (name, e, tol)
-    assert tm <= tol
-    assert abs(res["res_pri"] - pri) <= 1e-2 * pri
-    assert abs(res["res_dual"] - dual) <= 1e-2 * dual
+        assert e <= TOL, (name, e)
+    assert tm <= 3 * TOL, tm
+    assert abs(res["res_pri"] - pri) <= 1e-3 * pri
+    assert abs(res["res_dual"] - dual) <= 1e-3 * dual
 
 
 def test_rpca_rejects_bad_parameters(lib):
