@@ -218,6 +218,17 @@ int ot_prox_destroy(ot_prox_t h);
  * x-update keeps rho (line 9), s_t >= 0 (line 7).  Stopping: the ADMM primal
  * and dual residuals (Boyd), each relative to ||Y||, both <= tol. */
 typedef struct ot_rpca* ot_rpca_t;
+/* Signed foreground (signed_fg = 1; eq. RPCA_UOTDF_PN, Sec. IV-B, the
+ * real-video experiment): S = S+ - S- with S+, S- >= 0 and a transport term
+ * kappa V_mu(s+-_t, s+-_{t+1}) for each sign.  The paper gives only this
+ * objective; the iteration is Algorithm 3's ADMM with its splitting applied
+ * to each sign (X = S+ - S- + L, z+-_t = s+-_t, w+-_{t+1} = s+-_{t+1}, duals
+ * b+-, c+-), the S+ block updated before the S- block, each by its exact
+ * block minimiser (line 7 with S- in S+'s data target, S+ - X + L - A as
+ * S-'s), lines 8-10 on S = S+ - S-, line 11 for both signs as one batch of
+ * 2 (T - 1) Algorithm 1 problems, lines 12-15 for both signs.  Residuals
+ * add both signs' terms.  The SVT runs as its own Gram, eigensolver and
+ * apply kernels (not fused with the elementwise passes). */
 
 typedef struct {
   int32_t T, H, W;        /* frames (2..128), rows, columns                      */
@@ -233,6 +244,8 @@ typedef struct {
   int32_t svt_max_sweeps; /* Jacobi sweeps cap of the T x T eigensolver           */
   int32_t prox_kernel;    /* OT_KERNEL_* of the inner Algorithm 1                 */
   int32_t use_graph;      /* 1: replay warm outer iterations as a CUDA graph     */
+  int32_t signed_fg;      /* 1: signed foreground S = S+ - S- (eq. RPCA_UOTDF_PN),
+                             see below; 0: S >= 0 (eq. RPCA_UOTDF)                */
 } ot_rpca_params;
 
 typedef struct {
@@ -260,6 +273,11 @@ typedef struct {
 #define OT_RPCA_MY   11   /* inner prox flux My (pairs)            */
 #define OT_RPCA_R    12   /* inner prox source r (pairs)           */
 #define OT_RPCA_DUAL 13   /* inner prox dual a (pairs)             */
+#define OT_RPCA_SP   14   /* signed_fg: S+ (frames)                */
+#define OT_RPCA_SM   15   /* signed_fg: S- (frames)                */
+/* signed_fg: OT_RPCA_MINUS | (a pair variable, 6..13) reads the S- sign's
+ * copy of it; the plain id reads the S+ sign's.  OT_RPCA_S reads S+ - S-. */
+#define OT_RPCA_MINUS 0x100
 
 /* Defaults: lambda 0.02, gamma lambda sqrt(max(N,T)), kappa 0.005, mu 3,
  * rho 1, n_inner 1, tol 1e-5, max_iter 5000, check_every 1,
@@ -288,7 +306,10 @@ int ot_rpca_solve(ot_rpca_t h, ot_rpca_result* res);
  * lines 4-9 of the second (for T <= 64 also the first's SVT apply and the
  * second's Gram matrix, its partials reduced in the same launch), 7 the
  * second's Gram where that pass does not produce it (T > 64; about 0
- * otherwise).  Sync. */
+ * otherwise).  With signed_fg: one outer iteration, whose phases are 0 the
+ * lines 4-9 pass, 1 the Gram, 2 the eigensolver, 3 the SVT apply, 4 the
+ * Algorithm 1 iterations on both signs' pairs, 5 the lines 12-15 pass; 6 and
+ * 7 are 0 (no fused pass).  Sync. */
 int ot_rpca_step_profiled(ot_rpca_t h, double* phase_ms);
 
 /* Copy one variable (OT_RPCA_*) out, dense.  Sync. */
@@ -490,7 +511,9 @@ int ot_neumann_solve(const float* X, float* Y, int32_t B, int32_t H, int32_t W, 
  *  - cuda_stream: cudaStream_t or NULL.  Sync: returns after the stream
  *    reaches the end of the evaluation.
  * The first call on a device looks up the scratch array's device address
- * for that device; make that first call before any stream capture.  All
+ * for that device (and looks it up again after a cudaDeviceReset, which
+ * ends the context it belongs to); make that first call before any stream
+ * capture.  All
  * calls share the one array, so calls that overlap on the GPU (other
  * streams, other threads) race and give wrong results; every call rewrites
  * all the scratch it reads, so nothing needs clearing between calls. */

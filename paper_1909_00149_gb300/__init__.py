@@ -199,7 +199,7 @@ def rpca_default_params(**kw) -> "_abi.ot_rpca_params":
         k = "lambda_" if k in ("lam", "lambda") else k
         if k == "prox_kernel":
             v = KERNELS[v] if isinstance(v, str) else v
-        elif k == "use_graph":
+        elif k in ("use_graph", "signed_fg"):
             v = int(bool(v))
         if not hasattr(p, k):
             raise TypeError(f"unknown parameter {k!r}")
@@ -262,12 +262,15 @@ class Rpca:
     def reset(self):
         check(_lib.ot_rpca_reset(self.h), "ot_rpca_reset")
 
-    def get(self, name: str, device=None):
+    def get(self, name: str, device=None, out=None):
+        """Copy of a variable ([T] or [T-1] x H x W float32) into ``out`` (host
+        or device, e.g. pinned host memory) or a new tensor on ``device``."""
         import torch
         nf = self.T - 1 if name in _abi.RPCA_PAIR_VARS else self.T
-        dev = torch.device("cuda") if device is None else torch.device(device)
-        out = torch.empty((nf, self.H, self.W), dtype=torch.float32, device=dev)
-        A = _Arrays(out.numel())
+        if out is None:
+            dev = torch.device("cuda") if device is None else torch.device(device)
+            out = torch.empty((nf, self.H, self.W), dtype=torch.float32, device=dev)
+        A = _Arrays(nf * self.H * self.W)
         check(_lib.ot_rpca_get(self.h, _abi.RPCA_VARS[name], A.ptr(out, True)), "ot_rpca_get")
         return out
 

@@ -53,7 +53,8 @@ class ot_rpca_params(ctypes.Structure):
                 ("lambda_", ctypes.c_double), ("gamma", ctypes.c_double), ("kappa", ctypes.c_double),
                 ("mu", ctypes.c_double), ("rho", ctypes.c_double), ("n_inner", ctypes.c_int32),
                 ("tol", ctypes.c_double), ("max_iter", ctypes.c_int32), ("check_every", ctypes.c_int32),
-                ("svt_max_sweeps", ctypes.c_int32), ("prox_kernel", ctypes.c_int32), ("use_graph", ctypes.c_int32)]
+                ("svt_max_sweeps", ctypes.c_int32), ("prox_kernel", ctypes.c_int32), ("use_graph", ctypes.c_int32),
+                ("signed_fg", ctypes.c_int32)]
 
 
 class ot_rpca_result(ctypes.Structure):
@@ -91,8 +92,14 @@ class ot_uotdf_result(ctypes.Structure):
 UOTDF_VARS = {"s": 0, "x": 1, "z": 2, "a": 3, "b": 4}
 
 RPCA_VARS = {"S": 0, "L": 1, "X": 2, "T": 3, "A": 4, "D": 5, "B": 6, "C": 7, "Z": 8, "W": 9,
-             "Mx": 10, "My": 11, "r": 12, "a": 13}
+             "Mx": 10, "My": 11, "r": 12, "a": 13, "Sp": 14, "Sm": 15}
 RPCA_PAIR_VARS = {"B", "C", "Z", "W", "Mx", "My", "r", "a"}
+# signed foreground: a pair variable of the S- sign is its name with a "-"
+# suffix ("Z-", "B-", ...), read with this flag on the variable id
+RPCA_MINUS = 0x100
+for _n in list(RPCA_PAIR_VARS):
+    RPCA_VARS[_n + "-"] = RPCA_VARS[_n] | RPCA_MINUS
+RPCA_PAIR_VARS |= {_n + "-" for _n in RPCA_PAIR_VARS}
 
 # (name, restype, argtypes)
 PROTOTYPES = [

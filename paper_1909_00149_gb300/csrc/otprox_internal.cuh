@@ -201,6 +201,10 @@ struct RpcaPlanes {
   float *X, *L, *A, *Tm, *D, *Y, *S, *LD;
   float* Tn;                // the SVT output of this outer iteration (Tm holds the previous one)
   float *z, *w, *Bz, *Cw, *p0, *p1, *zprev, *wprev;
+  // signed-foreground variant only: S+ and S- frame planes (S = S+ - S-);
+  // every pair plane then holds both signs, S- at sgn_off floats after S+
+  float *Sp, *Sm;
+  long long sgn_off;
 };
 int rpca_num_blocks(const RpcaGeom& g);
 cudaError_t rpca_launch_pre(const RpcaGeom& g, const RpcaCoeffs& c, const RpcaPlanes& P, double* partials,
@@ -224,6 +228,11 @@ cudaError_t rpca_launch_apply_post_pre_gram(const RpcaGeom& g, const RpcaCoeffs&
 // preset (diagnostic: ot_debug_grid_barrier)
 cudaError_t grid_barrier_probe(int ctas, unsigned preset, int* err, unsigned* generation);
 cudaError_t rpca_launch_sumsq(const RpcaGeom& g, const float* Y, double* partials, cudaStream_t st);
+// signed-foreground variant (rpca_pn_kernels.cu): lines 4-9 and 12-15 for S+
+// and S-, residual sums in the same slots as rpca_launch_pre / _post
+cudaError_t rpca_launch_pn_pre(const RpcaGeom& g, const RpcaCoeffs& c, const RpcaPlanes& P, double* partials,
+                               cudaStream_t st);
+cudaError_t rpca_launch_pn_post(const RpcaGeom& g, const RpcaPlanes& P, double* partials, cudaStream_t st);
 
 // ----------------------------------------------------------------- SVT
 int svt_padded_T(int T);                       // 16, 32, 64 or 128

@@ -34,6 +34,7 @@ struct ot_rpca {
   RpcaGeom G;
   RpcaCoeffs C;
   float* slab;
+  size_t slab_floats;
   RpcaPlanes P;
   ot_prox* prox;             // B = T-1 problems, rho_prox = kappa / rho
   // SVT workspace
@@ -87,6 +88,7 @@ void ot_rpca_default_params(ot_rpca_params* p) {
   p->svt_max_sweeps = 30;
   p->prox_kernel = OT_KERNEL_AUTO;
   p->use_graph = 1;
+  p->signed_fg = 0;
 }
 
 int ot_rpca_destroy(ot_rpca_t h) {
@@ -120,6 +122,7 @@ int ot_rpca_create(const ot_rpca_params* params, void* cuda_stream, ot_rpca_t* o
   if (p.max_iter < 0 || p.check_every < 1 || p.svt_max_sweeps < 1)
     return fail(OT_EINVAL, "ot_rpca_create: max_iter >= 0, check_every >= 1, svt_max_sweeps >= 1 required");
   if (!(p.tol >= 0)) return fail(OT_EINVAL, "ot_rpca_create: tol must be >= 0");
+  if (p.signed_fg != 0 && p.signed_fg != 1) return fail(OT_EINVAL, "ot_rpca_create: signed_fg must be 0 or 1");
   const double N = (double)p.H * p.W;
   if (p.gamma <= 0) p.gamma = p.lambda * sqrt(N > p.T ? N : (double)p.T);
 
@@ -136,10 +139,12 @@ int ot_rpca_create(const ot_rpca_params* params, void* cuda_stream, ot_rpca_t* o
   h->C.rho = (float)p.rho;
   h->TP = svt_padded_T(p.T);
 
-  // the inner prox: B = T-1 pairs, weight kappa / rho (line 11)
+  // the inner prox: B = T-1 pairs (both signs' 2 (T-1) for the signed
+  // foreground), weight kappa / rho (line 11)
+  const int nsign = p.signed_fg ? 2 : 1;
   ot_prox_params pp;
   ot_prox_default_params(&pp);
-  pp.B = p.T - 1;
+  pp.B = nsign * (p.T - 1);
   pp.H = p.H;
   pp.W = p.W;
   pp.mode = OT_MODE_PROX;
@@ -157,7 +162,9 @@ int ot_rpca_create(const ot_rpca_params* params, void* cuda_stream, ot_rpca_t* o
 
   const size_t plane = (size_t)h->G.plane;
   const size_t nframe = (size_t)p.T * plane, npair = (size_t)(p.T - 1) * plane;
-  cudaError_t e = cudaMalloc(&h->slab, (9 * nframe + 4 * npair) * sizeof(float));
+  // Y is the sixth plane; ot_rpca_reset zeroes everything before and after it
+  h->slab_floats = (9 + 2 * (nsign - 1)) * nframe + 4 * nsign * npair;
+  cudaError_t e = cudaMalloc(&h->slab, h->slab_floats * sizeof(float));
   if (e != cudaSuccess) {
     ot_rpca_destroy(h);
     return cuda_fail(e, "ot_rpca_create: cudaMalloc(state)");
@@ -172,11 +179,16 @@ int ot_rpca_create(const ot_rpca_params* params, void* cuda_stream, ot_rpca_t* o
   P.Y = q; q += nframe;
   P.S = q; q += nframe;
   P.LD = q; q += nframe;
-  P.Bz = q; q += npair;
-  P.Cw = q; q += npair;
-  P.zprev = q; q += npair;
-  P.wprev = q; q += npair;
+  P.Bz = q; q += nsign * npair;
+  P.Cw = q; q += nsign * npair;
+  P.zprev = q; q += nsign * npair;
+  P.wprev = q; q += nsign * npair;
   P.Tn = q; q += nframe;
+  if (p.signed_fg) {
+    P.Sp = q; q += nframe;
+    P.Sm = q; q += nframe;
+  }
+  P.sgn_off = (long long)npair;
   P.z = h->prox->x0;
   P.w = h->prox->x1;
   P.p0 = h->prox->p0;
@@ -202,7 +214,7 @@ int ot_rpca_create(const ot_rpca_params* params, void* cuda_stream, ot_rpca_t* o
     h->dsums = h->partials + (size_t)(3 * h->nb_rpca + h->nb_apply) * kNumSums;
     e = cudaMallocHost(&h->hsums, (kNumSums + 2 + 128) * sizeof(double));
   }
-  if (e == cudaSuccess && TP <= 64) {
+  if (e == cudaSuccess && TP <= 64 && !p.signed_fg) {
     h->fgram_parts = rpca_gram_parts(h->G);
     const size_t nf = (size_t)h->fgram_parts * TP * TP;
     e = cudaMalloc(&h->fgram, nf * sizeof(float) + 4 * sizeof(unsigned));
@@ -215,7 +227,7 @@ int ot_rpca_create(const ot_rpca_params* params, void* cuda_stream, ot_rpca_t* o
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming);
-  if (e == cudaSuccess) e = cudaMemsetAsync(h->slab, 0, (9 * nframe + 4 * npair) * sizeof(float), h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->slab, 0, h->slab_floats * sizeof(float), h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) {
     ot_rpca_destroy(h);
@@ -233,14 +245,12 @@ int ot_rpca_get_params(ot_rpca_t h, ot_rpca_params* out) {
 
 int ot_rpca_reset(ot_rpca_t h) {
   if (!h) return fail(OT_EINVAL, "ot_rpca_reset: NULL handle");
-  const size_t plane = (size_t)h->G.plane;
-  const size_t nframe = (size_t)h->prm.T * plane, npair = (size_t)(h->prm.T - 1) * plane;
-  // every plane but Y (X L A Tm D are adjacent, as are S LD and the pair planes; Tm, Tn may have swapped)
-  OT_CUDA(cudaMemsetAsync(h->P.X, 0, 3 * nframe * sizeof(float), h->stream), "ot_rpca_reset");
-  OT_CUDA(cudaMemsetAsync(h->P.D, 0, nframe * sizeof(float), h->stream), "ot_rpca_reset");
-  OT_CUDA(cudaMemsetAsync(h->P.Tm, 0, nframe * sizeof(float), h->stream), "ot_rpca_reset");
-  OT_CUDA(cudaMemsetAsync(h->P.Tn, 0, nframe * sizeof(float), h->stream), "ot_rpca_reset");
-  OT_CUDA(cudaMemsetAsync(h->P.S, 0, (2 * nframe + 4 * npair) * sizeof(float), h->stream), "ot_rpca_reset");
+  const size_t nframe = (size_t)h->prm.T * (size_t)h->G.plane;
+  // every plane but Y, the sixth of the slab (Tm and Tn may have swapped, but
+  // both lie in the zeroed ranges)
+  OT_CUDA(cudaMemsetAsync(h->slab, 0, 5 * nframe * sizeof(float), h->stream), "ot_rpca_reset");
+  OT_CUDA(cudaMemsetAsync(h->slab + 6 * nframe, 0, (h->slab_floats - 6 * nframe) * sizeof(float), h->stream),
+          "ot_rpca_reset");
   h->warm = 0;
   return ot_prox_reset(h->prox);
 }
@@ -352,20 +362,66 @@ static int enqueue_interval(ot_rpca* h, int n, bool sums) {
   return OT_OK;
 }
 
+// The signed-foreground variant: per outer iteration lines 4-9 for both
+// signs, the SVT as its own Gram, eigensolver (beside line 11 on a side
+// stream) and apply, line 11 on both signs' 2 (T-1) pairs, and lines 12-15;
+// the residual rows of lines 4-9 are [0, nb), of lines 12-15 [nb, 2 nb).
+static int enqueue_interval_pn(ot_rpca* h, int n, bool sums) {
+  const long long plane = h->G.plane;
+  for (int k = 0; k < n; ++k) {
+    OT_CUDA(rpca_launch_pn_pre(h->G, h->C, h->P, h->partials, h->stream), "rpca signed pre");
+    OT_CUDA(svt_launch_gram(h->P.LD, plane, plane, h->prm.T, h->gram_partials, h->Gm, h->prox->derr, h->stream),
+            "svt gram");
+    OT_CUDA(cudaEventRecord(h->ev_fork, h->stream), "fork");
+    OT_CUDA(cudaStreamWaitEvent(h->side, h->ev_fork, 0), "fork wait");
+    OT_CUDA(svt_launch_eig(h->Gm, h->prm.T, h->warm, (float)(h->prm.gamma / h->prm.rho), h->prm.svt_max_sweeps,
+                           svt_tolerance(h->prm.T), h->V, h->Wm, h->sig, h->sweeps, h->side),
+            "svt eig");
+    h->warm = 1;
+    OT_CUDA(cudaEventRecord(h->ev_join, h->side), "join");
+    const int rc = ot_prox_step(h->prox, h->prm.n_inner);
+    if (rc != OT_OK) return rc;
+    OT_CUDA(cudaStreamWaitEvent(h->stream, h->ev_join, 0), "join wait");
+    OT_CUDA(svt_launch_apply(h->P.LD, plane, plane, h->prm.T, h->Wm, h->P.Tn, plane, false, nullptr, h->prox->derr,
+                             h->stream),
+            "svt apply");
+    OT_CUDA(rpca_launch_pn_post(h->G, h->P, post_rows(h), h->stream), "rpca signed post");
+    swap_svt_planes(h);
+  }
+  if (sums) {
+    OT_CUDA(launch_finalize_sums(h->partials, 2 * h->nb_rpca, h->dsums, h->stream), "rpca finalize");
+    OT_CUDA(cudaMemcpyAsync(h->hsums, h->dsums, kNumSums * sizeof(double), cudaMemcpyDeviceToHost, h->stream),
+            "rpca sums copy");
+    OT_CUDA(cudaMemcpyAsync(reinterpret_cast<int*>(h->hsums + kNumSums), h->sweeps, sizeof(int),
+                            cudaMemcpyDeviceToHost, h->stream),
+            "rpca sweeps copy");
+    OT_CUDA(cudaMemcpyAsync(reinterpret_cast<float*>(h->hsums + kNumSums + 2), h->sig, h->TP * sizeof(float),
+                            cudaMemcpyDeviceToHost, h->stream),
+            "rpca sigma copy");
+    OT_CUDA(cudaMemcpyAsync(h->prox->herr, h->prox->derr, sizeof(int), cudaMemcpyDeviceToHost, h->stream),
+            "rpca error flag copy");
+  }
+  return OT_OK;
+}
+
 // n outer iterations.  An interval of check_every iterations with a warm
 // eigensolver replays from a CUDA graph (one per starting parity of the
 // inner prox state and of the SVT output planes; the graph bakes in the warm
 // flag and the buffers of those parities, and always finalises the sums);
 // anything else is enqueued directly.
+static int enqueue_any(ot_rpca* h, int n, bool sums) {
+  return h->prm.signed_fg ? enqueue_interval_pn(h, n, sums) : enqueue_interval(h, n, sums);
+}
+
 static int run_interval(ot_rpca* h, int n, bool sums) {
   const bool can_graph = h->prm.use_graph && h->stream != nullptr && h->warm && n == h->prm.check_every;
-  if (!can_graph) return enqueue_interval(h, n, sums);
+  if (!can_graph) return enqueue_any(h, n, sums);
   ot_prox* px = h->prox;
   const int par = px->cur, tp = h->tpar;
   if (!h->graph[par][tp]) {
     cudaGraph_t g = nullptr;
     OT_CUDA(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal), "rpca graph capture");
-    const int rc = enqueue_interval(h, n, true);
+    const int rc = enqueue_any(h, n, true);
     const cudaError_t e2 = cudaStreamEndCapture(h->stream, &g);
     // capture enqueued nothing: undo the parity bookkeeping
     px->cur = par;
@@ -479,9 +535,60 @@ int ot_debug_grid_barrier(int32_t ctas, uint32_t preset_count, int32_t* err, uin
   return OT_OK;
 }
 
+// One signed-foreground outer iteration with its phases serialised and timed.
+static int step_profiled_pn(ot_rpca* h, double* phase_ms) {
+  constexpr int kEv = 7;
+  cudaEvent_t ev[kEv] = {};
+  cudaError_t e = cudaSuccess;
+  for (int k = 0; k < kEv && e == cudaSuccess; ++k) e = cudaEventCreate(&ev[k]);
+  const long long plane = h->G.plane;
+  int rc = OT_OK;
+  auto rec = [&](int k) {
+    if (e == cudaSuccess && rc == OT_OK) e = cudaEventRecord(ev[k], h->stream);
+  };
+  rec(0);
+  if (e == cudaSuccess) e = rpca_launch_pn_pre(h->G, h->C, h->P, h->partials, h->stream);
+  rec(1);
+  if (e == cudaSuccess)
+    e = svt_launch_gram(h->P.LD, plane, plane, h->prm.T, h->gram_partials, h->Gm, h->prox->derr, h->stream);
+  rec(2);
+  if (e == cudaSuccess) {
+    e = svt_launch_eig(h->Gm, h->prm.T, h->warm, (float)(h->prm.gamma / h->prm.rho), h->prm.svt_max_sweeps,
+                       svt_tolerance(h->prm.T), h->V, h->Wm, h->sig, h->sweeps, h->stream);
+    h->warm = 1;
+  }
+  rec(3);
+  if (e == cudaSuccess) rc = ot_prox_step(h->prox, h->prm.n_inner);
+  rec(4);
+  if (e == cudaSuccess && rc == OT_OK)
+    e = svt_launch_apply(h->P.LD, plane, plane, h->prm.T, h->Wm, h->P.Tn, plane, false, nullptr, h->prox->derr,
+                         h->stream);
+  rec(5);
+  if (e == cudaSuccess && rc == OT_OK) {
+    e = rpca_launch_pn_post(h->G, h->P, post_rows(h), h->stream);
+    swap_svt_planes(h);
+  }
+  rec(6);
+  if (e == cudaSuccess && rc == OT_OK) e = cudaEventSynchronize(ev[6]);
+  // phases: pre, Gram, eig, apply, prox, post
+  const int from[6] = {0, 1, 2, 4, 3, 5}, to[6] = {1, 2, 3, 5, 4, 6};
+  for (int k = 0; k < 6 && e == cudaSuccess && rc == OT_OK; ++k) {
+    float ms = 0.f;
+    e = cudaEventElapsedTime(&ms, ev[from[k]], ev[to[k]]);
+    phase_ms[k] = ms;
+  }
+  phase_ms[6] = phase_ms[7] = 0.0;
+  for (int k = 0; k < kEv; ++k)
+    if (ev[k]) cudaEventDestroy(ev[k]);
+  if (rc != OT_OK) return rc;
+  if (e != cudaSuccess) return cuda_fail(e, "ot_rpca_step_profiled");
+  return OT_OK;
+}
+
 int ot_rpca_step_profiled(ot_rpca_t h, double* phase_ms) {
   if (!h || !phase_ms) return fail(OT_EINVAL, "ot_rpca_step_profiled: NULL argument");
   if (!h->have_input) return fail(OT_EINVAL, "ot_rpca_step_profiled: no input (call ot_rpca_set_input)");
+  if (h->prm.signed_fg) return step_profiled_pn(h, phase_ms);
   // the kernels of ot_rpca_step(h, 2), serialised on the handle's stream:
   //   ev0 pre ev1 Gram ev2 eig ev3 [apply, T_pad > 64] ev4 prox ev5 fused pass ev6
   //   [Gram, T_pad > 64] ev7 eig ev8 apply ev9 prox ev10 post ev11
@@ -562,6 +669,14 @@ int ot_rpca_get(ot_rpca_t h, int32_t var, float* out) {
   const RpcaPlanes& P = h->P;
   const float* src = nullptr;
   int nf = h->prm.T;
+  const bool minus = (var & OT_RPCA_MINUS) != 0;
+  if (minus) {
+    var &= ~OT_RPCA_MINUS;
+    if (!h->prm.signed_fg || var < OT_RPCA_B || var > OT_RPCA_DUAL)
+      return fail(OT_EINVAL, "ot_rpca_get: OT_RPCA_MINUS needs the signed foreground and a pair variable");
+  }
+  if ((var == OT_RPCA_SP || var == OT_RPCA_SM) && !h->prm.signed_fg)
+    return fail(OT_EINVAL, "ot_rpca_get: S+ and S- exist only with signed_fg");
   switch (var) {
     case OT_RPCA_S: src = P.S; break;
     case OT_RPCA_L: src = P.L; break;
@@ -577,8 +692,11 @@ int ot_rpca_get(ot_rpca_t h, int32_t var, float* out) {
     case OT_RPCA_MY: src = h->prox->My[h->prox->cur]; nf = h->prm.T - 1; break;
     case OT_RPCA_R: src = h->prox->r; nf = h->prm.T - 1; break;
     case OT_RPCA_DUAL: src = h->prox->a[h->prox->cur]; nf = h->prm.T - 1; break;
+    case OT_RPCA_SP: src = P.Sp; break;
+    case OT_RPCA_SM: src = P.Sm; break;
     default: return fail(OT_EINVAL, "ot_rpca_get: unknown variable %d", var);
   }
+  if (minus) src += P.sgn_off;     // the S- sign's pairs follow the S+ sign's
   const size_t wb = (size_t)h->G.W * sizeof(float);
   OT_CUDA(cudaMemcpy2DAsync(out, wb, src, (size_t)h->G.Wp * sizeof(float), wb, (size_t)nf * h->G.H,
                             cudaMemcpyDefault, h->stream),

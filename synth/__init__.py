@@ -127,6 +127,31 @@ def rpca_video(rng: np.random.Generator, T: int = 64, H: int = 256, W: int = 256
     return Y.astype(np.float32), L.astype(np.float32), S.astype(np.float32)
 
 
+def signed_rpca_video(rng: np.random.Generator, T: int = 64, H: int = 256, W: int = 256,
+                      rank: int = 3, n_blobs: int = 8, noise: float = 0.02, **kw):
+    """As ``rpca_video``, but every second blob is darker than the
+    background (its amplitude negated): the foreground of the signed
+    variant, S = S+ - S-.  The background is lifted by 1 so that Y stays
+    positive under the dark blobs.  Returns (Y, L, S)."""
+    rng2 = np.random.Generator(np.random.PCG64(rng.integers(0, 2**63)))
+    Y, L, S = rpca_video(rng, T, H, W, rank=rank, n_blobs=0, noise=noise, **kw)
+    Sd = np.zeros((T, H, W), np.float64)
+    sigma_blob, max_speed = kw.get("sigma_blob", 3.0), kw.get("max_speed", 2.0)
+    for k in range(n_blobs):
+        cy, cx = rng2.uniform(0.15 * H, 0.85 * H), rng2.uniform(0.15 * W, 0.85 * W)
+        ang = rng2.uniform(0.0, 2.0 * np.pi)
+        spd = rng2.uniform(0.0, max_speed)
+        vy, vx = spd * np.sin(ang), spd * np.cos(ang)
+        amp = rng2.uniform(0.5, 1.0) * (1.0 if k % 2 == 0 else -1.0)
+        t0 = int(rng2.integers(0, max(T // 2, 1)))
+        t1 = int(rng2.integers(t0 + 1, T + 1))
+        for t in range(t0, t1):
+            Sd[t] += _blob(H, W, cy + vy * (t - t0), cx + vx * (t - t0), amp, sigma_blob)
+    L1 = L.astype(np.float64) + 1.0
+    Y = Y.astype(np.float64) + 1.0 + Sd
+    return Y.astype(np.float32), L1.astype(np.float32), Sd.astype(np.float32)
+
+
 def uneven_sequences(rng: np.random.Generator, n_seq: int = 48,
                      sizes=(96, 128, 192, 256, 384), t_range=(8, 64)):
     """``n_seq`` blob videos with H, W drawn independently from ``sizes`` and

@@ -117,3 +117,22 @@ def test_null_arguments():
         assert getattr(otp, name)(*args) == -1, name
         assert otp.ot_last_error().decode().startswith(name), (name, otp.ot_last_error())
     assert otp.ot_rpca_destroy(None) == 0 and otp.ot_unet_destroy(None) == 0
+
+
+def test_param_structs_match_their_ctypes_mirrors(cdll):
+    """The default-parameter calls write exactly the C structs: a buffer one
+    ctypes-size long plus a sentinel tail keeps its tail, so the C struct is
+    no larger than the binding's mirror; the fields the mirror names come back
+    with the documented defaults."""
+    from paper_1909_00149_gb300 import _abi
+    for name, cls in (("ot_rpca_default_params", _abi.ot_rpca_params),
+                      ("ot_prox_default_params", _abi.ot_prox_params)):
+        n = ctypes.sizeof(cls)
+        buf = (ctypes.c_ubyte * (n + 64))(*([0xA5] * (n + 64)))
+        fn = getattr(cdll, name)
+        fn.restype = None
+        fn(ctypes.byref(buf))
+        assert bytes(buf[n:]) == b"\xa5" * 64, name
+        p = cls.from_buffer_copy(bytes(buf[:n]))
+        if cls is _abi.ot_rpca_params:
+            assert p.signed_fg == 0 and p.use_graph == 1 and p.rho == 1.0 and p.kappa == 0.005
