@@ -7,6 +7,7 @@
 // pool which forbids allocations outside it, or a latency-critical loop where
 // cudaMalloc/cudaFree would synchronise the device.  This entry point calls
 // no cudaMalloc, cudaFree or any allocating library routine.
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <math.h>
 #include <string.h>
@@ -37,23 +38,63 @@ constexpr long long kMaxElems = 2147483647LL;   // B * H * W
 static __device__ __align__(256) double g_eval_scratch[kScratchDoubles];
 
 std::mutex g_setup_mu;
-double* g_scratch_ptr[kMaxDevices] = {};
+struct ScratchEntry {
+  unsigned long long ctx_id;   // context the address belongs to (0 = none yet)
+  double* ptr;
+};
+ScratchEntry g_scratch[kMaxDevices] = {};
 
-// Device address of the scratch array on the current device, looked up once
-// per device (the first call on a device does this set-up).
+typedef CUresult (*CtxGetCurrentFn)(CUcontext*);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long*);
+
+// Unique id of the context current on this thread (the device's primary
+// context once the runtime has set it up).  A cudaDeviceReset by the caller
+// ends that context; the next one has a new id, so an address looked up in
+// the old one is never reused.
+int current_context_id(unsigned long long* id) {
+  static CtxGetCurrentFn get_current = nullptr;
+  static CtxGetIdFn get_id = nullptr;
+  if (!get_current || !get_id) {
+    void* p = nullptr;
+    void* q = nullptr;
+    cudaDriverEntryPointQueryResult r1, r2;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &r1) != cudaSuccess ||
+        r1 != cudaDriverEntryPointSuccess ||
+        cudaGetDriverEntryPointByVersion("cuCtxGetId", &q, 12000, cudaEnableDefault, &r2) != cudaSuccess ||
+        r2 != cudaDriverEntryPointSuccess)
+      return fail(OT_ECUDA, "ot_prox_evaluate_noalloc: driver entry points cuCtxGetCurrent / cuCtxGetId unavailable");
+    get_current = reinterpret_cast<CtxGetCurrentFn>(p);
+    get_id = reinterpret_cast<CtxGetIdFn>(q);
+  }
+  CUcontext ctx = nullptr;
+  if (get_current(&ctx) != CUDA_SUCCESS || !ctx || get_id(ctx, id) != CUDA_SUCCESS)
+    return fail(OT_ECUDA, "ot_prox_evaluate_noalloc: no current CUDA context");
+  return OT_OK;
+}
+
+// Device address of the scratch array in the current device's context,
+// looked up once per device and context (the first call on a device, and the
+// first after a cudaDeviceReset, does this set-up).
 int scratch_for_current_device(double** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_fail(e, "ot_prox_evaluate_noalloc: cudaGetDevice");
   if (dev < 0 || dev >= kMaxDevices) return fail(OT_EINVAL, "ot_prox_evaluate_noalloc: device %d out of range", dev);
+  // makes the device's primary context current on this thread (set up if needed)
+  e = cudaSetDevice(dev);
+  if (e != cudaSuccess) return cuda_fail(e, "ot_prox_evaluate_noalloc: cudaSetDevice");
+  unsigned long long ctx_id = 0;
+  int rc = current_context_id(&ctx_id);
+  if (rc != OT_OK) return rc;
   std::lock_guard<std::mutex> lock(g_setup_mu);
-  if (!g_scratch_ptr[dev]) {
+  if (g_scratch[dev].ctx_id != ctx_id || !g_scratch[dev].ptr) {
     void* p = nullptr;
     e = cudaGetSymbolAddress(&p, g_eval_scratch);
     if (e != cudaSuccess) return cuda_fail(e, "ot_prox_evaluate_noalloc: cudaGetSymbolAddress");
-    g_scratch_ptr[dev] = static_cast<double*>(p);
+    g_scratch[dev].ptr = static_cast<double*>(p);
+    g_scratch[dev].ctx_id = ctx_id;
   }
-  *out = g_scratch_ptr[dev];
+  *out = g_scratch[dev].ptr;
   return OT_OK;
 }
 

@@ -3,7 +3,7 @@
 Every pixel of a sequence goes through the same arithmetic as the
 one-problem tiled kernel (the same tile body, whatever the tile height), so
 the batched iterates must equal OtProx(kernel="tiled") on each sequence bit
-for bit, and the per-sequence stopping decisions must coincide.  One small
+for bit, and the per-sequence stopping decisions must coincide.  Every
 sequence is also checked against the FP64 oracle.
 """
 import numpy as np
@@ -72,21 +72,23 @@ def test_batch_solve_matches_single_problem_solves(lib, kernel):
             assert torch.equal(states[k][name], ref[name]), (k, name)
 
 
-def test_batch_sequence_matches_oracle(lib):
-    """One sequence of the batch against the FP64 oracle trajectory."""
+@pytest.mark.parametrize("mode", ["prox", "fixed_first"])
+def test_batch_sequences_match_oracle(lib, mode):
+    """Every sequence of the uneven batch against the FP64 oracle trajectory
+    (its own size, hence its own step sizes from Theorem 1's lambda_max)."""
     n = 40
     ins = [seq_inputs(20 + k, *sz) for k, sz in enumerate(SIZES)]
-    with lib.ProxBatch(SIZES, **KW) as bt:
+    with lib.ProxBatch(SIZES, mode=mode, **KW) as bt:
         for k, (p0, p1) in enumerate(ins):
             bt.set_input(k, p0, p1)
         bt.step(n)
-        got = {k: v.double().cpu().numpy() for k, v in bt.get_state(0).items()}
-    p0, p1 = ins[0]
-    st = P.iterate(p0.astype(np.float64), p1.astype(np.float64), P.ProxParams(**KW), n)
-    for name in ("Mx", "My", "x0", "x1", "r", "a"):
-        o = getattr(st, name)
-        e = np.linalg.norm(got[name] - o) / max(np.linalg.norm(o), 1e-3 * np.linalg.norm(p0))
-        assert e <= 1e-5 * max(1, n / 20), (name, e)
+        got = [{k: v.double().cpu().numpy() for k, v in bt.get_state(q).items()} for q in range(len(SIZES))]
+    for q, (p0, p1) in enumerate(ins):
+        st = P.iterate(p0.astype(np.float64), p1.astype(np.float64), P.ProxParams(mode=mode, **KW), n)
+        for name in ("Mx", "My", "x0", "x1", "r", "a"):
+            o = getattr(st, name)
+            e = np.linalg.norm(got[q][name] - o) / max(np.linalg.norm(o), 1e-3 * np.linalg.norm(p0))
+            assert e <= 1e-5 * max(1, n / 20), (q, name, e)
 
 
 def test_batch_autotune_keeps_results(lib):

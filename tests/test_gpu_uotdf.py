@@ -42,12 +42,15 @@ CASES = [dict(lam=0.0, norm="iso", p_exp=1, n_inner=1),
 
 @pytest.mark.parametrize("case", range(len(CASES)))
 @pytest.mark.parametrize("k", [1, 10, 50])
-def test_uotdf_trajectory_parity(lib, case, k):
+@pytest.mark.parametrize("rho", [1.0, 0.4, 2.5])
+def test_uotdf_trajectory_parity(lib, case, k, rho):
+    """rho != 1 as well: at rho = 1 a misplaced rho (lambda/(2 rho), the
+    x-update's rho, the prox weight kappa/rho) would not show."""
     B, H, W = 2, 24, 30
     c = CASES[case]
     y, s0 = inputs(B, H, W, 10 + case)
-    prm = U.UotdfParams(kappa=0.5, mu=3.0, rho=1.0, **c)
-    with lib.Uotdf(B, H, W, kappa=0.5, mu=3.0, rho=1.0, **c) as u:
+    prm = U.UotdfParams(kappa=0.5, mu=3.0, rho=rho, **c)
+    with lib.Uotdf(B, H, W, kappa=0.5, mu=3.0, rho=rho, **c) as u:
         u.set_input(y, s0)
         res = u.iterate_checked(k)
         got = {n: u.get(n).double().cpu().numpy() for n in VARS}
@@ -61,11 +64,12 @@ def test_uotdf_trajectory_parity(lib, case, k):
     assert np.min(got["s"]) >= 0
 
 
-def test_uotdf_solve_matches_oracle(lib):
+@pytest.mark.parametrize("rho", [1.0, 2.5])
+def test_uotdf_solve_matches_oracle(lib, rho):
     B, H, W = 3, 20, 20
     y, s0 = inputs(B, H, W, 21)
-    prm = U.UotdfParams(kappa=0.5, mu=3.0, rho=1.0, n_inner=1, tol=1e-6, max_iter=20000)
-    with lib.Uotdf(B, H, W, kappa=0.5, mu=3.0, rho=1.0, n_inner=1, tol=1e-6, max_iter=20000) as u:
+    prm = U.UotdfParams(kappa=0.5, mu=3.0, rho=rho, n_inner=1, tol=1e-6, max_iter=20000)
+    with lib.Uotdf(B, H, W, kappa=0.5, mu=3.0, rho=rho, n_inner=1, tol=1e-6, max_iter=20000) as u:
         u.set_input(y, s0)
         res = u.solve()
         s = u.get("s").double().cpu().numpy()
