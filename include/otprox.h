@@ -84,11 +84,17 @@ extern "C" {
 #define OT_ALG_PROJECTION  1
 
 /* Arithmetic of the dense DCT contractions (the Neumann solve below):
- *  FP32       -- FP32 CUDA-core GEMMs;
- *  SPLIT_BF16 -- tcgen05 tensor-core GEMMs on a 3-term BF16 split
- *                (a_hi b_hi + a_hi b_lo + a_lo b_hi, FP32 accumulation). */
-#define OT_PREC_FP32       0
-#define OT_PREC_SPLIT_BF16 1
+ *  FP32         -- FP32 CUDA-core GEMMs;
+ *  SPLIT_BF16   -- tcgen05 tensor-core GEMMs on a 2-piece BF16 split, three
+ *                  products (a_hi b_hi + a_hi b_lo + a_lo b_hi), FP32
+ *                  accumulation: about 2^-17 relative per product (a solve
+ *                  about 1e-5 of its result);
+ *  SPLIT_BF16_3 -- the exact 3-piece split (h + m + l = x for every FP32 x)
+ *                  and the six products down to 2^-16 (hh, hm, mh, mm, hl,
+ *                  lh): FP32-level results at twice the tensor work. */
+#define OT_PREC_FP32         0
+#define OT_PREC_SPLIT_BF16   1
+#define OT_PREC_SPLIT_BF16_3 2
 
 typedef struct ot_prox* ot_prox_t;
 
@@ -492,6 +498,12 @@ int ot_svt(const float* X, float* Y, int64_t N, int32_t T, double theta, void* c
  * precision: OT_PREC_*.  Allocates its tables per call.  Sync. */
 int ot_neumann_solve(const float* X, float* Y, int32_t B, int32_t H, int32_t W, double c, int32_t precision,
                      void* cuda_stream);
+/* The same solve on one set of tables, once untimed and then n_rep >= 1
+ * times between CUDA events on cuda_stream; *ms_per_solve (host) = the
+ * device time of one solve (for split BF16: the operand split and the four
+ * tensor-core GEMMs).  X must not alias Y here.  Sync. */
+int ot_neumann_solve_timed(const float* X, float* Y, int32_t B, int32_t H, int32_t W, double c, int32_t precision,
+                           int32_t n_rep, double* ms_per_solve, void* cuda_stream);
 
 /* ot_prox_evaluate for a state the caller holds, without allocating.
  * The paper has no counterpart: this is a convenience for callers that

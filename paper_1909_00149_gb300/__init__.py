@@ -525,6 +525,19 @@ def neumann_solve(X, c: float, precision="fp32", out=None, stream=None):
     return Y
 
 
+def neumann_solve_timed(X, c: float, precision="fp32", n_rep: int = 10, out=None, stream=None) -> float:
+    """Device milliseconds of one (D D* + c I)^{-1} X solve, averaged over
+    n_rep solves on one set of tables (ot_neumann_solve_timed)."""
+    import torch
+    B, H, W = X.shape
+    Y = torch.empty_like(X) if out is None else out
+    prec = _abi.PRECISIONS[precision] if isinstance(precision, str) else precision
+    ms = ctypes.c_double()
+    check(_lib.ot_neumann_solve_timed(X.data_ptr(), Y.data_ptr(), B, H, W, float(c), prec, int(n_rep),
+                                      ctypes.byref(ms), _stream_handle(stream)), "ot_neumann_solve_timed")
+    return ms.value
+
+
 def svt(X, theta: float, stream=None):
     """shrink*_theta of the N x T matrix whose T columns are X[t] (X: [T, ...]
     float32 CUDA tensor).  Returns a tensor of the same shape."""

@@ -20,7 +20,7 @@ STATUS_NAMES = {0: "OT_OK", -1: "OT_EINVAL", -2: "OT_ENOMEM", -3: "OT_ECUDA", -4
 MODES = {"prox": 0, "fixed_first": 1, "eval": 2}
 NORMS = {"iso": 0, "aniso": 1}
 KERNELS = {"auto": 0, "tiled": 1, "resident": 2, "tma": 3}
-PRECISIONS = {"fp32": 0, "split_bf16": 1}
+PRECISIONS = {"fp32": 0, "split_bf16": 1, "split_bf16_3": 2}
 ALGORITHMS = {"alg1": 0, "projection": 1}
 
 c_float_p = ctypes.POINTER(ctypes.c_float)
@@ -175,6 +175,9 @@ PROTOTYPES = [
                               ctypes.c_void_p]),
     ("ot_neumann_solve", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
                                          ctypes.c_int32, ctypes.c_double, ctypes.c_int32, ctypes.c_void_p]),
+    ("ot_neumann_solve_timed", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
+                                               ctypes.c_int32, ctypes.c_double, ctypes.c_int32, ctypes.c_int32,
+                                               ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]),
     ("ot_prox_evaluate_noalloc", ctypes.c_int, [ctypes.POINTER(ot_prox_params)] + [ctypes.c_void_p] * 8 +
      [ctypes.POINTER(ot_prox_result), ctypes.c_void_p]),
 ]

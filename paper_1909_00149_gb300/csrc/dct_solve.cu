@@ -14,8 +14,9 @@
 //   G2: Xhat^T = U^T C_H^T, / lam   rows (b, l) -> stored [B][W][H]  (scaled)
 //   G3: P      = Xhat'^T C_H        rows (b, l) -> stored transposed [B][H][W]
 //   G4: Y      = P^T C_W            rows (b, i) -> stored [B][H][W]
-// Precision OT_PREC_FP32: FP32 CUDA-core tiles.  OT_PREC_SPLIT_BF16: tcgen05
-// tensor-core GEMMs on a 3-term BF16 split (dct_tcgen05.cu).
+// Precision OT_PREC_FP32: FP32 CUDA-core tiles.  OT_PREC_SPLIT_BF16 and
+// OT_PREC_SPLIT_BF16_3: tcgen05 tensor-core GEMMs on a 2- or 3-piece BF16
+// split of every operand (dct_tcgen05.cu).
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -165,7 +166,7 @@ int dct_plan_create(int B, int H, int W, double c, int precision, DctPlan** out)
     dct_plan_destroy(p);
     return cuda_fail(e, "dct plan: device tables");
   }
-  if (precision == OT_PREC_SPLIT_BF16) {
+  if (precision == OT_PREC_SPLIT_BF16 || precision == OT_PREC_SPLIT_BF16_3) {
     const int rc = dct_tc_create(p);
     if (rc != OT_OK) {
       dct_plan_destroy(p);
@@ -183,7 +184,7 @@ void dct_plan_set_error_flag(DctPlan* p, int* derr) {
 // Y = (D D* + c I)^{-1} X for B problems; X, Y device [B][H][*] with row
 // pitch x_ld / y_ld floats (problem stride H * ld).  X and Y may alias.
 cudaError_t dct_plan_solve(DctPlan* p, const float* X, long long x_ld, float* Y, long long y_ld, cudaStream_t st) {
-  if (p->precision == OT_PREC_SPLIT_BF16) return dct_tc_solve(p, X, x_ld, Y, y_ld, st);
+  if (p->precision != OT_PREC_FP32) return dct_tc_solve(p, X, x_ld, Y, y_ld, st);
   const int B = p->B, H = p->H, W = p->W;
   float* U = p->work;
   const dim3 blk(256);
@@ -222,7 +223,7 @@ extern "C" int ot_neumann_solve(const float* X, float* Y, int32_t B, int32_t H, 
   if (!X || !Y) return fail(OT_EINVAL, "ot_neumann_solve: NULL argument");
   if (B < 1 || H < 1 || W < 1) return fail(OT_EINVAL, "ot_neumann_solve: B, H, W must be >= 1");
   if (!(c >= 0) || !isfinite(c)) return fail(OT_EINVAL, "ot_neumann_solve: c must be >= 0");
-  if (precision != OT_PREC_FP32 && precision != OT_PREC_SPLIT_BF16)
+  if (precision != OT_PREC_FP32 && precision != OT_PREC_SPLIT_BF16 && precision != OT_PREC_SPLIT_BF16_3)
     return fail(OT_EINVAL, "ot_neumann_solve: unknown precision %d", precision);
   if ((double)B * H * W > 2.0e9) return fail(OT_EINVAL, "ot_neumann_solve: problem too large");
   DctPlan* p = nullptr;
@@ -237,5 +238,43 @@ extern "C" int ot_neumann_solve(const float* X, float* Y, int32_t B, int32_t H, 
   dct_plan_destroy(p);
   if (e != cudaSuccess) return cuda_fail(e, "ot_neumann_solve");
   if (flag) return fail(OT_ETIMEOUT, "ot_neumann_solve: a bounded device wait expired in a tensor-core GEMM");
+  return OT_OK;
+}
+
+// The same solve repeated n_rep times on one plan, bracketed by CUDA events
+// on the caller's stream after one untimed solve: the device time of one
+// solve (the operand split and the four GEMMs for split BF16), without the
+// plan's set-up.
+extern "C" int ot_neumann_solve_timed(const float* X, float* Y, int32_t B, int32_t H, int32_t W, double c,
+                                      int32_t precision, int32_t n_rep, double* ms_per_solve, void* cuda_stream) {
+  if (!X || !Y || !ms_per_solve) return fail(OT_EINVAL, "ot_neumann_solve_timed: NULL argument");
+  if (B < 1 || H < 1 || W < 1) return fail(OT_EINVAL, "ot_neumann_solve_timed: B, H, W must be >= 1");
+  if (!(c >= 0) || !isfinite(c)) return fail(OT_EINVAL, "ot_neumann_solve_timed: c must be >= 0");
+  if (precision != OT_PREC_FP32 && precision != OT_PREC_SPLIT_BF16 && precision != OT_PREC_SPLIT_BF16_3)
+    return fail(OT_EINVAL, "ot_neumann_solve_timed: unknown precision %d", precision);
+  if (n_rep < 1) return fail(OT_EINVAL, "ot_neumann_solve_timed: n_rep must be >= 1");
+  if ((double)B * H * W > 2.0e9) return fail(OT_EINVAL, "ot_neumann_solve_timed: problem too large");
+  DctPlan* p = nullptr;
+  int rc = dct_plan_create(B, H, W, c, precision, &p);
+  if (rc != OT_OK) return rc;
+  const cudaStream_t st = (cudaStream_t)cuda_stream;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e == cudaSuccess) e = dct_plan_solve(p, X, W, Y, W, st);
+  if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+  for (int k = 0; k < n_rep && e == cudaSuccess; ++k) e = dct_plan_solve(p, X, W, Y, W, st);
+  if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+  if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+  float ms = 0.f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+  int flag = 0;
+  if (e == cudaSuccess && p->err) e = cudaMemcpy(&flag, p->err, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  dct_plan_destroy(p);
+  if (e != cudaSuccess) return cuda_fail(e, "ot_neumann_solve_timed");
+  if (flag) return fail(OT_ETIMEOUT, "ot_neumann_solve_timed: a bounded device wait expired in a tensor-core GEMM");
+  *ms_per_solve = ms / n_rep;
   return OT_OK;
 }

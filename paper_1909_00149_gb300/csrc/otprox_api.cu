@@ -292,7 +292,7 @@ int ot_prox_create(const ot_prox_params* params, void* cuda_stream, ot_prox_t* o
   if (p.kernel < 0 || p.kernel > 3) return fail(OT_EINVAL, "ot_prox_create: unknown kernel %d", p.kernel);
   if (p.algorithm != OT_ALG_ALG1 && p.algorithm != OT_ALG_PROJECTION)
     return fail(OT_EINVAL, "ot_prox_create: unknown algorithm %d", p.algorithm);
-  if (p.precision != OT_PREC_FP32 && p.precision != OT_PREC_SPLIT_BF16)
+  if (p.precision != OT_PREC_FP32 && p.precision != OT_PREC_SPLIT_BF16 && p.precision != OT_PREC_SPLIT_BF16_3)
     return fail(OT_EINVAL, "ot_prox_create: unknown precision %d", p.precision);
   if (p.algorithm == OT_ALG_PROJECTION && (!(p.beta > 0) || !isfinite(p.beta)))
     return fail(OT_EINVAL, "ot_prox_create: beta must be > 0");

@@ -8,7 +8,7 @@ scaling amplifies it by at most the condition number (lam_max + c) / (lam_min
 The test bound is 8 u sqrt(max(H, W)) times that condition number, floored at
 1e-5.
 
-Split-BF16 precision (tensor cores).  Every GEMM operand is held as two BF16
+Split-BF16 precision (tensor cores, "split_bf16").  Every GEMM operand is held as two BF16
 pieces, x = hi + lo with |x - hi - lo| <= 2^-18 |x|, and the lo*lo product is
 dropped (another 2^-18 per term).  Along the four transforms the input and
 the three intermediates are re-split (four representation errors) and each
@@ -18,7 +18,11 @@ the second and third transform amplifies, and only components along small
 eigenvalues; for c >= 1 (the projection form's shifts) the test bound is
 8 * 2^-18 * sqrt(cond), about 1.1e-4 at c = 1.  One projection iteration is
 firmly nonexpansive, so over k iterations the trajectory error grows at most
-like k times the per-solve bound.
+like k times the per-solve bound.  The 3-piece split ("split_bf16_3": an
+exact representation, six products down to 2^-16, the correction products in
+their own accumulator) is held to the FP32 solve's bound per solve and to an
+eighth of the 2-piece bound: what remains is the tensor cores' FP32
+accumulation.
 """
 import numpy as np
 import pytest
@@ -80,6 +84,25 @@ def test_neumann_solve_split_bf16_matches_oracle(lib, B, H, W, c):
         assert eb <= 2 * split_bound(H, W, c), (b, eb)
 
 
+@pytest.mark.parametrize("B,H,W", [(3, 17, 30), (1, 64, 64), (2, 256, 256), (2, 96, 130), (1, 1, 9), (5, 200, 72),
+                                   (2, 1024, 1024)])
+@pytest.mark.parametrize("c", [3.0, 1.0])
+def test_neumann_solve_split_bf16_3_matches_fp32_bound(lib, B, H, W, c):
+    """The exact 3-piece split with six products: the FP32 solve's bound
+    (the dropped products are below 2^-24 of each term), well under the
+    2-piece split's."""
+    rng = np.random.default_rng(B * 1000 + H + W + 9)
+    X = rng.normal(size=(B, H, W)).astype(np.float32)
+    ref = dct.neumann_solve(X.astype(np.float64), c) if H * W <= 256 * 256 else None
+    Y = lib.neumann_solve(torch.from_numpy(X).cuda(), c, "split_bf16_3").double().cpu().numpy()
+    if ref is None:   # 1024 x 1024: one problem by the oracle
+        ref = dct.neumann_solve(X[:1].astype(np.float64), c)
+        Y = Y[:1]
+    err = np.linalg.norm(Y - ref) / np.linalg.norm(ref)
+    assert err <= solve_bound(H, W, c), err
+    assert err <= split_bound(H, W, c) / 8, err
+
+
 def test_neumann_solve_split_bf16_large_batch_sampled(lib):
     """63 problems of 256 x 256 (the batch of a 64-frame sequence); the oracle
     checks a sample of problems one by one."""
@@ -114,7 +137,7 @@ def oracle_admm(p0, p1, prm, n):
     return st
 
 
-@pytest.mark.parametrize("precision", ["fp32", "split_bf16"])
+@pytest.mark.parametrize("precision", ["fp32", "split_bf16", "split_bf16_3"])
 @pytest.mark.parametrize("mode,balanced", [("prox", False), ("fixed_first", False), ("eval", False), ("prox", True)])
 @pytest.mark.parametrize("k", [1, 10, 60])
 def test_projection_form_trajectory(lib, mode, balanced, k, precision):
@@ -136,12 +159,15 @@ def test_projection_form_trajectory(lib, mode, balanced, k, precision):
     # projection mixes all blocks), so it is measured against ||z||, not the
     # norm of one (possibly still tiny) block
     z_norm = np.sqrt(sum(np.linalg.norm(v) ** 2 for v in z.values()))
-    tol = 1e-5 * max(1, k / 20) if precision == "fp32" else max(1e-5, k * split_bound(H, W, float(n_id)))
+    # the 3-piece split's per-solve error is that of the tensor cores' FP32
+    # accumulation, within split_bound / 8 (test_neumann_solve_split_bf16_3...)
+    per_solve = {"split_bf16": split_bound(H, W, float(n_id)), "split_bf16_3": split_bound(H, W, float(n_id)) / 8}
+    tol = max(1e-5, k * per_solve[precision]) if precision in per_solve else 1e-5 * max(1, k / 20)
     for name in ("Mx", "My", "x0", "x1", "r"):
         if name not in z:
             continue
         o = z[name]
-        den = np.linalg.norm(o) if precision == "fp32" else z_norm
+        den = z_norm if precision in per_solve else np.linalg.norm(o)
         e = np.linalg.norm(g[name] - o) / max(den, 1e-3 * scale)
         assert e <= tol, (name, e)
 
