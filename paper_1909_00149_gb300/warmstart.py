@@ -14,6 +14,7 @@ order (Mx, My, r, a).
 """
 from __future__ import annotations
 
+import os
 import time
 
 import numpy as np
@@ -93,3 +94,73 @@ def solve(p0, p1, net: UNet | None = None, gate: float = 0.0, **params) -> dict:
         torch.cuda.synchronize()
         r["seconds"] = time.perf_counter() - t0
     return r
+
+
+# ---------------------------------------------------------------- trained weights
+WEIGHTS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "weights", "unet_warmstart_256.npz")
+
+
+def save_params(net: UNet, path: str, **meta) -> None:
+    """The network's FP32 parameters (``ot_unet_get_params`` order) and the
+    training record, as a compressed .npz."""
+    os.makedirs(os.path.dirname(path), exist_ok=True)
+    np.savez_compressed(path, params=net.get_params(), base_channels=net.base,
+                        **{k: np.asarray(v) for k, v in meta.items()})
+
+
+def load_params(net: UNet, path: str = WEIGHTS) -> dict:
+    """Load parameters written by ``save_params`` into ``net``; returns the
+    training record."""
+    with np.load(path) as d:
+        if int(d["base_channels"]) != net.base:
+            raise ValueError(f"{path}: base_channels {int(d['base_channels'])} != {net.base}")
+        net.set_params(d["params"].astype(np.float32))
+        return {k: d[k].tolist() for k in d.files if k not in ("params", "base_channels")}
+
+
+def main(argv=None) -> None:
+    """Train the warm-start network and write its parameters:
+
+        python -m paper_1909_00149_gb300.warmstart --pairs 20000 --size 256 \\
+            --epochs 4 --out paper_1909_00149_gb300/weights/unet_warmstart_256.npz
+
+    The training pairs come from the seeded blob-video generator of
+    ``synth.warmstart_pairs`` (run from the repository root); their targets
+    are the states the plain solver reaches at the 1e-5 stopping rule
+    (mu = 3, rho = 0.01, the library's defaults)."""
+    import argparse
+    import sys
+    import torch
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--pairs", type=int, default=20000)
+    ap.add_argument("--size", type=int, default=256)
+    ap.add_argument("--epochs", type=int, default=4)
+    ap.add_argument("--batch", type=int, default=16)
+    ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--seed", type=int, default=1000)
+    ap.add_argument("--out", default=WEIGHTS)
+    a = ap.parse_args(argv)
+    sys.path.insert(0, os.getcwd())
+    from synth import rng_for, warmstart_pairs
+    kw = dict(mode="prox", mu=3.0, rho=0.01, tol=1e-5, max_iter=100000, check_every=10)
+    t0 = time.perf_counter()
+    p0, p1 = warmstart_pairs(rng_for(5, a.seed), a.pairs, a.size)
+    X, T, its = solve_targets(p0, p1, **kw)
+    torch.cuda.synchronize()
+    t_solve = time.perf_counter() - t0
+    del p0, p1
+    net = UNet(a.size, a.size, a.batch, 32)
+    net.init(seed=0)
+    t0 = time.perf_counter()
+    losses = train(net, X, T, epochs=a.epochs, batch=a.batch, lr=a.lr)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    save_params(net, a.out, pairs=a.pairs, size=a.size, epochs=a.epochs, batch=a.batch, lr=a.lr, seed=a.seed,
+                mu=kw["mu"], rho=kw["rho"], tol=kw["tol"], loss_per_epoch=np.array(losses),
+                solve_seconds=t_solve, train_seconds=t_train, target_iters=np.array(its))
+    print({"out": a.out, "loss_per_epoch": losses, "solve_s": round(t_solve, 1), "train_s": round(t_train, 1)},
+          flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -87,6 +87,20 @@ def blob_video(rng: np.random.Generator, T: int, H: int, W: int, n_blobs: int = 
     return out.astype(np.float32)
 
 
+def warmstart_pairs(rng: np.random.Generator, n: int, S: int):
+    """n consecutive-frame pairs [n, S, S] (p0, p1) cut from 17-frame S x S
+    blob videos with 3 to 8 blobs each (sigma 3 px, amplitude U[0.5, 1],
+    integer moves in [-4, 4]^2 a frame, one amplitude rescaled a frame):
+    the 64x64 pair's generator scaled up, for training the warm start."""
+    p0s, p1s = [], []
+    for k in range(0, n, 16):
+        v = blob_video(rng, 17, S, S, n_blobs=int(rng.integers(3, 9)))
+        m = min(16, n - k)
+        p0s.append(v[:m])
+        p1s.append(v[1:m + 1])
+    return np.concatenate(p0s), np.concatenate(p1s)
+
+
 def _smooth_pattern(rng: np.random.Generator, H: int, W: int, sigma: float) -> np.ndarray:
     from scipy.ndimage import gaussian_filter
     g = gaussian_filter(rng.uniform(0.0, 1.0, (H, W)), sigma=sigma, mode="wrap")

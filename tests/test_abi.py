@@ -136,3 +136,17 @@ def test_param_structs_match_their_ctypes_mirrors(cdll):
         p = cls.from_buffer_copy(bytes(buf[:n]))
         if cls is _abi.ot_rpca_params:
             assert p.signed_fg == 0 and p.use_graph == 1 and p.rho == 1.0 and p.kappa == 0.005
+
+
+def test_committed_warm_start_weights_fit_the_network(cdll):
+    """The warm-start parameters that the benchmark loads have the network's
+    layout (weights [co, ci, k, k] then biases [co] per layer) and a record
+    of the training run that wrote them."""
+    import numpy as np
+    from paper_1909_00149_gb300 import unet_layer_specs, warmstart as WS
+    with np.load(WS.WEIGHTS) as d:
+        n = sum(co * ci * k * k + co for _, ci, co, k in unet_layer_specs(int(d["base_channels"])))
+        assert d["params"].shape == (n,) and d["params"].dtype == np.float32
+        assert np.all(np.isfinite(d["params"]))
+        assert int(d["pairs"]) >= 20000 and int(d["size"]) == 256
+        assert float(d["mu"]) == 3.0 and float(d["rho"]) == 0.01 and float(d["tol"]) == 1e-5
