@@ -345,9 +345,74 @@ def run_ours_rpca(args, rank, world, local_rank):
         "gpu_launches": (OUTER_PER_CHECK + 5 + (1 + args.n_inner) * OUTER_PER_CHECK) * CHECKS_PER_STEP * args.steps,
         "clocks": clocks,
     }
+    if not args.no_time_to_tol and rank == 0:
+        line["time_to_tol"] = time_to_tol_block(local_rank)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_rpca(Y, args.n_inner, budget_s=args.cpu_seconds)
     return line
+
+
+def time_to_tol_block(local_rank: int, frames: int = 128, size: int = 512, reps: int = 3) -> dict:
+    """Time to the 1e-5 stopping rule on the learned warm start's evaluation
+    set (every frame pair of a 128-frame 512x512 blob video, mu = 3, rho =
+    0.01), plain FP32 Algorithm 1 from zero against the same solver started
+    from the committed network's prediction (its forward pass inside the
+    timed region), both to the same rule; the split-BF16 projection form
+    beside them.  Host time around each solve with inputs resident."""
+    import torch
+    import paper_1909_00149_gb300 as otp
+    from paper_1909_00149_gb300 import warmstart as WS
+    from synth import blob_video, rng_for
+    torch.cuda.set_device(local_rank)
+    kw = dict(mode="prox", mu=PROX_KW["mu"], rho=PROX_KW["rho"], tol=1e-5, max_iter=100000, check_every=10)
+    v = blob_video(rng_for(5, 5000), frames, size, size)
+    q0, q1 = v[:-1].copy(), v[1:].copy()
+    B = frames - 1
+    d0, d1 = torch.from_numpy(q0).cuda(), torch.from_numpy(q1).cuda()
+    out = {"workload": f"the {B} frame pairs of a {frames}-frame {size}x{size} blob video, mu = {kw['mu']}, "
+                       f"rho = {kw['rho']}, stopping rule 1e-5 checked every 10 iterations",
+           "timing": f"host time around prediction + solve, inputs resident, median of {reps}"}
+    net = None
+    if os.path.exists(WS.WEIGHTS):
+        net = otp.UNet(size, size, B, 32)
+        out["network"] = WS.load_params(net)
+        out["network"].pop("target_iters", None)
+    x = WS.pair_tensor(q0, q1)
+    pred = torch.empty((B, 4, size, size), dtype=torch.float32, device="cuda")
+
+    def solve(warm: bool, **extra):
+        p = dict(kw, **extra)
+        with otp.OtProx(B, size, size, **p) as s_:
+            s_.set_input(d0, d1)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            if warm:
+                net.forward(x, out=pred)
+                s_.warm_start(pred, 1e-3)
+            r = s_.solve()
+            torch.cuda.synchronize()
+            r["seconds"] = time.perf_counter() - t0
+        return r
+
+    def med(runs):
+        return {"iters": runs[0]["iters"], "status": runs[0]["status"],
+                "ms": 1e3 * statistics.median(r["seconds"] for r in runs),
+                "res_pri": runs[0]["res_pri"], "res_fp": runs[0]["res_fp"]}
+
+    solve(False)
+    out["plain_fp32_cold"] = med([solve(False) for _ in range(reps)])
+    if net is not None:
+        solve(True)
+        out["warm_start_fp32"] = med([solve(True) for _ in range(reps)])
+        out["speedup_warm_vs_plain"] = out["plain_fp32_cold"]["ms"] / out["warm_start_fp32"]["ms"]
+        net.close()
+    r = solve(False, algorithm="projection", precision="split_bf16", max_iter=300)
+    out["projection_split_bf16_cold"] = {"iters": r["iters"], "status": r["status"], "ms": 1e3 * r["seconds"],
+                                         "res_pri": r["res_pri"], "res_fp": r["res_fp"],
+                                         "note": "capped at 300 iterations; status -4 = not converged"}
+    out["chosen"] = ("warm start + FP32 Algorithm 1: Algorithm 1 has no contraction for the tensor cores, and the "
+                     "split-BF16 projection form does not reach the rule at these parameters")
+    return out
 
 
 def run_ours_prox(args, rank, world, local_rank):
@@ -688,22 +753,94 @@ def run_ours_batch(args, rank, world, local_rank):
     }
 
 
+def precision_inputs(rank: int, frames: int = 32, size: int = 1024, n_blobs: int = 32):
+    """The precision workload's video: 32 frames of 1024 x 1024 blobs as in
+    the 64x64 pair's generator, 32 blobs; its 31 consecutive pairs."""
+    from synth import blob_video, rng_for
+    v = blob_video(rng_for(4, rank), frames, size, size, n_blobs=n_blobs)
+    return np.ascontiguousarray(v[:-1]), np.ascontiguousarray(v[1:])
+
+
+def run_ours_precision(args, rank, world, local_rank):
+    """The precision forms on 31 pairs of 1024 x 1024 (a 32-frame blob video):
+    time to the 1e-5 stopping rule of plain FP32 Algorithm 1 and of the
+    projection form with its DCT-II solves in FP32 and in split BF16 (tensor
+    cores), at the library's default parameters and at a well-conditioned
+    pair (mu = 8, rho = 1), and the split-BF16 DCT solve's tensor throughput.
+    value = pixel-iterations/s of the Algorithm 1 solve."""
+    import torch
+    import paper_1909_00149_gb300 as otp
+    torch.cuda.set_device(local_rank)
+    p0, p1 = precision_inputs(rank)
+    B, H, W = p0.shape
+    d0, d1 = torch.from_numpy(p0).cuda(), torch.from_numpy(p1).cuda()
+
+    def solve(**kw):
+        with otp.OtProx(B, H, W, tol=1e-5, check_every=10, **kw) as s_:
+            s_.set_input(d0, d1)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            r = s_.solve()
+            torch.cuda.synchronize()
+            r["ms"] = 1e3 * (time.perf_counter() - t0)
+            r["ms_per_iter"] = r["ms"] / max(r["iters"], 1)
+        return {k: r[k] for k in ("iters", "status", "ms", "ms_per_iter", "res_pri", "res_fp", "rel_gap")}
+
+    sampler = ClockSampler(local_rank)
+    sampler.start()
+    forms = {}
+    for tag, prm in (("mu3_rho0.01", dict(mu=3.0, rho=0.01)), ("mu8_rho1", dict(mu=8.0, rho=1.0))):
+        solve(max_iter=100000, **prm)       # warm-up (tables, graphs)
+        forms[tag] = {
+            "alg1_fp32": solve(max_iter=100000, **prm),
+            "projection_fp32": solve(algorithm="projection", precision="fp32", max_iter=args.prec_max_iter, **prm),
+            "projection_split_bf16": solve(algorithm="projection", precision="split_bf16",
+                                           max_iter=args.prec_max_iter, **prm),
+            "projection_split_bf16_3": solve(algorithm="projection", precision="split_bf16_3",
+                                             max_iter=args.prec_max_iter, **prm)}
+    # the DCT-II solve alone: (D D* + 3 I)^{-1} X on the 31 pairs' planes
+    X = torch.from_numpy(p1).cuda()
+    otp.neumann_solve_timed(X, 3.0, "split_bf16", n_rep=2)
+    ms_bf = statistics.median(otp.neumann_solve_timed(X, 3.0, "split_bf16", n_rep=10) for _ in range(3))
+    ms_bf3 = statistics.median(otp.neumann_solve_timed(X, 3.0, "split_bf16_3", n_rep=10) for _ in range(3))
+    ms_32 = statistics.median(otp.neumann_solve_timed(X, 3.0, "fp32", n_rep=10) for _ in range(3))
+    clocks = sampler.stop()
+    gemm_flops = 4.0 * B * H * W * (H + W)          # the four transforms' real flops
+    tensor_flops = 3.0 * gemm_flops                 # three BF16 products per K step
+    peaks = measured_peaks()
+    achieved = tensor_flops / (ms_bf * 1e-3) / 1e12
+    a1 = forms["mu3_rho0.01"]["alg1_fp32"]
+    return {
+        "metric": METRIC, "value": B * H * W * a1["iters"] / (a1["ms"] * 1e-3), "unit": UNIT, "n_gpus": world,
+        "steps": 1, "warmup": 1, "ms_per_step": a1["ms"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32 (DCT GEMMs in split bf16 where stated)", "data": "synthetic",
+        "config": {"workload": f"precision_31_pairs_1024x1024: the {B} pairs of a 32-frame 1024x1024 blob video "
+                               f"(32 blobs); a step is one Algorithm 1 solve to 1e-5 at mu = 3, rho = 0.01",
+                   "B": B, "H": H, "W": W, "projection_max_iter": args.prec_max_iter,
+                   "l2": "inputs larger than L2 (%.1f GB of Algorithm 1 state)" % (11 * B * H * W * 4 / 1e9)},
+        "time_to_tol": forms,
+        "dct_solve": {"ms_split_bf16": ms_bf, "ms_split_bf16_3": ms_bf3, "ms_fp32": ms_32,
+                      "speedup_split_bf16": ms_32 / ms_bf, "speedup_split_bf16_3": ms_32 / ms_bf3,
+                      "gemm_flops_per_solve": gemm_flops, "tensor_flops_per_solve": tensor_flops,
+                      "tensor_tflops_split_bf16_3": 6.0 * gemm_flops / (ms_bf3 * 1e-3) / 1e12,
+                      "note": "one solve = the operand split and four batched GEMMs (M = B x H rows); "
+                              "3 products per K step (2 pieces) or 6 (3 pieces)"},
+        "roofline": {"bound": "tensor", "achieved": achieved, "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
+                     "frac": achieved / peaks["bf16_tflops"], "traffic": None,
+                     "kernel": "tc_gemm_kernel (split-BF16 DCT-II solve: split + 4 GEMMs, 3 products per K step)",
+                     "peak_source": peaks["source"] + " bf16 burst (of measured)"},
+        "gpu_launches": None, "e2e": None, "clocks": clocks,
+    }
+
+
 UNET_MACS_PER_PIXEL = 161984   # multiply-adds of the warm-start U-Net's forward pass per full-resolution pixel
 
 
 def warmstart_pairs(seed: int, n: int, S: int):
-    """n consecutive-frame pairs of 17-frame S x S blob videos (blobs of
-    sigma 3 px, amplitude U[0.5, 1], moves in [-4, 4]^2 per frame, 3-8 blobs
-    a video): the evaluation's distribution."""
-    from synth import blob_video, rng_for
-    rng = rng_for(5, seed)
-    p0s, p1s = [], []
-    for k in range(0, n, 16):
-        v = blob_video(rng, 17, S, S, n_blobs=int(rng.integers(3, 9)))
-        m = min(16, n - k)
-        p0s.append(v[:m])
-        p1s.append(v[1:m + 1])
-    return np.concatenate(p0s), np.concatenate(p1s)
+    """n consecutive-frame pairs of S x S blob videos with 3 to 8 blobs (the
+    warm start's training distribution, ``synth.warmstart_pairs``)."""
+    from synth import rng_for, warmstart_pairs as pairs
+    return pairs(rng_for(5, seed), n, S)
 
 
 def run_ours_warmstart(args, rank, world, local_rank):
@@ -810,7 +947,8 @@ def main():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["rpca", "prox", "batch", "warmstart"], default="rpca")
+    ap.add_argument("--workload", choices=["rpca", "prox", "batch", "warmstart", "precision"], default="rpca")
+    ap.add_argument("--prec-max-iter", type=int, default=400, help="iteration cap of the projection forms")
     ap.add_argument("--ws-train-size", type=int, default=128)
     ap.add_argument("--ws-train-pairs", type=int, default=4096)
     ap.add_argument("--ws-epochs", type=int, default=8)
@@ -822,6 +960,7 @@ def main():
     ap.add_argument("--n-inner", type=int, default=1)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-time-to-tol", action="store_true", help="skip the time-to-tolerance block")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank = int(os.environ.get("RANK", "0"))
@@ -835,7 +974,7 @@ def main():
             torch.cuda.set_device(local_rank)
             torch.distributed.init_process_group("nccl")
         run = {"rpca": run_ours_rpca, "prox": run_ours_prox, "batch": run_ours_batch,
-               "warmstart": run_ours_warmstart}[args.workload]
+               "warmstart": run_ours_warmstart, "precision": run_ours_precision}[args.workload]
         line = run(args, rank, world, local_rank)
         if world > 1:
             import torch
