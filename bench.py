@@ -833,6 +833,43 @@ def run_ours_precision(args, rank, world, local_rank):
     }
 
 
+def run_ours_dct(args, rank, world, local_rank):
+    """The DCT-II Neumann solve alone, (D D* + 3 I)^{-1} X on B planes of
+    1024 x 1024 (the precision workload's frames), in FP32 and in 2- and
+    3-piece split BF16 on the tensor cores; a step is one solve.
+    value = solved pixels per second of the 3-piece split."""
+    import torch
+    import paper_1909_00149_gb300 as otp
+    torch.cuda.set_device(local_rank)
+    p0, _ = precision_inputs(rank)
+    X = torch.from_numpy(np.ascontiguousarray(p0[:args.dct_batch])).cuda()
+    B, H, W = X.shape
+    for prec in ("fp32", "split_bf16", "split_bf16_3"):
+        otp.neumann_solve_timed(X, 3.0, prec, n_rep=max(1, args.warmup))
+    sampler = ClockSampler(local_rank)
+    sampler.start()
+    ms = {prec: otp.neumann_solve_timed(X, 3.0, prec, n_rep=args.steps)
+          for prec in ("fp32", "split_bf16", "split_bf16_3")}
+    clocks = sampler.stop()
+    gemm_flops = 4.0 * B * H * W * (H + W)
+    peaks = measured_peaks()
+    achieved = 6.0 * gemm_flops / (ms["split_bf16_3"] * 1e-3) / 1e12
+    return {
+        "metric": "DCT-II Neumann solves, pixels/s", "value": B * H * W / (ms["split_bf16_3"] * 1e-3),
+        "unit": "pixel/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms["split_bf16_3"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16 pieces, fp32 accumulation", "data": "synthetic",
+        "config": {"workload": f"dct_{B}x{H}x{W}: (D D* + 3 I)^-1 X by the orthonormal DCT-II, four batched GEMMs",
+                   "B": B, "H": H, "W": W},
+        "ms_per_solve": ms, "gemm_flops_per_solve": gemm_flops,
+        "roofline": {"bound": "tensor", "achieved": achieved, "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
+                     "frac": achieved / peaks["bf16_tflops"], "traffic": None,
+                     "kernel": "tc_gemm_kernel (3-piece split-BF16 DCT-II solve: split + 4 GEMMs, 6 products)",
+                     "peak_source": peaks["source"] + " bf16 burst (of measured)"},
+        "gpu_launches": 5 * args.steps, "e2e": None, "clocks": clocks,
+    }
+
+
 UNET_MACS_PER_PIXEL = 161984   # multiply-adds of the warm-start U-Net's forward pass per full-resolution pixel
 
 
@@ -947,7 +984,8 @@ def main():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["rpca", "prox", "batch", "warmstart", "precision"], default="rpca")
+    ap.add_argument("--workload", choices=["rpca", "prox", "batch", "warmstart", "precision", "dct"], default="rpca")
+    ap.add_argument("--dct-batch", type=int, default=31, help="planes of the dct workload")
     ap.add_argument("--prec-max-iter", type=int, default=400, help="iteration cap of the projection forms")
     ap.add_argument("--ws-train-size", type=int, default=128)
     ap.add_argument("--ws-train-pairs", type=int, default=4096)
@@ -974,7 +1012,8 @@ def main():
             torch.cuda.set_device(local_rank)
             torch.distributed.init_process_group("nccl")
         run = {"rpca": run_ours_rpca, "prox": run_ours_prox, "batch": run_ours_batch,
-               "warmstart": run_ours_warmstart, "precision": run_ours_precision}[args.workload]
+               "warmstart": run_ours_warmstart, "precision": run_ours_precision,
+               "dct": run_ours_dct}[args.workload]
         line = run(args, rank, world, local_rank)
         if world > 1:
             import torch
