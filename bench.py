@@ -212,8 +212,12 @@ def rpca_phase_bytes(T: int, N: int, n_inner: int) -> list:
             4.0 * N * 2 * T,                  # apply: reads L+D, writes the new Tm
             56.0 * N * P * n_inner,           # Algorithm 1: 56 B per pixel-iteration
             4.0 * N * (9 * T + 8 * P),        # post: reads X S L Tm Tm_old A D z z' b w w' c, writes A D b c
-            4.0 * N * (13 * T + 10 * P) + 2 * gparts + 8.0 * TP * TP,   # apply + post + pre + the Gram
-                                                                      # (reads LD instead of the SVT output)
+            # apply + post + pre + the Gram, as profiled: the pass before the
+            # last iteration of a call, which also stores the SVT output and
+            # z, w for the last iteration's residuals (reads X S L Y A D LD z
+            # b w c, writes A D S L X LD Tn b p0 z' c p1 w'); the other passes
+            # of an interval write neither (13 T + 8 P planes)
+            4.0 * N * (14 * T + 10 * P) + 2 * gparts + 8.0 * TP * TP,
             0.0]                              # no separate Gram reduction
 
 
@@ -328,7 +332,9 @@ def run_ours_rpca(args, rank, world, local_rank):
                    "prox_kernel": "tma",
                    "l2": "inputs larger than L2 (state %.0f MB; %.0f MB moved per outer iteration)" %
                          ((12 * T + 15 * P) * H * W * 4 / 1e6,
-                          sum(b * c for b, c in zip(pbytes, PHASE_COUNT)) / OUTER_PER_STEP / 1e6)},
+                          (sum(b * c for b, c in zip(pbytes, PHASE_COUNT))
+                           - 4.0 * H * W * (T + 2 * P) * (OUTER_PER_CHECK - 2) * CHECKS_PER_STEP)
+                          / OUTER_PER_STEP / 1e6)},
         "roofline": roof,
         "phases": phases,
         "last_residuals": {"res_pri": res["res_pri"], "res_dual": res["res_dual"], "svt_rounds": res["svt_rounds"],

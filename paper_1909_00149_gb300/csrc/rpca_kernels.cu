@@ -249,10 +249,12 @@ rpca_post_pre_kernel(const RpcaGeom g, const RpcaCoeffs c, const RpcaPlanes P, d
 //     rpca_post_pre_kernel on chunk j with T^k from the shared tile and
 //     leave its LD^{k+1} values in another shared tile (LD is updated in
 //     place: a chunk's LD^k is copied before its LD^{k+1} is stored).
-// Double-buffered tiles, handed over through named barriers (hardware
-// barriers; every warp of the CTA runs the same number of chunks).  With
+// Double-buffered tiles, handed over through mbarriers (every producing
+// thread arrives, every consuming thread waits for the phase of the tile's
+// use; every thread of a role runs the same number of chunks).  With
 // store_tn the updating warps also store T^k (needed only before the last
-// outer iteration of a call, whose lines 12-15 form ||T^{k+1} - T^k||).
+// outer iteration of a call, whose lines 12-15 form ||T^{k+1} - T^k||),
+// and the z, w it read (that iteration's dual residual ||z^{k+1} - z^k||).
 // Every CTA writes its partial Gram to gpart[blockIdx.x]; the CTAs then meet
 // at a grid barrier (all resident: the launch is cooperative) and each sums
 // its slice of the TP x TP entries over the partials, in partial order and
@@ -265,7 +267,11 @@ constexpr int kFGGram = 128;                     // contraction threads (4 warps
 constexpr int kFGThreads = kFGUpd + kFGGram;     // one CTA per SM: 152 partial Grams
 // named barriers (0 is __syncthreads): tile b of T^k full / free, tile b of
 // LD^{k+1} full / free, and one among the contraction warps alone
-constexpr int kBarTnFull = 1, kBarTnFree = 3, kBarLdFull = 5, kBarLdFree = 7, kBarMma = 9;
+constexpr int kBarMma = 9;   // named barrier among the contraction warps alone
+// mbarriers of the tile hand-over, two tiles each: T^k full (arrivals: the
+// kFGGram contraction threads), T^k free and LD^{k+1} full (the kFGUpd
+// updating threads), LD^{k+1} free (the contraction threads)
+enum { kMbTnFull = 0, kMbTnFree = 2, kMbLdFull = 4, kMbLdFree = 6, kMbCount = 8 };
 
 template <int TP>
 constexpr size_t between_smem() {   // Wm^T, 2 x LD^k chunk, 2 x T^k chunk, 2 x LD^{k+1} chunk
@@ -285,8 +291,32 @@ __device__ __forceinline__ int ld_col(int p, int t) {
 __device__ __forceinline__ void named_sync(int id, int n) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
 }
-__device__ __forceinline__ void named_arrive(int id, int n) {
-  asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(n) : "memory");
+
+// Tile hand-over between the warp roles by mbarriers: a producing thread
+// arrives (release) once its part of a tile is written or read, a consuming
+// thread waits (acquire) for the phase of the tile's use.  Unlike a named
+// barrier, a waiting warp is held only by the producers, not by the other
+// consumers.  Waits are bounded; on expiry the error flag is set and the
+// thread goes on (the host reports OT_ETIMEOUT).
+__device__ __forceinline__ void mb_init(uint64_t* b, unsigned n) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"((unsigned)__cvta_generic_to_shared(b)), "r"(n)
+               : "memory");
+}
+__device__ __forceinline__ void mb_arrive(uint64_t* b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"((unsigned)__cvta_generic_to_shared(b)) : "memory");
+}
+__device__ __forceinline__ void mb_wait(uint64_t* b, unsigned parity, int* err) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(b);
+  for (unsigned it = 0; it < (1u << 22); ++it) {
+    unsigned done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return;
+  }
+  atomicExch(err, 1);
 }
 
 constexpr unsigned kBarSpin = 1u << 20;         // polls (about 1 s) before the grid barrier gives up
@@ -412,10 +442,20 @@ rpca_apply_post_pre_gram_kernel(const RpcaGeom g, const RpcaCoeffs c, const Rpca
   float* sIn = sW + TP * LDS;            // [2][TP][LDP]: LD^k of a chunk, frame rows
   float* sTn = sIn + 2 * TP * LDP;       // [2][TP][LDP]: T^k of a chunk, frame rows
   float* sLD = sTn + 2 * TP * LDP;       // [2][kGC][TP]: LD^{k+1} of a chunk, pixel rows (ld_col)
+  __shared__ __align__(8) uint64_t mb[kMbCount];
   float acc[kNumSums] = {};
   const int tid = threadIdx.x;
   const int nsm = (int)(between_smem<TP>() / sizeof(float));
   for (int e = tid; e < nsm; e += kFGThreads) smf[e] = 0.f;   // frames T..TP-1 stay zero
+  if (tid == 0) {
+    for (int q = 0; q < 2; ++q) {
+      mb_init(&mb[kMbTnFull + q], kFGGram);
+      mb_init(&mb[kMbTnFree + q], kFGUpd);
+      mb_init(&mb[kMbLdFull + q], kFGUpd);
+      mb_init(&mb[kMbLdFree + q], kFGGram);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
   __syncthreads();
   const long long nch = (g.plane + kGC - 1) / kGC;
   const int nk = blockIdx.x < nch ? (int)((nch - 1 - blockIdx.x) / gridDim.x + 1) : 0;   // chunks of this CTA
@@ -427,8 +467,8 @@ rpca_apply_post_pre_gram_kernel(const RpcaGeom g, const RpcaCoeffs c, const Rpca
     const int items = g.T * (kGC / 4);
     for (int k = 0; k < nk; ++k) {
       const int b = k & 1;
-      named_sync(kBarTnFull + b, kFGThreads);
-      if (k >= 2) named_sync(kBarLdFree + b, kFGThreads);
+      mb_wait(&mb[kMbTnFull + b], (k >> 1) & 1, err);
+      if (k >= 2) mb_wait(&mb[kMbLdFree + b], ((k >> 1) - 1) & 1, err);
       const long long p0 = (blockIdx.x + (long long)k * gridDim.x) * kGC;
       const float* tnb = sTn + b * TP * LDP;
       float* ldb = sLD + b * kGC * TP;
@@ -477,19 +517,22 @@ rpca_apply_post_pre_gram_kernel(const RpcaGeom g, const RpcaCoeffs c, const Rpca
         stg4v(P.L + o, l4);
         stg4v(P.X + o, x4);
         stg4v(P.LD + o, ld4);
+        // z^k and w^k enter only the dual residual of the next outer
+        // iteration's lines 12-15, which run in a pass of their own after
+        // the last iteration of a call: the pass before it (store_tn) keeps them
         if (hz) {
           stg4v(P.Bz + oz, bz);
           stg4v(P.p0 + oz, p04);
-          stg4v(P.zprev + oz, z);
+          if (store_tn) stg4v(P.zprev + oz, z);
         }
         if (hw) {
           stg4v(P.Cw + ow, cc);
           stg4v(P.p1 + ow, p14);
-          stg4v(P.wprev + ow, w);
+          if (store_tn) stg4v(P.wprev + ow, w);
         }
       }
-      if (k + 2 < nk) named_arrive(kBarTnFree + b, kFGThreads);
-      named_arrive(kBarLdFull + b, kFGThreads);
+      mb_arrive(&mb[kMbTnFree + b]);
+      mb_arrive(&mb[kMbLdFull + b]);
     }
   } else {
     const int gt = tid - kFGUpd, bi = gt / 8, bj = gt % 8;
@@ -516,7 +559,7 @@ rpca_apply_post_pre_gram_kernel(const RpcaGeom g, const RpcaCoeffs c, const Rpca
     // Gram of chunk j from LD^{k+1} tile j & 1
     auto gram_chunk = [&](int j) {
       const int b = j & 1;
-      named_sync(kBarLdFull + b, kFGThreads);
+      mb_wait(&mb[kMbLdFull + b], (j >> 1) & 1, err);
       const float* ldb = sLD + b * kGC * TP;
 #pragma unroll 4
       for (int p = 0; p < kGC; ++p) {
@@ -539,7 +582,7 @@ rpca_apply_post_pre_gram_kernel(const RpcaGeom g, const RpcaCoeffs c, const Rpca
 #pragma unroll
           for (int q = 0; q < CB; ++q) gacc[r][q] = fmaf(av[r], bv[q], gacc[r][q]);
       }
-      if (j + 2 < nk) named_arrive(kBarLdFree + b, kFGThreads);
+      mb_arrive(&mb[kMbLdFree + b]);
     };
     prefetch(0);
     prefetch(1);
@@ -547,7 +590,7 @@ rpca_apply_post_pre_gram_kernel(const RpcaGeom g, const RpcaCoeffs c, const Rpca
       const int b = k & 1;
       cp_async_wait<1>();                      // this thread's copies of chunk k are in
       named_sync(kBarMma, kFGGram);            // ... and every contraction thread's
-      if (k >= 2) named_sync(kBarTnFree + b, kFGThreads);
+      if (k >= 2) mb_wait(&mb[kMbTnFree + b], ((k >> 1) - 1) & 1, err);
       // T^k of chunk k, pixels 4 bi .. 4 bi + 3: AT rows t in runs of AH,
       // the run starting at h = 0, AH, ... covering t = 8 h + AH bj .. + AH - 1
       // (the 8 threads of a pixel group read consecutive Wm runs), one run at
@@ -577,7 +620,7 @@ rpca_apply_post_pre_gram_kernel(const RpcaGeom g, const RpcaCoeffs c, const Rpca
           *reinterpret_cast<float4*>(tnb + (8 * h + AH * bj + r) * LDP + 4 * bi) =
               make_float4(o[r][0], o[r][1], o[r][2], o[r][3]);
       }
-      named_arrive(kBarTnFull + b, kFGThreads);
+      mb_arrive(&mb[kMbTnFull + b]);
       named_sync(kBarMma, kFGGram);            // every contraction thread is done with tile b of LD^k
       prefetch(k + 2);
       if (k >= 1) gram_chunk(k - 1);
