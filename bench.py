@@ -66,6 +66,7 @@ PHASE_COUNT_PER_CHECK = [1, 1, OUTER_PER_CHECK, 1, OUTER_PER_CHECK, 1, OUTER_PER
 PHASE_COUNT = [c * CHECKS_PER_STEP for c in PHASE_COUNT_PER_CHECK]   # per step
 PROFILE_FILES = {  # kernel -> (ncu summary holding its DRAM traffic per launch, its source file)
     "prox_tma_kernel": ("prox_tma_63x256x256.md", "prox_tma.cu"),
+    "prox_temporal_kernel": ("prox_temporal_63x256x256.md", "prox_temporal.cu"),
     "rpca_pre_kernel": ("rpca_step_64x256x256.md", "rpca_kernels.cu"),
     "rpca_post_kernel": ("rpca_step_64x256x256.md", "rpca_kernels.cu"),
     "rpca_apply_post_pre_gram_kernel": ("rpca_step_64x256x256.md", "rpca_kernels.cu"),
@@ -436,8 +437,10 @@ def run_ours_prox(args, rank, world, local_rank):
     def barrier():
         dist_barrier(world)
 
+    kw = dict(PROX_KW, kernel=args.prox_kernel, tb_depth=args.tb_depth)
+    temporal = args.prox_kernel == "temporal"
     with torch.cuda.stream(stream):
-        s = otp.OtProx(B, H, W, stream=stream, **PROX_KW)
+        s = otp.OtProx(B, H, W, stream=stream, **kw)
         s.set_input(torch.from_numpy(p0).cuda(), torch.from_numpy(p1).cuda())
         torch.cuda.synchronize()
         for _ in range(args.warmup):
@@ -455,8 +458,10 @@ def run_ours_prox(args, rank, world, local_rank):
         barrier()
         clocks = sampler.stop()
         ms = ev0.elapsed_time(ev1)
-        k_ms = statistics.median(s.step_timed(PROX_ITERS_PER_STEP) / PROX_ITERS_PER_STEP
-                                 for _ in range(max(args.steps, 3)))
+        # kernel time of one launch: an iteration, or a pass of tb_depth iterations
+        per_launch = args.tb_depth if temporal else 1
+        k_iters = TB_ITERS if temporal else PROX_ITERS_PER_STEP
+        k_ms = statistics.median(s.step_timed(k_iters) / k_iters * per_launch for _ in range(max(args.steps, 3)))
         h0 = torch.from_numpy(p0).pin_memory()
         h1 = torch.from_numpy(p1).pin_memory()
         for _ in range(max(1, args.warmup // 2)):
@@ -474,34 +479,87 @@ def run_ours_prox(args, rank, world, local_rank):
         barrier()
         e2e_ms = e0.elapsed_time(e1)
         s.close()
+        tb = None if temporal else temporal_block(p0, p1, stream, args.steps, args.warmup)
     ms, e2e_ms, k_ms = max_over_ranks([ms, e2e_ms, k_ms], world)
     if rank != 0:
         return None
     units = px * PROX_ITERS_PER_STEP * args.steps * world
     peaks = measured_peaks()
-    alg_bytes = 56 * px
+    alg_bytes = 56 * px              # one launch reads and writes the state once
     achieved = alg_bytes / (k_ms / 1e3) / 1e9
+    kname = "prox_temporal_kernel" if temporal else "prox_tma_kernel"
+    n_launch = -(-PROX_ITERS_PER_STEP // args.tb_depth) if temporal else PROX_ITERS_PER_STEP
     line = {
         "metric": METRIC, "value": units / (ms / 1e3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": "prox_63_pairs_256x256: Algorithm 1 check interval on the 63 pairs of a 64-frame "
                                "256x256 blob video", "B": B, "H": H, "W": W, "iters_per_step": PROX_ITERS_PER_STEP,
-                   "mu": PROX_KW["mu"], "rho": PROX_KW["rho"], "kernel": PROX_KW["kernel"], "cuda_graph": True,
+                   "mu": PROX_KW["mu"], "rho": PROX_KW["rho"], "kernel": args.prox_kernel, "cuda_graph": True,
+                   **({"tb_depth": args.tb_depth} if temporal else {}),
                    "l2": "inputs larger than L2 (state %.0f MB; 231 MB moved per iteration)" % (11 * px * 4 / 1e6)},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                     "frac": achieved / peaks["hbm_gbs"], "traffic": ncu_traffic("prox_tma_kernel", "nored"),
-                     "kernel": "prox_tma_kernel (Algorithm 1 iteration, no reduction)",
+                     "frac": achieved / peaks["hbm_gbs"], "traffic": ncu_traffic(kname, "nored"),
+                     "kernel": (f"prox_temporal_kernel (a pass of {args.tb_depth} Algorithm 1 iterations, "
+                                "no reduction)") if temporal else "prox_tma_kernel (Algorithm 1 iteration, no reduction)",
                      "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_ms": k_ms,
                      "peak_source": peaks["source"] + " copy bandwidth (of measured)"},
         "e2e": {"value": units / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": 2 * px * 4,
                 "d2h_bytes_per_step": 8 * 8},
-        "gpu_launches": (PROX_ITERS_PER_STEP + 1) * args.steps,
+        "gpu_launches": (n_launch + 1) * args.steps,
         "clocks": clocks,
     }
+    if tb is not None:
+        for d in tb["depths"]:
+            d["vs_one_pass"] = k_ms / d["ms_per_iter"]
+        line["temporal_blocking"] = tb
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_prox(p0, p1, args.cpu_seconds)
     return line
+
+
+TB_ITERS = 12     # divisible by 2, 3 and 4: passes of equal length at every depth
+
+
+def temporal_block(p0, p1, stream, steps: int, warmup: int) -> dict:
+    """Algorithm 1 with temporal blocking on the same 63 pairs: per depth, the
+    kernel time of TB_ITERS iterations (TB_ITERS / depth passes; CUDA events
+    around the launches, median of the runs) and the check interval of
+    PROX_ITERS_PER_STEP iterations as the main line times it.  Reported
+    beside the one-pass roofline: a pass reads and writes the state once, so
+    the HBM floor falls to 56 / depth bytes per pixel-iteration; the pass's
+    own HBM rate shows how far the stage-iterate-write pipeline is from it."""
+    import torch
+    import paper_1909_00149_gb300 as otp
+    B, H, W = p0.shape
+    px = B * H * W
+    peaks = measured_peaks()
+    out = []
+    for depth in (2, 3, 4):
+        kw = dict(PROX_KW, kernel="temporal", tb_depth=depth)
+        with otp.OtProx(B, H, W, stream=stream, **kw) as s:
+            s.set_input(torch.from_numpy(p0).cuda(), torch.from_numpy(p1).cuda())
+            for _ in range(warmup):
+                s.check_interval(PROX_ITERS_PER_STEP)
+            torch.cuda.synchronize()
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            for _ in range(steps):
+                s.check_interval(PROX_ITERS_PER_STEP)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            step_ms = ev0.elapsed_time(ev1) / steps
+            it_ms = statistics.median(s.step_timed(TB_ITERS) / TB_ITERS for _ in range(max(steps, 3)))
+        pass_ms = it_ms * depth
+        out.append({"depth": depth, "ms_per_iter": it_ms, "px_iter_per_s": px / (it_ms / 1e3),
+                    "check_interval_ms": step_ms,
+                    "check_interval_px_iter_per_s": px * PROX_ITERS_PER_STEP / (step_ms / 1e3),
+                    "hbm_floor_bytes_per_px_iter": 56.0 / depth,
+                    "pass_hbm_gbs": 56.0 * px / (pass_ms / 1e3) / 1e9,
+                    "pass_hbm_frac": 56.0 * px / (pass_ms / 1e3) / 1e9 / peaks["hbm_gbs"]})
+    return {"kernel": "prox_temporal_kernel (depth iterations per pass; bit-identical to the one-pass kernels)",
+            "tile": "136 x 45 staged (128 x 37 own at depth 3-4, 128 x 41 at depth 2), 512 threads, one CTA per SM",
+            "iters_timed": TB_ITERS, "depths": out}
 
 
 # --------------------------------------------------------------------- oracle timing
@@ -1005,6 +1063,9 @@ def main():
     ap.add_argument("--ws-gate", type=float, default=1e-3, help="warm-start mass gate (0: none)")
     ap.add_argument("--ws-gate-sweep", default="", help="comma-separated gates to report as well")
     ap.add_argument("--n-inner", type=int, default=1)
+    ap.add_argument("--prox-kernel", choices=["tma", "temporal"], default="tma",
+                    help="iteration kernel of the prox workload")
+    ap.add_argument("--tb-depth", type=int, default=4, help="iterations per pass of the temporal kernel")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-time-to-tol", action="store_true", help="skip the time-to-tolerance block")

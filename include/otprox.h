@@ -68,11 +68,18 @@ extern "C" {
  * state fits in one CTA's shared memory, TMA otherwise.
  *  TILED    -- one CTA per 16 x 128 tile, loads through the L1 path;
  *  RESIDENT -- one CTA per problem, all iterations of a call in shared memory;
- *  TMA      -- persistent CTAs (one per SM) fed by a multi-stage TMA pipeline. */
+ *  TMA      -- persistent CTAs (one per SM) fed by a multi-stage TMA pipeline;
+ *  TEMPORAL -- temporal blocking: tb_depth iterations per pass over the state
+ *              (a CTA stages its tile with a halo of tb_depth rounded up to 2
+ *              or 4 rows and 4 columns, iterates on it, writes the tile once);
+ *              bit-identical to TILED.  Standalone Algorithm 1 only (not the
+ *              projection form, the batch, or the inner prox of ot_rpca_* and
+ *              ot_uotdf_*); it allocates three more state planes. */
 #define OT_KERNEL_AUTO     0
 #define OT_KERNEL_TILED    1
 #define OT_KERNEL_RESIDENT 2
 #define OT_KERNEL_TMA      3
+#define OT_KERNEL_TEMPORAL 4
 /* Solver of eq. (Prox_UOT):
  *  ALG1       -- Algorithm 1, the paper's primal-dual iteration (Sec. III-B);
  *  PROJECTION -- ADMM with an exact projection onto {K z = k0} through the
@@ -118,6 +125,9 @@ typedef struct {
   int32_t algorithm;      /* OT_ALG_*                                            */
   int32_t precision;      /* OT_PREC_* of the DCT solves (projection form)       */
   double  beta;           /* ADMM penalty of the projection form (> 0)           */
+  int32_t tb_depth;       /* OT_KERNEL_TEMPORAL: iterations per pass, 2..4 (the
+                             default 4); a call's n iterations run as
+                             ceil(n / tb_depth) passes of near-equal length      */
 } ot_prox_params;
 
 typedef struct {

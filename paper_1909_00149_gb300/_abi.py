@@ -19,7 +19,7 @@ STATUS_NAMES = {0: "OT_OK", -1: "OT_EINVAL", -2: "OT_ENOMEM", -3: "OT_ECUDA", -4
 
 MODES = {"prox": 0, "fixed_first": 1, "eval": 2}
 NORMS = {"iso": 0, "aniso": 1}
-KERNELS = {"auto": 0, "tiled": 1, "resident": 2, "tma": 3}
+KERNELS = {"auto": 0, "tiled": 1, "resident": 2, "tma": 3, "temporal": 4}
 PRECISIONS = {"fp32": 0, "split_bf16": 1, "split_bf16_3": 2}
 ALGORITHMS = {"alg1": 0, "projection": 1}
 
@@ -35,7 +35,8 @@ class ot_prox_params(ctypes.Structure):
                 ("tau1", ctypes.c_double), ("tau2", ctypes.c_double), ("tol", ctypes.c_double),
                 ("max_iter", ctypes.c_int32), ("check_every", ctypes.c_int32),
                 ("kernel", ctypes.c_int32), ("use_graph", ctypes.c_int32),
-                ("algorithm", ctypes.c_int32), ("precision", ctypes.c_int32), ("beta", ctypes.c_double)]
+                ("algorithm", ctypes.c_int32), ("precision", ctypes.c_int32), ("beta", ctypes.c_double),
+                ("tb_depth", ctypes.c_int32)]
 
 
 class ot_prox_result(ctypes.Structure):

@@ -76,6 +76,7 @@ void ot_prox_default_params(ot_prox_params* p) {
   p->algorithm = OT_ALG_ALG1;
   p->precision = OT_PREC_FP32;
   p->beta = 1.0;
+  p->tb_depth = 4;
 }
 
 double ot_lambda_max(int32_t H, int32_t W) {
@@ -131,8 +132,47 @@ static cudaError_t enqueue_admm(ot_prox* h, int n, bool reduce) {
   return e;
 }
 
+static TbPtrs tb_ptrs(ot_prox* h, int parity) {
+  TbPtrs s;
+  const int o = parity ^ 1;
+  s.Mx_in = h->Mx[parity];
+  s.My_in = h->My[parity];
+  s.a_in = h->a[parity];
+  s.x0_in = h->x0s[parity];
+  s.x1_in = h->x1s[parity];
+  s.r_in = h->rs[parity];
+  s.Mx_out = h->Mx[o];
+  s.My_out = h->My[o];
+  s.a_out = h->a[o];
+  s.x0_out = h->x0s[o];
+  s.x1_out = h->x1s[o];
+  s.r_out = h->rs[o];
+  s.p0 = h->p0;
+  s.p1 = h->p1;
+  return s;
+}
+
+// Temporal blocking: n iterations as ceil(n / depth) passes of near-equal
+// length (each <= depth), one ping-pong flip per pass.
+static int tb_passes(const ot_prox* h, int n) { return (n + h->tb_depth - 1) / h->tb_depth; }
+
+static cudaError_t enqueue_temporal(ot_prox* h, int parity, int n, bool reduce) {
+  const int np = tb_passes(h, n);
+  cudaError_t e = cudaSuccess;
+  for (int k = 0; k < np && e == cudaSuccess; ++k) {
+    const int sub = n / np + (k < n % np ? 1 : 0);
+    e = launch_prox_temporal(h->prm.mode, h->prm.balanced != 0, reduce && k == np - 1, h->tb_depth, sub, h->G, h->C,
+                             tb_ptrs(h, parity), h->partials, h->stream);
+    parity ^= 1;
+  }
+  if (e == cudaSuccess && reduce && n > 0)
+    e = launch_finalize_sums(h->partials, temporal_num_ctas(h->G, h->tb_depth), h->dsums, h->stream);
+  return e;
+}
+
 static cudaError_t enqueue_iterations(ot_prox* h, int parity, int n, bool reduce) {
   if (h->admm) return enqueue_admm(h, n, reduce);
+  if (h->tb) return n > 0 ? enqueue_temporal(h, parity, n, reduce) : cudaSuccess;
   const int mode = h->prm.mode;
   const bool bal = h->prm.balanced != 0;
   cudaError_t e = cudaSuccess;
@@ -159,7 +199,18 @@ static cudaError_t enqueue_iterations(ot_prox* h, int parity, int n, bool reduce
 }
 
 static int parity_after(const ot_prox* h, int parity, int n) {
+  if (h->tb) return parity ^ (tb_passes(h, n) & 1);
   return (h->resident || h->admm) ? parity : (parity ^ (n & 1));
+}
+
+// The current ping-pong parity; with temporal blocking x0, x1, r follow it.
+static void set_cur(ot_prox* h, int c) {
+  h->cur = c;
+  if (h->tb) {
+    h->x0 = h->x0s[c];
+    h->x1 = h->x1s[c];
+    h->r = h->rs[c];
+  }
 }
 
 // One check interval: n iterations, reduction, copy of the sums to the host.
@@ -194,7 +245,7 @@ static int run_check_interval(ot_prox* h, int n) {
             "copying check sums");
     OT_CUDA(cudaMemcpyAsync(h->herr, h->derr, sizeof(int), cudaMemcpyDeviceToHost, h->stream), "copying the error flag");
   }
-  h->cur = parity_after(h, parity, n);
+  set_cur(h, parity_after(h, parity, n));
   OT_CUDA(cudaStreamSynchronize(h->stream), "synchronising after a check interval");
   if (*h->herr) return fail(OT_ETIMEOUT, "a bounded device wait expired in the iteration kernel");
   return OT_OK;
@@ -289,7 +340,11 @@ int ot_prox_create(const ot_prox_params* params, void* cuda_stream, ot_prox_t* o
   if (!(p.tol >= 0) || !isfinite(p.tol)) return fail(OT_EINVAL, "ot_prox_create: tol must be >= 0");
   if (p.max_iter < 0) return fail(OT_EINVAL, "ot_prox_create: max_iter must be >= 0");
   if (p.check_every < 1) return fail(OT_EINVAL, "ot_prox_create: check_every must be >= 1");
-  if (p.kernel < 0 || p.kernel > 3) return fail(OT_EINVAL, "ot_prox_create: unknown kernel %d", p.kernel);
+  if (p.kernel < 0 || p.kernel > 4) return fail(OT_EINVAL, "ot_prox_create: unknown kernel %d", p.kernel);
+  if (p.kernel == OT_KERNEL_TEMPORAL && p.algorithm != OT_ALG_ALG1)
+    return fail(OT_EINVAL, "ot_prox_create: OT_KERNEL_TEMPORAL runs Algorithm 1 only");
+  if (p.kernel == OT_KERNEL_TEMPORAL && (p.tb_depth < 2 || p.tb_depth > 4))
+    return fail(OT_EINVAL, "ot_prox_create: tb_depth must be in [2, 4] (got %d)", p.tb_depth);
   if (p.algorithm != OT_ALG_ALG1 && p.algorithm != OT_ALG_PROJECTION)
     return fail(OT_EINVAL, "ot_prox_create: unknown algorithm %d", p.algorithm);
   if (p.precision != OT_PREC_FP32 && p.precision != OT_PREC_SPLIT_BF16 && p.precision != OT_PREC_SPLIT_BF16_3)
@@ -318,7 +373,8 @@ int ot_prox_create(const ot_prox_params* params, void* cuda_stream, ot_prox_t* o
   const double ctas = (double)G.B * G.tiles_x * G.tiles_y;
   if (ctas > 2.0e9) return fail(OT_EINVAL, "ot_prox_create: problem too large for one launch (%g tiles)", ctas);
   const size_t plane_elems = (size_t)G.B * (size_t)G.plane;
-  const size_t nplanes = 11;
+  const bool tb = p.kernel == OT_KERNEL_TEMPORAL;
+  const size_t nplanes = tb ? 14 : 11;
   if ((double)plane_elems * nplanes * 4.0 > 2.6e11) return fail(OT_ENOMEM, "ot_prox_create: state would exceed device memory");
 
   const bool fits = resident_fits(G, p.mode, p.balanced != 0);
@@ -332,7 +388,7 @@ int ot_prox_create(const ot_prox_params* params, void* cuda_stream, ot_prox_t* o
   } else if (p.kernel == OT_KERNEL_TMA) {
     tma = true;
   }
-  if (p.algorithm == OT_ALG_PROJECTION) resident = tma = false;
+  if (p.algorithm == OT_ALG_PROJECTION || tb) resident = tma = false;
 
   ot_prox* h = (ot_prox*)calloc(1, sizeof(ot_prox));
   if (!h) return fail(OT_ENOMEM, "ot_prox_create: host allocation failed");
@@ -371,11 +427,22 @@ int ot_prox_create(const ot_prox_params* params, void* cuda_stream, ot_prox_t* o
   h->r = q; q += plane_elems;
   h->p0 = q; q += plane_elems;
   h->p1 = q; q += plane_elems;
+  h->tb = tb;
+  h->tb_depth = p.tb_depth;
+  h->x0s[0] = h->x0;
+  h->x1s[0] = h->x1;
+  h->rs[0] = h->r;
+  if (tb) {
+    h->x0s[1] = q; q += plane_elems;
+    h->x1s[1] = q; q += plane_elems;
+    h->rs[1] = q; q += plane_elems;
+  }
   int n_sm = 0, dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
     n_sm = 152;
   h->tma_grid = (int)(ctas < (double)n_sm ? ctas : n_sm);
   int n_parts = (int)(ctas > (double)G.B ? ctas : G.B);
+  if (tb && temporal_num_ctas(G, p.tb_depth) > n_parts) n_parts = temporal_num_ctas(G, p.tb_depth);
   if (h->admm && 3 * admm_num_blocks(G) > n_parts) n_parts = 3 * admm_num_blocks(G);
   const int n_cert = cert_num_blocks(G);
   const int np = n_parts > n_cert ? n_parts : n_cert;
@@ -435,6 +502,7 @@ int ot_prox_create(const ot_prox_params* params, void* cuda_stream, ot_prox_t* o
     }
   }
   if (resident && e == cudaSuccess) e = prepare_prox_resident(p.mode, p.balanced != 0, G);
+  if (tb && e == cudaSuccess) e = prepare_prox_temporal(p.mode, p.balanced != 0, p.tb_depth);
   if (tma && e == cudaSuccess) {
     e = prepare_prox_tma(p.mode, p.balanced != 0);
     int bw, bh;
@@ -486,9 +554,11 @@ int ot_prox_reset(ot_prox_t h) {
   if (!h) return fail(OT_EINVAL, "ot_prox_reset: NULL handle");
   // everything but the inputs p0, p1 (the last two planes)
   OT_CUDA(cudaMemsetAsync(h->slab, 0, h->plane_elems * 9 * sizeof(float), h->stream), "ot_prox_reset");
+  if (h->tb)
+    OT_CUDA(cudaMemsetAsync(h->x0s[1], 0, h->plane_elems * 3 * sizeof(float), h->stream), "ot_prox_reset");
   if (h->admm)
     OT_CUDA(cudaMemsetAsync(h->admm_slab, 0, h->plane_elems * 10 * sizeof(float), h->stream), "ot_prox_reset");
-  h->cur = 0;
+  set_cur(h, 0);
   return OT_OK;
 }
 
@@ -497,7 +567,7 @@ int ot_prox_step(ot_prox_t h, int32_t n_iter) {
   if (n_iter < 0) return fail(OT_EINVAL, "ot_prox_step: n_iter must be >= 0");
   if (n_iter == 0) return OT_OK;
   OT_CUDA(enqueue_iterations(h, h->cur, n_iter, false), "ot_prox_step");
-  h->cur = parity_after(h, h->cur, n_iter);
+  set_cur(h, parity_after(h, h->cur, n_iter));
   return OT_OK;
 }
 
@@ -527,7 +597,7 @@ int ot_prox_step_timed(ot_prox_t h, int32_t n_iter, double* elapsed_ms) {
   if (e == cudaSuccess) e = cudaEventRecord(e0, h->stream);
   if (e == cudaSuccess) e = enqueue_iterations(h, h->cur, n_iter, false);
   if (e == cudaSuccess) {
-    h->cur = parity_after(h, h->cur, n_iter);
+    set_cur(h, parity_after(h, h->cur, n_iter));
     e = cudaEventRecord(e1, h->stream);
   }
   if (e == cudaSuccess) e = cudaEventSynchronize(e1);

@@ -70,6 +70,21 @@ struct StatePtrs {
   const float* p1;
 };
 
+// Temporally blocked Algorithm 1 (prox_temporal.cu): a CTA of 512 threads
+// stages a 136 x 45 tile (34 float4 groups; 128 own columns with 4 halo
+// columns each side, own rows with a halo of 2 or 4 rows above and below) and
+// runs up to 4 iterations on it.  Every plane is ping-ponged.
+constexpr int kTbGroups = 34;
+constexpr int kTbThreadRows = 15;
+constexpr int kTbRowsPerThread = 3;
+constexpr int kTbExtRows = kTbThreadRows * kTbRowsPerThread;
+constexpr int kTbThreads = 512;
+struct TbPtrs {
+  const float *Mx_in, *My_in, *a_in, *x0_in, *x1_in, *r_in;
+  float *Mx_out, *My_out, *a_out, *x0_out, *x1_out, *r_out;
+  const float *p0, *p1;
+};
+
 // TMA descriptors of the planes one iteration reads (ping-pong resolved).
 struct TmaMaps {
   CUtensorMap a, Mx, My, x0, x1, r, p0, p1;
@@ -107,6 +122,16 @@ int tiled_num_ctas(const Geometry& g);
 cudaError_t launch_prox_tiled(int mode, bool balanced, bool reduce, const Geometry& g,
                               const IterCoeffs& c, const StatePtrs& s, double* partials,
                               cudaStream_t st);
+
+// Temporal blocking: `depth` iterations per pass (2..4) selects the halo
+// (2 rows for depth 2, 4 otherwise); a launch runs n_sub <= halo iterations.
+int temporal_halo(int depth);
+int temporal_tile_rows(int depth);
+int temporal_num_ctas(const Geometry& g, int depth);
+// Raise the kernels' dynamic shared-memory limits (once, outside any capture).
+cudaError_t prepare_prox_temporal(int mode, bool balanced, int depth);
+cudaError_t launch_prox_temporal(int mode, bool balanced, bool reduce, int depth, int n_sub, const Geometry& g,
+                                 const IterCoeffs& c, const TbPtrs& s, double* partials, cudaStream_t st);
 
 size_t resident_smem_bytes(const Geometry& g, int mode, bool balanced);
 bool resident_fits(const Geometry& g, int mode, bool balanced);

@@ -45,6 +45,13 @@ struct ot_prox {
   otp::AdmmCoeffs AC;
   otp::DctPlan* dct;
   int n_id;                  // identity blocks of K: the Laplacian shift c
+  // temporal blocking (OT_KERNEL_TEMPORAL): x0, x1, r are ping-ponged with
+  // M and a; x0 / x1 / r above point at the copies of parity cur
+  bool tb;
+  int tb_depth;
+  float* x0s[2];
+  float* x1s[2];
+  float* rs[2];
 };
 
 // Cap the persistent TMA kernel's grid at (SMs - k) CTAs (otprox_api.cu).

@@ -53,11 +53,55 @@ __device__ __forceinline__ float r_step(float r, float a, const IterCoeffs& c) {
   return q * c.r2;
 }
 
+// Line 4 for one pixel, each marginal: x' = Pi_+((tau1 p + rho x +/- rho tau1 a) / (rho + tau1)),
+// + for x0 (A = [-I, I] puts -x0 in K) and - for x1.
+__device__ __forceinline__ float x0_step(float p, float x, float a, const IterCoeffs& c) {
+  return fmaxf(fmaf(c.cp, p, fmaf(c.cx, x, c.ca * a)), 0.f);
+}
+__device__ __forceinline__ float x1_step(float p, float x, float a, const IterCoeffs& c) {
+  return fmaxf(fmaf(c.cp, p, fmaf(c.cx, x, -c.ca * a)), 0.f);
+}
+
+// Lines 6-7 for one pixel: a' = a + tau2 K(2z' - z), with dmb = D(Mbar) at
+// the pixel and K(z) = D(M) - x0 + x1 - r.
+template <bool BAL>
+__device__ __forceinline__ float dual_step(float dmb, float vx0, float x0, float vx1, float x1, float vr, float r,
+                                           float a, const IterCoeffs& c) {
+  float bk = dmb - (2.f * vx0 - x0) + (2.f * vx1 - x1);
+  if (!BAL) bk -= 2.f * vr - r;
+  return fmaf(c.tau2, bk, a);
+}
+
 __device__ __forceinline__ float norm_term(float mx, float my, int iso) {
   return iso ? sqrtf(fmaf(mx, mx, my * my)) : fabsf(mx) + fabsf(my);
 }
 
 __device__ __forceinline__ bool nonfinite(float v) { return !isfinite(v); }
+
+// One pixel's terms of the stopping-check sums (kNumSums) after an
+// iteration: new flux (nmx, nmy) with its up / left neighbours' new flux,
+// the old flux (mx, my), new and old x0, x1, r, a, and the inputs p0, p1.
+template <int MODE, bool BAL>
+__device__ __forceinline__ void check_terms(float nmxe, float nmye, float nmx_up, float nmy_l, float mx, float my,
+                                            float vx0, float x0, float vx1, float x1, float vr, float r, float va,
+                                            float a, float p0, float p1, const IterCoeffs& C,
+                                            float (&acc)[kNumSums]) {
+  const float kz = (nmxe - nmx_up) + (nmye - nmy_l) - vx0 + vx1 - (BAL ? 0.f : vr);
+  acc[0] = fmaf(kz, kz, acc[0]);
+  const float d0 = nmxe - mx, d1 = nmye - my;
+  const float d2 = vx0 - x0, d3 = vx1 - x1;
+  const float d4 = vr - r, d5 = va - a;
+  acc[1] += d0 * d0 + d1 * d1 + d2 * d2 + d3 * d3 + d4 * d4 + d5 * d5;
+  acc[2] += nmxe * nmxe + nmye * nmye + vx0 * vx0 + vx1 * vx1 + vr * vr + va * va;
+  acc[3] += norm_term(nmxe, nmye, C.iso);
+  acc[4] += C.pexp == 1 ? fabsf(vr) : vr * vr;
+  const float e0 = vx0 - p0, e1 = vx1 - p1;
+  if (MODE == 0) acc[5] = fmaf(e0, e0, acc[5]);
+  if (MODE != 2) acc[5] = fmaf(e1, e1, acc[5]);
+  acc[6] += p0 * p0 + p1 * p1;
+  acc[7] += (nonfinite(va) || nonfinite(nmxe) || nonfinite(nmye) || nonfinite(vx0) || nonfinite(vx1) ||
+             nonfinite(vr) || nonfinite(p0) || nonfinite(p1)) ? 1.f : 0.f;
+}
 
 // Sum kNumSums values over the block in FP64; thread 0 writes them to out.
 // Each thread's own partial sums (a handful of pixels) are FP32: FP64
@@ -252,38 +296,21 @@ __device__ __forceinline__ void prox_tile(const Geometry& G, const IterCoeffs& C
       const bool in = jj < W;
       const float a = compc(a4, e);
       float vx0 = compc(p0[q], e), vx1 = compc(p1[q], e);
-      if (MODE == 0) vx0 = fmaxf(fmaf(C.cp, compc(p0[q], e), fmaf(C.cx, compc(x0[q], e), C.ca * a)), 0.f);
-      if (MODE != 2) vx1 = fmaxf(fmaf(C.cp, compc(p1[q], e), fmaf(C.cx, compc(x1[q], e), -C.ca * a)), 0.f);
+      if (MODE == 0) vx0 = x0_step(compc(p0[q], e), compc(x0[q], e), a, C);
+      if (MODE != 2) vx1 = x1_step(compc(p1[q], e), compc(x1[q], e), a, C);
       const float vr = BAL ? 0.f : r_step(compc(rv[q], e), a, C);
       const float dmb = (compc(mbx, e) - compc(mbx_up, e)) +
                         (compc(mby, e) - (e == 0 ? mby_l : compc(mby, e - 1)));
-      float bk = dmb - (2.f * vx0 - compc(x0[q], e)) + (2.f * vx1 - compc(x1[q], e));
-      if (!BAL) bk -= 2.f * vr - compc(rv[q], e);
-      const float va = fmaf(C.tau2, bk, a);
+      const float va = dual_step<BAL>(dmb, vx0, compc(x0[q], e), vx1, compc(x1[q], e), vr, compc(rv[q], e), a, C);
       comp(nx0, e) = in ? vx0 : 0.f;
       comp(nx1, e) = in ? vx1 : 0.f;
       comp(nr, e) = in ? vr : 0.f;
       comp(na, e) = in ? va : 0.f;
-      if (RED && in) {
-        const float nmxe = compc(nmx[q], e), nmye = compc(nmy[q], e);
-        const float nmx_up = s_mnx[rr - 1][4 * tx + e];
-        const float nmy_l = s_mny[rr - 1][4 * tx + 3 + e];
-        const float kz = (nmxe - nmx_up) + (nmye - nmy_l) - vx0 + vx1 - (BAL ? 0.f : vr);
-        acc[0] = fmaf(kz, kz, acc[0]);
-        const float d0 = nmxe - compc(mx[q], e), d1 = nmye - compc(my[q], e);
-        const float d2 = vx0 - compc(x0[q], e), d3 = vx1 - compc(x1[q], e);
-        const float d4 = vr - compc(rv[q], e), d5 = va - a;
-        acc[1] += d0 * d0 + d1 * d1 + d2 * d2 + d3 * d3 + d4 * d4 + d5 * d5;
-        acc[2] += nmxe * nmxe + nmye * nmye + vx0 * vx0 + vx1 * vx1 + vr * vr + va * va;
-        acc[3] += norm_term(nmxe, nmye, C.iso);
-        acc[4] += C.pexp == 1 ? fabsf(vr) : vr * vr;
-        const float e0 = vx0 - compc(p0[q], e), e1 = vx1 - compc(p1[q], e);
-        if (MODE == 0) acc[5] = fmaf(e0, e0, acc[5]);
-        if (MODE != 2) acc[5] = fmaf(e1, e1, acc[5]);
-        acc[6] += compc(p0[q], e) * compc(p0[q], e) + compc(p1[q], e) * compc(p1[q], e);
-        acc[7] += (nonfinite(va) || nonfinite(nmxe) || nonfinite(nmye) || nonfinite(vx0) || nonfinite(vx1) ||
-                   nonfinite(vr) || nonfinite(compc(p0[q], e)) || nonfinite(compc(p1[q], e))) ? 1.f : 0.f;
-      }
+      if (RED && in)
+        check_terms<MODE, BAL>(compc(nmx[q], e), compc(nmy[q], e), s_mnx[rr - 1][4 * tx + e],
+                               s_mny[rr - 1][4 * tx + 3 + e], compc(mx[q], e), compc(my[q], e), vx0,
+                               compc(x0[q], e), vx1, compc(x1[q], e), vr, compc(rv[q], e), va, a, compc(p0[q], e),
+                               compc(p1[q], e), C, acc);
     }
     const long long off = base + (long long)i * Wp + j;
     st4(S.Mx_out + off, nmx[q]);

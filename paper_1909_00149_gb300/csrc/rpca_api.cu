@@ -118,6 +118,8 @@ int ot_rpca_create(const ot_rpca_params* params, void* cuda_stream, ot_rpca_t* o
   if (!(p.lambda > 0) || !(p.kappa > 0) || !(p.mu > 0) || !(p.rho > 0))
     return fail(OT_EINVAL, "ot_rpca_create: lambda, kappa, mu, rho must be > 0");
   if (!isfinite(p.gamma)) return fail(OT_EINVAL, "ot_rpca_create: gamma must be finite");
+  if (p.prox_kernel == OT_KERNEL_TEMPORAL)
+    return fail(OT_EINVAL, "ot_rpca_create: the inner prox cannot use OT_KERNEL_TEMPORAL (its x planes are shared)");
   if (p.n_inner < 1) return fail(OT_EINVAL, "ot_rpca_create: n_inner must be >= 1");
   if (p.max_iter < 0 || p.check_every < 1 || p.svt_max_sweeps < 1)
     return fail(OT_EINVAL, "ot_rpca_create: max_iter >= 0, check_every >= 1, svt_max_sweeps >= 1 required");

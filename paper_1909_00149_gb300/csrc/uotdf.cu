@@ -174,6 +174,8 @@ int ot_uotdf_create(const ot_uotdf_params* params, void* cuda_stream, ot_uotdf_t
     return fail(OT_EINVAL, "ot_uotdf_create: kappa, mu, rho must be > 0 and lambda >= 0 (finite)");
   if (p.n_inner < 1 || p.max_iter < 0 || p.check_every < 1 || !(p.tol >= 0))
     return fail(OT_EINVAL, "ot_uotdf_create: n_inner >= 1, max_iter >= 0, check_every >= 1, tol >= 0 required");
+  if (p.prox_kernel == OT_KERNEL_TEMPORAL)
+    return fail(OT_EINVAL, "ot_uotdf_create: the inner prox cannot use OT_KERNEL_TEMPORAL (its x planes are shared)");
   ot_uotdf* h = (ot_uotdf*)calloc(1, sizeof(ot_uotdf));
   if (!h) return fail(OT_ENOMEM, "ot_uotdf_create: host allocation failed");
   h->prm = p;

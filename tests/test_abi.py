@@ -85,11 +85,32 @@ def _create(**kw):
     (dict(B=1, H=4, W=4, tau1=1.0, tau2=1.0), "Theorem 1"),
     (dict(B=1, H=4, W=4, tau1=0.5, tau2=0.25), "Theorem 1"),
     (dict(B=1, H=200, W=200, kernel="resident"), "resident"),
+    (dict(B=1, H=4, W=4, kernel="temporal", tb_depth=5), "tb_depth"),
+    (dict(B=1, H=4, W=4, kernel="temporal", tb_depth=1), "tb_depth"),
+    (dict(B=1, H=4, W=4, kernel="temporal", algorithm="projection"), "TEMPORAL"),
+    (dict(B=1, H=4, W=4, kernel=5), "kernel"),
 ])
 def test_create_rejects_invalid_arguments(kw, needle):
     rc, msg = _create(**kw)
     assert rc == -1, (rc, msg)
     assert needle in msg
+
+
+def test_inner_prox_rejects_the_temporal_kernel():
+    """ot_rpca_* and ot_uotdf_* hold the inner prox's x planes as their z, w:
+    the ping-ponged planes of temporal blocking are refused before any CUDA
+    call."""
+    import paper_1909_00149_gb300 as otp
+    from paper_1909_00149_gb300 import _abi
+    p = otp.rpca_default_params(T=4, H=8, W=8, prox_kernel=4)
+    h = ctypes.c_void_p()
+    assert otp.ot_rpca_create(ctypes.byref(p), None, ctypes.byref(h)) == -1
+    assert "OT_KERNEL_TEMPORAL" in otp.ot_last_error().decode()
+    q = _abi.ot_uotdf_params()
+    otp.ot_uotdf_default_params(ctypes.byref(q))
+    q.B, q.H, q.W, q.prox_kernel = 2, 8, 8, 4
+    assert otp.ot_uotdf_create(ctypes.byref(q), None, ctypes.byref(h)) == -1
+    assert "OT_KERNEL_TEMPORAL" in otp.ot_last_error().decode()
 
 
 def test_theorem1_boundary():
@@ -136,6 +157,8 @@ def test_param_structs_match_their_ctypes_mirrors(cdll):
         p = cls.from_buffer_copy(bytes(buf[:n]))
         if cls is _abi.ot_rpca_params:
             assert p.signed_fg == 0 and p.use_graph == 1 and p.rho == 1.0 and p.kappa == 0.005
+        else:
+            assert p.tb_depth == 4 and p.beta == 1.0 and p.check_every == 10
 
 
 def test_committed_warm_start_weights_fit_the_network(cdll):
