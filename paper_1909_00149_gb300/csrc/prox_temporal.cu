@@ -46,7 +46,8 @@ constexpr size_t tb_smem_bytes() {
 
 template <int MODE, bool BAL, bool RED, int KD>
 __global__ void __launch_bounds__(kNT, 1)
-prox_temporal_kernel(const Geometry G, const IterCoeffs C, const TbPtrs S, int n_sub, double* __restrict__ partials) {
+prox_temporal_kernel(const Geometry G, const IterCoeffs C, const TbPtrs S, int n_sub, int pf_stride,
+                     double* __restrict__ partials) {
   constexpr int TH = kEH - 2 * KD;
   extern __shared__ float4 tb_smem[];
   float4(*s_a)[kGX] = reinterpret_cast<float4(*)[kGX]>(tb_smem);
@@ -60,14 +61,20 @@ prox_temporal_kernel(const Geometry G, const IterCoeffs C, const TbPtrs S, int n
   const int tid = threadIdx.x;
   const bool owner = tid < kGX * kGY;
   const int tx = owner ? tid % kGX : 0, ty = owner ? tid / kGX : 0;
-  int t = blockIdx.x;
-  const int bx = t % G.tiles_x;
-  t /= G.tiles_x;
-  const int by = t % G.tiles_y;
-  const int b = t / G.tiles_y;
-  const int i0 = by * TH, j0 = bx * kTW;
   const int H = G.H, W = G.W, Wp = G.Wp;
-  const long long base = (long long)b * G.plane;
+  const int ntiles = G.B * G.tiles_x * G.tiles_y;
+  // tile t -> problem b, tile row by, tile column bx; rows from i0 - KD, columns from j0 - 4
+  auto tile_origin = [&](int t, long long& base, int& i0, int& j0) {
+    const int bx = t % G.tiles_x;
+    t /= G.tiles_x;
+    const int by = t % G.tiles_y;
+    base = (long long)(t / G.tiles_y) * G.plane;
+    i0 = by * TH;
+    j0 = bx * kTW;
+  };
+  long long base;
+  int i0, j0;
+  tile_origin(blockIdx.x, base, i0, j0);
   const int j = j0 - 4 + 4 * tx;
   const bool colok = owner && j >= 0 && j < Wp;
   const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -91,6 +98,23 @@ prox_temporal_kernel(const Geometry G, const IterCoeffs C, const TbPtrs S, int n
       s_p1[u][tx] = ok ? ld4(S.p1 + off) : z4;
     }
   }
+  // ---- L2 prefetch of the tile the next wave runs here (one CTA per SM:
+  // block + pf_stride), one row of one plane per thread, once this block's
+  // own loads are in flight
+  if (pf_stride > 0 && blockIdx.x + pf_stride < ntiles && tid < 8 * kEH) {
+    long long nb;
+    int ni0, nj0;
+    tile_origin(blockIdx.x + pf_stride, nb, ni0, nj0);
+    const int pl = tid / kEH, i = ni0 - KD + tid % kEH;
+    const float* src = pl == 0 ? S.Mx_in : pl == 1 ? S.My_in : pl == 2 ? S.a_in : pl == 3 ? S.p0 : pl == 4 ? S.p1
+                     : pl == 5 ? (MODE == 0 ? S.x0_in : nullptr) : pl == 6 ? (MODE != 2 ? S.x1_in : nullptr)
+                     : (!BAL ? S.r_in : nullptr);
+    const int c0 = nj0 - 4 > 0 ? nj0 - 4 : 0, c1 = nj0 + kTW + 4 < Wp ? nj0 + kTW + 4 : Wp;
+    if (src && i >= 0 && i < H && c1 > c0) {
+      const float* row = src + nb + (long long)i * Wp + c0;
+      asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(row), "r"((c1 - c0) * 4) : "memory");
+    }
+  }
   __syncthreads();
 
   float acc[kNumSums];
@@ -99,11 +123,17 @@ prox_temporal_kernel(const Geometry G, const IterCoeffs C, const TbPtrs S, int n
 
   for (int s = 1; s <= n_sub; ++s) {
     const bool chk = RED && s == n_sub;
-    // ---- line 3 on every owned pixel; Mbar = 2M' - M to shared memory
-    if (owner) {
+    // the region later iterations still read: rows [lo, kEH - lo) for a, x, r
+    // (the halo shrinks by one row per iteration), one row more above for M;
+    // the halo column groups only before the last iteration
+    const int lo = KD - (n_sub - s);
+    const bool edge_groups = s < n_sub;
+    // ---- line 3; Mbar = 2M' - M to shared memory
+    if (owner && (edge_groups || tx < kGX - 1)) {
 #pragma unroll
       for (int q = 0; q < kRPT; ++q) {
         const int u = ty + kGY * q;
+        if (u < lo - 1 || u >= kEH - lo) continue;
         const int i = i0 - KD + u;
         const bool rowin = i >= 0 && i < H && j >= 0;
         const float4 ac = s_a[u][tx];
@@ -136,17 +166,18 @@ prox_temporal_kernel(const Geometry G, const IterCoeffs C, const TbPtrs S, int n
       }
     }
     __syncthreads();
-    // ---- lines 4-7 on every owned pixel; a' in place (only the own pixel's a is read here)
-    if (owner) {
+    // ---- lines 4-7; a' in place (only the own pixel's a is read here)
+    if (owner && (edge_groups || (tx >= 1 && tx < kGX - 1))) {
 #pragma unroll
       for (int q = 0; q < kRPT; ++q) {
         const int u = ty + kGY * q;
+        if (u < lo || u >= kEH - lo) continue;
         const int i = i0 - KD + u;
         const bool rowin = i >= 0 && i < H && j >= 0;
         const bool own = chk && u >= KD && u < KD + TH && i < H && tx >= 1 && tx < kGX - 1;
         const float4 a4 = s_a[u][tx];
         const float4 mbx = s_mbx[u][tx];
-        const float4 mbx_up = u > 0 ? s_mbx[u - 1][tx] : z4;
+        const float4 mbx_up = s_mbx[u - 1][tx];
         const float4 mby = s_mby[u][tx];
         const float mby_l = tx > 0 ? s_mby[u][tx - 1].w : 0.f;
         const float4 p04 = s_p0[u][tx], p14 = s_p1[u][tx];
@@ -213,8 +244,16 @@ prox_temporal_kernel(const Geometry G, const IterCoeffs C, const TbPtrs S, int n
 template <int MODE, bool BAL, bool RED, int KD>
 cudaError_t launch_t(const Geometry& g, const IterCoeffs& c, const TbPtrs& s, int n_sub, double* partials,
                      cudaStream_t st) {
+  // one CTA per SM: the block pf_stride further runs on this SM in the next wave
+  static int n_sm = 0;
+  if (n_sm == 0) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) !=
+                                                   cudaSuccess)
+      n_sm = 152;
+  }
   prox_temporal_kernel<MODE, BAL, RED, KD>
-      <<<temporal_num_ctas(g, KD), kNT, tb_smem_bytes<RED>(), st>>>(g, c, s, n_sub, partials);
+      <<<temporal_num_ctas(g, KD), kNT, tb_smem_bytes<RED>(), st>>>(g, c, s, n_sub, n_sm, partials);
   return cudaGetLastError();
 }
 
