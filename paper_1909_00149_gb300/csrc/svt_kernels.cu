@@ -469,6 +469,85 @@ constexpr int kJregThreads = 512;
 constexpr int kJregCheck = 16;  // rounds between stopping tests
 constexpr int kJregM = 4;       // pairs per register segment of a V row
 
+// C[i][j] = sum_k X[k][i] d_k Y[k][j] for TP x TP matrices in shared memory
+// with 16-byte aligned rows of LDA floats (d_k = 1 when diag is null): both
+// operands are read along k as float4 rows.  Thread t owns the 4 x 4 output
+// block t % NB (NB = (TP/4)^2) over half of the k range; the second half's
+// partials pass through C to the first half's threads, which add them.
+// Every thread of the block must reach it; C may not alias X or Y.
+template <int TP, int LDA>
+__device__ __forceinline__ void kgemm(const float* X, const float* Y, float* C, const float* diag) {
+  static_assert(LDA % 4 == 0 && TP % 4 == 0, "float4 rows");
+  constexpr int NBS = TP / 4, NB = NBS * NBS;
+  constexpr int KS = 2 * NB <= kJregThreads ? 2 : 1;
+  static_assert(NB * KS <= kJregThreads, "one output block per thread");
+  const int t = threadIdx.x;
+  const int blk = t % NB, part = t / NB;
+  const int bi = blk / NBS, bj = blk % NBS;
+  float acc[4][4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[r][c] = 0.f;
+  if (part < KS) {
+    const int k0 = part * (TP / KS);
+#pragma unroll 4
+    for (int k = k0; k < k0 + TP / KS; ++k) {
+      const float4 x = *reinterpret_cast<const float4*>(X + k * LDA + 4 * bi);
+      float4 y = *reinterpret_cast<const float4*>(Y + k * LDA + 4 * bj);
+      if (diag) {
+        const float dk = diag[k];
+        y.x *= dk;
+        y.y *= dk;
+        y.z *= dk;
+        y.w *= dk;
+      }
+      const float xv[4] = {x.x, x.y, x.z, x.w}, yv[4] = {y.x, y.y, y.z, y.w};
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[r][c] = fmaf(xv[r], yv[c], acc[r][c]);
+    }
+  }
+  if (KS == 2 && part == 1) {
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+      *reinterpret_cast<float4*>(C + (4 * bi + r) * LDA + 4 * bj) =
+          make_float4(acc[r][0], acc[r][1], acc[r][2], acc[r][3]);
+  }
+  __syncthreads();
+  if (part == 0) {
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      float4 o = make_float4(acc[r][0], acc[r][1], acc[r][2], acc[r][3]);
+      if (KS == 2) {
+        const float4 h = *reinterpret_cast<const float4*>(C + (4 * bi + r) * LDA + 4 * bj);
+        o.x += h.x;
+        o.y += h.y;
+        o.z += h.z;
+        o.w += h.w;
+      }
+      *reinterpret_cast<float4*>(C + (4 * bi + r) * LDA + 4 * bj) = o;
+    }
+  }
+}
+
+// The Newton-Schulz step V <- V (3 I - V^T V) / 2 of reorthonormalize, in
+// k-major products: M = V^T V, then V = (V^T)^T M with V^T staged in Out.
+template <int TP, int LDA>
+__device__ __forceinline__ void reorthonormalize_k(float* V, float* Tmp, float* Out) {
+  kgemm<TP, LDA>(V, V, Tmp, nullptr);   // V^T V
+  __syncthreads();
+  for (int e = threadIdx.x; e < TP * TP; e += blockDim.x) {
+    const int i = e / TP, j = e % TP;
+    Tmp[i * LDA + j] = (i == j ? 1.5f : 0.f) - 0.5f * Tmp[i * LDA + j];
+    Out[i * LDA + j] = V[j * LDA + i];
+  }
+  __syncthreads();
+  kgemm<TP, LDA>(Out, Tmp, V, nullptr);   // V M (M symmetric)
+  __syncthreads();
+}
+
 __host__ __device__ constexpr int upper_idx(int i, int j, int ld) { return i < j ? i * ld + j : j * ld + i; }
 
 // slot that the value at slot s moves to between rounds, and its inverse
@@ -488,7 +567,7 @@ __device__ __forceinline__ float rot_hi(float c, float s, float x, float y) { re
 
 template <int TP>
 constexpr size_t jreg_smem() {
-  return (size_t)(4 * TP * (TP + 1) + TP) * sizeof(float);
+  return (size_t)(4 * TP * (TP + 4) + TP) * sizeof(float);
 }
 
 template <int TP>
@@ -496,7 +575,7 @@ __global__ void __launch_bounds__(kJregThreads, 1)
 jacobi_reg_kernel(const double* __restrict__ G, int warm, float theta, int max_sweeps, float tol,
                   float* __restrict__ V_io, float* __restrict__ Wm, float* __restrict__ sig_out,
                   int* __restrict__ rounds_out) {
-  constexpr int LDA = TP + 1;
+  constexpr int LDA = TP + 4;            // 16-byte aligned rows for the float4 products
   constexpr int NP = TP / 2;
   constexpr int S = NP / kJregM;           // register segments per V row
   constexpr int NOFF = NP * (NP - 1) / 2;  // off-diagonal pair blocks kb < kc
@@ -529,6 +608,8 @@ jacobi_reg_kernel(const double* __restrict__ G, int warm, float theta, int max_s
   __shared__ int s_nbig;
   __shared__ double s_wbig[kMaxDeflate][TP];   // sqrt(lam) v of the deflated pairs, FP64
   __shared__ int s_floor;                 // the plain off-diagonal norm is at its FP32 floor
+  __shared__ float s_sig[TP];
+  __shared__ double s_sq[kMaxDeflate];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   if (tid == 0) {
     s_best = 3.0e38f;
@@ -620,17 +701,26 @@ jacobi_reg_kernel(const double* __restrict__ G, int warm, float theta, int max_s
       g[u] = e < TP * TP ? __ldg(G + e) : 0.0;
       v[u] = (e < TP * TP && warm) ? V_io[e] : 0.f;
     }
-    if (tid == 0) {
-      // warm start: the previous solve's dominant eigenpairs (sigma > 8 theta)
-      // are deflated from G in FP64 before G is rounded to FP32, see below
-      int nb = 0;
-      for (int j = 0; j < TP; ++j) {
-        const float sg = warm && theta > 0.f ? sig_out[j] : 0.f;
-        const bool big = sg > 8.f * theta && nb < kMaxDeflate;
-        if (big) s_big[nb++] = (unsigned char)j;
-        s_lam_big[j] = big ? sg * sg : 0.f;
+    // warm start: the previous solve's dominant eigenpairs (sigma > 8 theta),
+    // the first kMaxDeflate of them in index order, are deflated from G in
+    // FP64 before G is rounded to FP32, see below
+    if (tid < TP) s_sig[tid] = warm && theta > 0.f ? sig_out[tid] : 0.f;
+    __syncthreads();
+    if (warp == 0) {
+      int base = 0;
+#pragma unroll
+      for (int h = 0; h < TP; h += 32) {
+        const int j = h + lane;
+        const float sg = j < TP ? s_sig[j] : 0.f;
+        const bool over = j < TP && sg > 8.f * theta;
+        const unsigned m = __ballot_sync(0xffffffffu, over);
+        const int rank = base + __popc(m & ((1u << lane) - 1u));
+        const bool big = over && rank < kMaxDeflate;
+        if (big) s_big[rank] = (unsigned char)j;
+        if (j < TP) s_lam_big[j] = big ? sg * sg : 0.f;
+        base += __popc(m);
       }
-      s_nbig = nb;
+      if (lane == 0) s_nbig = base < kMaxDeflate ? base : kMaxDeflate;
     }
 #pragma unroll
     for (int u = 0; u < NL; ++u) {
@@ -652,28 +742,34 @@ jacobi_reg_kernel(const double* __restrict__ G, int warm, float theta, int max_s
     // of the dominant eigenvalues, harmlessly).
     const int nb = s_nbig;
     // w_b = sqrt(lam_c) v_c in FP64, once, so that each entry costs one FP64
-    // FMA per deflated pair (FP64 throughput is a small fraction of FP32 here)
+    // FMA per deflated pair (FP64 throughput is a small fraction of FP32
+    // here); one square root per pair
+    if (tid < nb) s_sq[tid] = sqrt((double)s_lam_big[s_big[tid]]);
+    __syncthreads();
     for (int e = tid; e < nb * TP; e += kJregThreads) {
       const int b = e / TP, k = e % TP, c = s_big[b];
-      s_wbig[b][k] = sqrt((double)s_lam_big[c]) * (double)V[k * LDA + c];
+      s_wbig[b][k] = s_sq[b] * (double)V[k * LDA + c];
     }
     __syncthreads();
+    // G' on the upper triangle (G is symmetric), mirrored: A is exactly symmetric
 #pragma unroll
     for (int u = 0; u < NL; ++u) {
       const int e = tid + u * kJregThreads;
       if (e < TP * TP) {
         const int i = e / TP, j = e % TP;
-        double gd = g[u];
-        for (int b = 0; b < nb; ++b) gd = fma(-s_wbig[b][i], s_wbig[b][j], gd);
-        A[i * LDA + j] = (float)gd;
+        if (i <= j) {
+          double gd = g[u];
+          for (int b = 0; b < nb; ++b) gd = fma(-s_wbig[b][i], s_wbig[b][j], gd);
+          A[i * LDA + j] = A[j * LDA + i] = (float)gd;
+        }
       }
     }
   }
   __syncthreads();
   if (warm) {   // A <- V^T G' V + diag(lam_big)
-    small_gemm<TP, LDA, (TP >= 32 ? 2 : 4)>(A, V, Tmp, false, nullptr);
+    kgemm<TP, LDA>(A, V, Tmp, nullptr);   // G' V (G' symmetric)
     __syncthreads();
-    small_gemm<TP, LDA, (TP >= 32 ? 2 : 4)>(V, Tmp, A, true, nullptr);
+    kgemm<TP, LDA>(V, Tmp, A, nullptr);   // V^T (G' V)
     __syncthreads();
     if (tid < TP) A[tid * LDA + tid] += s_lam_big[tid];
     __syncthreads();
@@ -757,7 +853,7 @@ jacobi_reg_kernel(const double* __restrict__ G, int warm, float theta, int max_s
           const int i = e / TP, j = e % TP;
           if (i < j && (s_act[i] | s_act[j])) {
             const float gap = fabsf(s_dg[i] - s_dg[j]) - 2.f * eps;
-            const float dd = gap > 0.f ? fminf(fmaxf(s_slope[i], s_slope[j]), __frcp_rn(gap))
+            const float dd = gap > 0.f ? fminf(fmaxf(s_slope[i], s_slope[j]), __fdividef(1.f, gap))
                                        : fmaxf(s_slope[i], s_slope[j]);
             const float t = A[i * LDA + j] * dd;
             // (i, j) and (j, i) of the change of Wm, seen through X: sigma_i^2 + sigma_j^2
@@ -906,13 +1002,13 @@ jacobi_reg_kernel(const double* __restrict__ G, int warm, float theta, int max_s
   float* Out = sm + (cur ^ 1) * (TP * LDA);
   // a solve that rotated nothing leaves V as the previous solve left it,
   // already re-orthonormalised
-  if (done > 0) reorthonormalize<TP, LDA, (TP >= 32 ? 2 : 4)>(V, Tmp, Out);
+  if (done > 0) reorthonormalize_k<TP, LDA>(V, Tmp, Out);
   for (int e = tid; e < TP * TP; e += kJregThreads) {
     const int i = e / TP, j = e % TP;
     Tmp[i * LDA + j] = V[j * LDA + i];
   }
   __syncthreads();
-  small_gemm<TP, LDA, (TP >= 32 ? 2 : 4)>(V, Tmp, Out, false, f);    // V diag(f) V^T
+  kgemm<TP, LDA>(Tmp, Tmp, Out, f);    // V diag(f) V^T = (V^T)^T diag(f) V^T
   __syncthreads();
   for (int e = tid; e < TP * TP; e += kJregThreads) {
     const int i = e / TP, j = e % TP;
