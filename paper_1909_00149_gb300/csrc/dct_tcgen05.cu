@@ -187,28 +187,57 @@ tc_gemm_kernel(const __grid_constant__ TcMaps maps, const TcEpi ep, int* __restr
     const int m = m0 + warp * 32 + lane;            // this thread's tile row
     const bool row_ok = m < ep.M;
     const int b = row_ok ? m / ep.rows_per_prob : 0, i = row_ok ? m % ep.rows_per_prob : 0;
+    // untransposed output: the warp's 32 x 32 block goes through shared
+    // memory (the stage buffers are idle once the accumulator is complete),
+    // so that a lane holds a column and each store covers a row segment
+    float* tw = reinterpret_cast<float*>(smem) + warp * 32 * 33;
 #pragma unroll 1
     for (int cc = 0; cc < NT / 32; ++cc) {
       float v[32], w[32];
       tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(cc * 32), v);
       tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(NT + cc * 32), w);
-      if (!row_ok) continue;
       const int nb = n0 + cc * 32;
+      if (TRANS) {
+        if (!row_ok) continue;
 #pragma unroll
-      for (int j = 0; j < 32; ++j) {
-        const int n = nb + j;
-        if (n >= ep.N) break;
-        float x = v[j] + w[j];
-        if (SCALE) x *= __ldg(ep.inv_lam + (long long)i * ep.lam_ld + n);
-        const long long o = TRANS ? ((long long)b * ep.N + n) * ep.out_ld + i : (long long)m * ep.out_ld + n;
-        if (OUT_BF16) {
-          __nv_bfloat16 pc[kMaxPieces];
-          split_pieces<NP>(x, pc);
+        for (int j = 0; j < 32; ++j) {
+          const int n = nb + j;
+          if (n >= ep.N) break;
+          float x = v[j] + w[j];
+          if (SCALE) x *= __ldg(ep.inv_lam + (long long)i * ep.lam_ld + n);
+          const long long o = ((long long)b * ep.N + n) * ep.out_ld + i;
+          if (OUT_BF16) {
+            __nv_bfloat16 pc[kMaxPieces];
+            split_pieces<NP>(x, pc);
 #pragma unroll
-          for (int q = 0; q < NP; ++q) ep.out[q][o] = pc[q];
-        } else {
-          ep.out_f[o] = x;
+            for (int q = 0; q < NP; ++q) ep.out[q][o] = pc[q];
+          } else {
+            ep.out_f[o] = x;
+          }
         }
+      } else {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) tw[lane * 33 + j] = v[j] + w[j];
+        __syncwarp();
+        const int n = nb + lane;
+        for (int r = 0; r < 32; ++r) {
+          const int mr = m0 + warp * 32 + r;
+          if (mr >= ep.M) break;
+          if (n < ep.N) {
+            float x = tw[r * 33 + lane];
+            if (SCALE) x *= __ldg(ep.inv_lam + (long long)(mr % ep.rows_per_prob) * ep.lam_ld + n);
+            const long long o = (long long)mr * ep.out_ld + n;
+            if (OUT_BF16) {
+              __nv_bfloat16 pc[kMaxPieces];
+              split_pieces<NP>(x, pc);
+#pragma unroll
+              for (int q = 0; q < NP; ++q) ep.out[q][o] = pc[q];
+            } else {
+              ep.out_f[o] = x;
+            }
+          }
+        }
+        __syncwarp();
       }
     }
   } else if (tid == 0) {
