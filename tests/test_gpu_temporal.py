@@ -122,3 +122,40 @@ def test_full_size_video_batch(lib):
     assert_identical(a, b)
     o = P.iterate(p0.astype(np.float64), p1.astype(np.float64), oracle_params(), 20)
     check_state(b, o, 1e-5, np.linalg.norm(p0))
+
+
+def _run_sequence(lib, kernel, p0, p1, pred):
+    """After an odd number of passes (x0, x1, r in the second copy under
+    temporal blocking): a warm start, more iterations, the certificate, a
+    reset and a fresh run."""
+    B, H, W = p0.shape
+    kw = dict(mu=MU, rho=RHO, kernel=kernel, use_graph=False)
+    if kernel == "temporal":
+        kw["tb_depth"] = 4
+    with lib.OtProx(B, H, W, **kw) as s:
+        s.set_input(p0, p1)
+        s.step(5)                    # temporal: passes of 3 and 2
+        s.step(3)                    # one pass: the parity is odd now
+        s.warm_start(pred, 1e-3)
+        s.step(7)
+        ev = s.evaluate()
+        st1 = {k: v.double().cpu().numpy() for k, v in s.get_state().items()}
+        s.reset()
+        s.step(6)
+        st2 = {k: v.double().cpu().numpy() for k, v in s.get_state().items()}
+    return ev, st1, st2
+
+
+def test_warm_start_evaluate_reset_follow_the_parity(lib):
+    """warm_start writes x0, x1 (and M, r, a) into the current copy, the
+    certificate reads it, and reset returns to the first copy: every result
+    equals the tiled kernel's."""
+    p0, p1 = inputs(2, 60, 140)
+    g = torch.Generator(device="cpu").manual_seed(5)
+    pred = (1e-3 * torch.randn((2, 4, 60, 140), generator=g)).cuda()
+    ev_a, a1, a2 = _run_sequence(lib, "tiled", p0, p1, pred)
+    ev_b, b1, b2 = _run_sequence(lib, "temporal", p0, p1, pred)
+    assert_identical(a1, b1)
+    assert_identical(a2, b2)
+    for key in ("objective", "primal_feasible", "dual_obj", "rel_gap"):
+        assert ev_a[key] == ev_b[key], key
