@@ -43,6 +43,32 @@ def test_svt_matches_oracle(lib, N, T, rank):
     assert np.sum(np.linalg.svd(Yg, compute_uv=False) > 1e-3 * s_ref[0]) == np.sum(s_ref > 1e-3 * s_ref[0])
 
 
+@pytest.mark.parametrize("T", [16, 64])
+def test_svt_clustered_singular_values_near_the_threshold(lib, T):
+    """Repeated singular values (degenerate eigenvalues of the Gram) in
+    clusters at 3 theta, just above and just below theta, and below it: the
+    shrinkage keeps the clusters above theta, drops the rest, and the result
+    matches the oracle's to 1e-5."""
+    N = 20000
+    rng = np.random.default_rng(77 + T)
+    U, _ = np.linalg.qr(rng.normal(size=(N, T)))
+    Vt, _ = np.linalg.qr(rng.normal(size=(T, T)))
+    theta = 5.0
+    s = np.zeros(T)
+    k = T // 4
+    s[:k] = 3 * theta
+    s[k:2 * k] = 1.02 * theta
+    s[2 * k:3 * k] = 0.98 * theta
+    s[3 * k:] = 0.3 * theta
+    Xm = ((U * s) @ Vt).astype(np.float32)
+    ref = SV.svt(Xm.astype(np.float64), theta)
+    Yg = lib.svt(torch.from_numpy(np.ascontiguousarray(Xm.T)).cuda(), theta).cpu().numpy().T.astype(np.float64)
+    assert np.linalg.norm(Yg - ref) <= TOL * np.linalg.norm(ref)
+    sv = np.linalg.svd(Yg, compute_uv=False)
+    assert np.allclose(sv[:k], 2 * theta, rtol=1e-4) and np.allclose(sv[k:2 * k], 0.02 * theta, rtol=2e-2)
+    assert np.all(sv[2 * k:] <= 1e-4 * theta)
+
+
 def test_svt_zero_threshold_is_identity(lib):
     rng = np.random.default_rng(1)
     Xm = rng.normal(size=(16, 500)).astype(np.float32)
