@@ -100,6 +100,18 @@ def solve(p0, p1, net: UNet | None = None, gate: float = 0.0, **params) -> dict:
 WEIGHTS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "weights", "unet_warmstart_256.npz")
 
 
+def fold_output_scale(net: UNet, channel: int, factor: float) -> None:
+    """Multiply output ``channel`` of the network by ``factor``: the last
+    layer is a 1x1 convolution (weights [4, base], then biases [4]), so its
+    weights and bias of that channel are scaled."""
+    params = net.get_params().astype(np.float32)
+    c = net.base
+    off = params.size - (4 * c + 4)
+    params[off + channel * c:off + (channel + 1) * c] *= factor
+    params[off + 4 * c + channel] *= factor
+    net.set_params(params)
+
+
 def save_params(net: UNet, path: str, **meta) -> None:
     """The network's FP32 parameters (``ot_unet_get_params`` order) and the
     training record, as a compressed .npz."""
@@ -139,6 +151,9 @@ def main(argv=None) -> None:
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--seed", type=int, default=1000)
     ap.add_argument("--out", default=WEIGHTS)
+    ap.add_argument("--a-weight", type=float, default=1.0,
+                    help="train on this multiple of the dual a (its squared error weighs a-weight^2 in the "
+                         "loss); the factor is divided out of the output layer before saving")
     a = ap.parse_args(argv)
     sys.path.insert(0, os.getcwd())
     from synth import rng_for, warmstart_pairs
@@ -149,15 +164,21 @@ def main(argv=None) -> None:
     torch.cuda.synchronize()
     t_solve = time.perf_counter() - t0
     del p0, p1
+    rms = [float(torch.sqrt(torch.mean(T[:, c] ** 2))) for c in range(len(STATE_CHANNELS))]
+    if a.a_weight != 1.0:
+        T[:, STATE_CHANNELS.index("a")] *= a.a_weight
     net = UNet(a.size, a.size, a.batch, 32)
     net.init(seed=0)
     t0 = time.perf_counter()
     losses = train(net, X, T, epochs=a.epochs, batch=a.batch, lr=a.lr)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
+    if a.a_weight != 1.0:
+        fold_output_scale(net, STATE_CHANNELS.index("a"), 1.0 / a.a_weight)
     save_params(net, a.out, pairs=a.pairs, size=a.size, epochs=a.epochs, batch=a.batch, lr=a.lr, seed=a.seed,
                 mu=kw["mu"], rho=kw["rho"], tol=kw["tol"], loss_per_epoch=np.array(losses),
-                solve_seconds=t_solve, train_seconds=t_train, target_iters=np.array(its))
+                solve_seconds=t_solve, train_seconds=t_train, target_iters=np.array(its),
+                a_weight=a.a_weight, target_rms=np.array(rms))
     print({"out": a.out, "loss_per_epoch": losses, "solve_s": round(t_solve, 1), "train_s": round(t_train, 1)},
           flush=True)
 
