@@ -154,6 +154,9 @@ def main(argv=None) -> None:
     ap.add_argument("--a-weight", type=float, default=1.0,
                     help="train on this multiple of the dual a (its squared error weighs a-weight^2 in the "
                          "loss); the factor is divided out of the output layer before saving")
+    ap.add_argument("--normalize", action="store_true",
+                    help="train on targets scaled to unit RMS per channel (equal relative errors); the scales "
+                         "are divided out of the output layer before saving")
     a = ap.parse_args(argv)
     sys.path.insert(0, os.getcwd())
     from synth import rng_for, warmstart_pairs
@@ -165,20 +168,24 @@ def main(argv=None) -> None:
     t_solve = time.perf_counter() - t0
     del p0, p1
     rms = [float(torch.sqrt(torch.mean(T[:, c] ** 2))) for c in range(len(STATE_CHANNELS))]
-    if a.a_weight != 1.0:
-        T[:, STATE_CHANNELS.index("a")] *= a.a_weight
+    scale = [1.0 / max(r, 1e-30) if a.normalize else 1.0 for r in rms]
+    scale[STATE_CHANNELS.index("a")] *= a.a_weight
+    for c, f in enumerate(scale):
+        if f != 1.0:
+            T[:, c] *= f
     net = UNet(a.size, a.size, a.batch, 32)
     net.init(seed=0)
     t0 = time.perf_counter()
     losses = train(net, X, T, epochs=a.epochs, batch=a.batch, lr=a.lr)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
-    if a.a_weight != 1.0:
-        fold_output_scale(net, STATE_CHANNELS.index("a"), 1.0 / a.a_weight)
+    for c, f in enumerate(scale):
+        if f != 1.0:
+            fold_output_scale(net, c, 1.0 / f)
     save_params(net, a.out, pairs=a.pairs, size=a.size, epochs=a.epochs, batch=a.batch, lr=a.lr, seed=a.seed,
                 mu=kw["mu"], rho=kw["rho"], tol=kw["tol"], loss_per_epoch=np.array(losses),
                 solve_seconds=t_solve, train_seconds=t_train, target_iters=np.array(its),
-                a_weight=a.a_weight, target_rms=np.array(rms))
+                a_weight=a.a_weight, normalized=a.normalize, target_rms=np.array(rms))
     print({"out": a.out, "loss_per_epoch": losses, "solve_s": round(t_solve, 1), "train_s": round(t_train, 1)},
           flush=True)
 
